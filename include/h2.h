@@ -1,0 +1,158 @@
+/*
+ * h2.h -- C ABI of the GB300 H^2 matrix-vector product library (libh2gb300.so).
+ *
+ * The library computes y = A^H x for an H^2 matrix A^H (Boukaram, Turkiyyah,
+ * Keyes, "Hierarchical Matrix Operations on GPUs", Sec. 2.2 and Sec. 4):
+ *
+ *   A^H = A_D + A_LR, y = A_D x + A_LR x                               (Sec. 4.1)
+ *   leaf projection  xhat^q_j = V_j^T x(j)                              (Sec. 4.2, Alg. 2)
+ *   upsweep          xhat^{l-1}_p = sum_{c child of p} F_c^T xhat^l_c   (Eq. 2)
+ *   coupling         yhat^l_i = sum_{j in b_i} S^l_ij xhat^l_j          (Eq. 3, Alg. 3)
+ *   downsweep        yhat^l_c += E_c yhat^{l-1}_p                       (Eq. 5, Alg. 4)
+ *   leaf expansion   y(i) = U_i yhat^q_i                                (Eq. 4, Alg. 4)
+ *   dense blocks     y(i) += sum_j D_ij x(j)                            (Sec. 2.2)
+ *
+ * Conventions shared by every entry point
+ *   - All integer sizes are int64_t or int32_t as declared; all matrices are
+ *     column-major; every block is stored contiguously.
+ *   - Vectors are in cluster (tree) order: x(j) is the contiguous range
+ *     [leaf_offset[j], leaf_offset[j+1]) of x. Permuting from the caller's
+ *     point order is the caller's job.
+ *   - The basis trees are one complete binary tree of depth q in heap order:
+ *     root 0, children of node h are 2h+1 and 2h+2, level l holds nodes
+ *     2^l-1 .. 2^(l+1)-2, the leaves are level q (the paper's flattened tree,
+ *     Sec. 3.1, with head/next/parent implied by the numbering).
+ *   - Errors: every call returns an h2_status; nothing is thrown across the
+ *     ABI. h2_last_error() gives a message for the calling thread's last
+ *     failed call.
+ */
+#ifndef H2GB300_H
+#define H2GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  H2_OK = 0,
+  H2_ERR_INVALID = 1,      /* bad argument or malformed tree / block structure */
+  H2_ERR_OOM = 2,          /* device or host allocation failed */
+  H2_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  H2_ERR_UNSUPPORTED = 4,  /* valid input outside what the kernels implement */
+  H2_ERR_TIMEOUT = 5       /* a bounded device-side wait ran out */
+} h2_status;
+
+/* How h2_create stores the matrix on the device. */
+typedef enum {
+  H2_FP64 = 0  /* plain form: FP64 storage; products in double-float
+                  (pairs of FP32 with error-free transformations, 46+ bits) */
+} h2_storage;
+
+typedef struct h2_matrix_s* h2_handle;
+
+/*
+ * Description of an H^2 matrix (host memory, read-only, owned by the caller;
+ * h2_create deep-copies everything, so the caller may free it on return).
+ *
+ *   n            matrix order (>= 1)
+ *   depth        q, leaf level of the cluster tree (0 <= q <= 24)
+ *   rank         k, the uniform rank of every basis node (1 <= k <= 64)
+ *   symmetric    nonzero: the column tree equals the row tree (V = U, F = E;
+ *                V and F are then ignored and may be NULL)
+ *   storage      an h2_storage value
+ *   leaf_offset  [2^q + 1] int64; leaf_offset[0] = 0, leaf_offset[2^q] = n,
+ *                leaf sizes 1 .. 64
+ *   U, V         leaf bases: leaf i is a size_i x k block at +leaf_offset[i]*k
+ *                (Table 1: U, V)
+ *   E, F         transfer matrices: node h >= 1 has a k x k block at
+ *                +(h-1)*k*k; E_c relates child c to its parent by Eq. 1
+ *   S_rowptr     [2^(q+1)] int32 block-row pointers over ALL nodes (heap order)
+ *   S_colidx     [S_rowptr[last]] heap index of each block's column node; it
+ *                must lie on the same level as the row node (Sec. 2.2, Fig. 4)
+ *   S_val        k x k coupling block b at +b*k*k
+ *   D_rowptr     [2^q + 1] int32 block-row pointers over the leaves
+ *   D_colidx     [D_rowptr[2^q]] leaf index of each dense block's column
+ *   D_val        dense blocks in block order, block (i, j) is size_i x size_j,
+ *                each one following the previous one without gaps
+ *   check_cover  nonzero: also verify that the coupling and dense blocks
+ *                together cover every (row leaf, column leaf) pair exactly
+ *                once (O(leaves * (q * row length)) host work)
+ */
+typedef struct {
+  int64_t n;
+  int32_t depth;
+  int32_t rank;
+  int32_t symmetric;
+  int32_t storage;
+  const int64_t* leaf_offset;
+  const double* U;
+  const double* V;
+  const double* E;
+  const double* F;
+  const int32_t* S_rowptr;
+  const int32_t* S_colidx;
+  const double* S_val;
+  const int32_t* D_rowptr;
+  const int32_t* D_colidx;
+  const double* D_val;
+  int32_t check_cover;
+} h2_desc;
+
+/*
+ * Validate d, copy the matrix to the current CUDA device in the layout the
+ * kernels stream, and allocate the per-handle workspace (the xhat / yhat
+ * vector trees, Sec. 4.5). Synchronous. On success *out owns all device
+ * memory until h2_destroy.
+ * Errors: H2_ERR_INVALID (NULL pointers, sizes, non-monotone row pointers,
+ * column indices off the row's level or out of range, leaf sizes, non-finite
+ * values or |value| >= 2^126, cover violation), H2_ERR_UNSUPPORTED (k > 64,
+ * leaf size > 64), H2_ERR_OOM, H2_ERR_CUDA.
+ */
+h2_status h2_create(const h2_desc* d, h2_handle* out);
+
+/*
+ * y = A^H x for nv right-hand sides (Sec. 4, all phases), asynchronously on
+ * `stream` (a cudaStream_t; NULL = legacy default stream).
+ *   x   device FP64, n x nv, column-major, leading dimension ldx >= n
+ *   y   device FP64, n x nv, column-major, leading dimension ldy >= n;
+ *       overwritten (never accumulated into); must not overlap x
+ * The handle's workspace is reused: calls on one handle must be ordered (same
+ * stream or externally synchronized). No host synchronization happens inside.
+ * Errors: H2_ERR_INVALID (NULL, nv < 1, ld < n), H2_ERR_CUDA (launch failed).
+ */
+h2_status h2_matvec(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream);
+
+/*
+ * Same product with HOST buffers: x is copied host->device, the product runs,
+ * y is copied device->host, and the call returns after `stream` has drained.
+ * Pinned host memory gives full-speed copies; pageable memory works too.
+ * Device staging buffers are allocated on the first call and grown when a
+ * larger n x nv is requested.
+ */
+h2_status h2_matvec_host(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream);
+
+/*
+ * Sizes of the stored representation.
+ *   info[0]  paper_bytes: bytes of U, V, E, F, S and D as streamed by one
+ *            single-vector product (V and F counted even when aliased to U and
+ *            E, since each is read in its own phase; Sec. 4.6 metric)
+ *   info[1]  total device bytes held by the handle (matrix + workspace)
+ *   info[2]  number of coupling blocks     info[3] number of dense blocks
+ *   info[4]  q                             info[5] k
+ *   info[6]  largest leaf size             info[7] n
+ */
+h2_status h2_info(h2_handle h, int64_t info[8]);
+
+/* Free all device memory of the handle (synchronizes the device first). NULL is a no-op. */
+h2_status h2_destroy(h2_handle h);
+
+/* Message of the calling thread's last failed call ("" if none). Valid until the next call. */
+const char* h2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H2GB300_H */

@@ -1,0 +1,160 @@
+"""GB300 H^2 matrix-vector product: thin ctypes binding of libh2gb300.so.
+
+The binding only marshals arguments: every step of the product runs in the
+library's CUDA kernels (include/h2.h documents the ABI). PyTorch supplies
+device memory and streams. There is no CPU fallback: if the shared library is
+missing, importing ``paper_1902_01829_gb300`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libh2gb300.so")
+
+H2_OK, H2_ERR_INVALID, H2_ERR_OOM, H2_ERR_CUDA, H2_ERR_UNSUPPORTED, H2_ERR_TIMEOUT = range(6)
+STORAGE = {"fp64": 0}
+STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUDA", 4: "H2_ERR_UNSUPPORTED",
+                5: "H2_ERR_TIMEOUT"}
+
+# every symbol include/h2.h declares
+EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_info", "h2_destroy", "h2_last_error"]
+
+
+class H2Error(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class h2_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("depth", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("symmetric", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("leaf_offset", ctypes.c_void_p), ("U", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("E", ctypes.c_void_p), ("F", ctypes.c_void_p),
+                ("S_rowptr", ctypes.c_void_p), ("S_colidx", ctypes.c_void_p), ("S_val", ctypes.c_void_p),
+                ("D_rowptr", ctypes.c_void_p), ("D_colidx", ctypes.c_void_p), ("D_val", ctypes.c_void_p),
+                ("check_cover", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.h2_create.argtypes = [ctypes.POINTER(h2_desc), ctypes.POINTER(vp)]
+    lib.h2_matvec.argtypes = [vp, i32, vp, i64, vp, i64, vp]
+    lib.h2_matvec_host.argtypes = [vp, i32, vp, i64, vp, i64, vp]
+    lib.h2_info.argtypes = [vp, vp]
+    lib.h2_destroy.argtypes = [vp]
+    lib.h2_last_error.restype = ctypes.c_char_p
+    for name in ("h2_create", "h2_matvec", "h2_matvec_host", "h2_info", "h2_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int):
+    if status != H2_OK:
+        raise H2Error(status, _lib.h2_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())  # torch tensor
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class H2Matrix:
+    """An H^2 matrix resident on the current CUDA device (h2_create / h2_destroy)."""
+
+    def __init__(self, *, n, depth, rank, leaf_offset, U, E, S_rowptr, S_colidx, S_val, D_rowptr, D_colidx, D_val,
+                 V=None, F=None, storage="fp64", check_cover=False):
+        sym = V is None and F is None
+        keep = dict(leaf_offset=np.ascontiguousarray(leaf_offset, dtype=np.int64),
+                    U=np.ascontiguousarray(U, dtype=np.float64), E=np.ascontiguousarray(E, dtype=np.float64),
+                    V=None if sym else np.ascontiguousarray(V, dtype=np.float64),
+                    F=None if sym else np.ascontiguousarray(F, dtype=np.float64),
+                    S_rowptr=np.ascontiguousarray(S_rowptr, dtype=np.int32),
+                    S_colidx=np.ascontiguousarray(S_colidx, dtype=np.int32),
+                    S_val=np.ascontiguousarray(S_val, dtype=np.float64),
+                    D_rowptr=np.ascontiguousarray(D_rowptr, dtype=np.int32),
+                    D_colidx=np.ascontiguousarray(D_colidx, dtype=np.int32),
+                    D_val=np.ascontiguousarray(D_val, dtype=np.float64))
+        d = h2_desc(n=int(n), depth=int(depth), rank=int(rank), symmetric=1 if sym else 0, storage=STORAGE[storage],
+                    check_cover=1 if check_cover else 0,
+                    **{key: _ptr(val) for key, val in keep.items()})
+        self._h = ctypes.c_void_p()
+        _check(_lib.h2_create(ctypes.byref(d), ctypes.byref(self._h)))
+        self.n = int(n)
+
+    @classmethod
+    def from_generator(cls, A, storage="fp64", check_cover=False) -> "H2Matrix":
+        """From an object with the generator's arrays (h2gen.H2Matrix)."""
+        return cls(n=A.n, depth=A.q, rank=A.k, leaf_offset=A.leaf_offset, U=A.U, E=A.E, S_rowptr=A.S_rowptr,
+                   S_colidx=A.S_colidx, S_val=A.S_val, D_rowptr=A.D_rowptr, D_colidx=A.D_colidx, D_val=A.D_val,
+                   storage=storage, check_cover=check_cover)
+
+    def matvec(self, x, y=None, stream=None):
+        """y = A^H x on the device. x, y: torch float64 CUDA tensors, shape (n,) or (n, nv) column-major."""
+        import torch
+        assert x.is_cuda and x.dtype == torch.float64
+        vec = x.dim() == 1
+        X = x.unsqueeze(1) if vec else x
+        if X.stride(0) != 1:
+            X = X.t().contiguous().t()
+        nv = X.shape[1]
+        if y is None:
+            Y = torch.empty((nv, self.n), dtype=torch.float64, device=x.device).t()
+        else:
+            Y = y.unsqueeze(1) if y.dim() == 1 else y
+            assert Y.stride(0) == 1 and Y.dtype == torch.float64
+        ldx = X.stride(1) if nv > 1 else self.n
+        ldy = Y.stride(1) if nv > 1 else self.n
+        _check(_lib.h2_matvec(self._h, nv, _ptr(X), ldx, _ptr(Y), ldy, _stream_ptr(stream)))
+        return Y[:, 0] if (vec and y is None) else (y if y is not None else Y)
+
+    def matvec_host(self, x: np.ndarray, y: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """y = A^H x with host (numpy) buffers; copies are part of the call."""
+        vec = x.ndim == 1
+        X = np.asfortranarray(x[:, None] if vec else x, dtype=np.float64)
+        nv = X.shape[1]
+        Y = np.empty((self.n, nv), order="F") if y is None else y
+        _check(_lib.h2_matvec_host(self._h, nv, _ptr(X), self.n, _ptr(Y), self.n, _stream_ptr(stream)))
+        return Y[:, 0] if (vec and y is None) else Y
+
+    def info(self) -> dict:
+        a = np.zeros(8, dtype=np.int64)
+        _check(_lib.h2_info(self._h, _ptr(a)))
+        keys = ["paper_bytes", "device_bytes", "nS", "nD", "q", "k", "m_max", "n"]
+        return {key: int(v) for key, v in zip(keys, a)}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.h2_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

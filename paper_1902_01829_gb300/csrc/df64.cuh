@@ -1,0 +1,81 @@
+// Double-float arithmetic on the FP32 pipes for the FP64 plain form.
+//
+// GB300 issues FP64 FMAs at about 2 per clock per SM, too slow for one FMA per
+// streamed 8-byte matrix entry at HBM speed, while its FP32 pipes issue 128.
+// An FP64 entry is therefore split (with integer ops) into an unevaluated sum
+// hi + lo of two floats, and products are accumulated with error-free
+// transformations (Knuth's TwoSum, Dekker-style exact product via FMA):
+//
+//   a*x = ah*xh + (ah*xl + al*xh) + O(2^-46 |a x|),  ah*xh = p + e exactly.
+//
+// Accumulators are pairs (s, c): s carries the TwoSum running sum of the
+// leading products, c collects the rounding errors and cross terms.
+// Intrinsics (__fmul_rn, __fadd_rn) keep the compiler from contracting or
+// reassociating the error-free steps.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace h2 {
+
+// |a| >= 2^-103 keeps both halves normal floats; smaller magnitudes (and zero)
+// become 0. h2_create rejects |a| >= 2^126, so the exponent never overflows.
+__device__ __forceinline__ void split_f64(double a, float& h, float& l) {
+  const uint32_t hi = (uint32_t)__double2hiint(a);
+  const uint32_t lo = (uint32_t)__double2loint(a);
+  const uint32_t t = hi - 0x38000000u;                       // exponent bias 1023 -> 127
+  const uint32_t u = __funnelshift_l(lo, t, 3);              // 20 + 3 mantissa bits
+  const uint32_t hb = (u & 0x7FFFFFFFu) | (hi & 0x80000000u);
+  const uint32_t fb = (hb - (23u << 23)) & 0xFF800000u;      // sign, exponent of hi - 23
+  const uint32_t r = (lo >> 6) & 0x7FFFFFu;                  // next 23 mantissa bits
+  const float hv = __uint_as_float(hb);
+  const float lv = __fsub_rn(__uint_as_float(fb | r), __uint_as_float(fb));
+  const bool ok = (hi & 0x7FFFFFFFu) >= 0x39800000u;         // biased exponent >= 920
+  h = ok ? hv : 0.0f;
+  l = ok ? lv : 0.0f;
+}
+
+// x (any finite double in float range) -> hi + lo, both rounded to nearest
+__device__ __forceinline__ float2 f64_to_df(double x) {
+  const float h = __double2float_rn(x);
+  const float l = __double2float_rn(x - (double)h);
+  return make_float2(h, l);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, c) += (ah + al) * (xh + xl)
+__device__ __forceinline__ void df_fma(float& s, float& c, float ah, float al, float xh, float xl) {
+  const float p = __fmul_rn(ah, xh);
+  const float e = __fmaf_rn(ah, xh, -p);
+  c = __fmaf_rn(ah, xl, c);
+  c = __fmaf_rn(al, xh, c);
+  float t, err;
+  two_sum(s, p, t, err);
+  s = t;
+  c = __fadd_rn(c, e);
+  c = __fadd_rn(c, err);
+}
+
+// (s1, c1) += (s2, c2)
+__device__ __forceinline__ void df_add(float& s1, float& c1, float s2, float c2) {
+  float t, err;
+  two_sum(s1, s2, t, err);
+  s1 = t;
+  c1 = __fadd_rn(__fadd_rn(c1, c2), err);
+}
+
+// renormalize (s, c) into hi + lo with |lo| <= ulp(hi)/2
+__device__ __forceinline__ float2 df_norm(float s, float c) {
+  float h, l;
+  two_sum(s, c, h, l);
+  return make_float2(h, l);
+}
+
+__device__ __forceinline__ double df_to_f64(float s, float c) { return (double)s + (double)c; }
+
+}  // namespace h2

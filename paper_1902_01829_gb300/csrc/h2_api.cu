@@ -1,0 +1,407 @@
+// C ABI of the H^2 matrix-vector product library: validation, device layout,
+// launch sequence. See include/h2.h for the contract of each entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "h2.h"
+#include "hmv_fp64.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+h2_status fail(h2_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(call)                                                                                 \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) {                                                                           \
+      if (e_ == cudaErrorMemoryAllocation) return fail(H2_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_)); \
+      return fail(H2_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                               \
+    }                                                                                                  \
+  } while (0)
+
+constexpr int kMaxLeaf = 64;
+constexpr int kMaxRank = 64;
+constexpr int kPassVectors = 16;  // right-hand sides per pass over the matrix
+
+}  // namespace
+
+struct h2_matrix_s {
+  int64_t n = 0, leaves = 0, n_nodes = 0, leaf0 = 0, nS = 0, nD = 0, nDval = 0;
+  int q = 0, k = 0, m_max = 0, lr = 32;
+  int64_t paper_bytes = 0, device_bytes = 0;
+  std::vector<void*> allocs;
+  int64_t* leaf_off = nullptr;
+  double* U = nullptr;   // leaf i: size_i x k col-major (expansion)
+  double* Vt = nullptr;  // leaf j: k x size_j col-major (= V_j^T, projection)
+  double* E = nullptr;   // node h >= 1: k x k col-major (downsweep)
+  double* Ft = nullptr;  // node h >= 1: F_h^T, k x k col-major (upsweep)
+  int32_t* Srow = nullptr;
+  int32_t* Scol = nullptr;
+  double* S = nullptr;
+  int32_t* Drow = nullptr;
+  int32_t* Dcol = nullptr;
+  int64_t* Doff = nullptr;
+  double* D = nullptr;
+  float2* x2 = nullptr;    // n x kPassVectors
+  float2* xhat = nullptr;  // n_nodes x kPassVectors x k
+  float2* yhat = nullptr;
+  // host-buffer staging (h2_matvec_host)
+  double* hx = nullptr;
+  double* hy = nullptr;
+  int64_t host_cap = 0;
+};
+
+namespace {
+
+template <class T>
+h2_status dalloc(h2_matrix_s* h, T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA, "cudaMalloc of %lld bytes failed: %s",
+                (long long)(count * sizeof(T)), cudaGetErrorString(e));
+  }
+  h->allocs.push_back(q);
+  h->device_bytes += count * (int64_t)sizeof(T);
+  *p = (T*)q;
+  return H2_OK;
+}
+
+template <class T>
+h2_status upload(h2_matrix_s* h, T** p, const T* src, int64_t count) {
+  h2_status st = dalloc(h, p, count);
+  if (st != H2_OK) return st;
+  if (count > 0) CUDA_TRY(cudaMemcpy(*p, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice));
+  return H2_OK;
+}
+
+void free_all(h2_matrix_s* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->hx) cudaFree(h->hx);
+  if (h->hy) cudaFree(h->hy);
+  h->hx = h->hy = nullptr;
+}
+
+int level_of(int64_t node) {
+  int l = 0;
+  while (((int64_t)2 << l) - 1 <= node) l++;
+  return l;
+}
+
+// values must be finite with |v| < 2^126 (the double-float split keeps the exponent in float range)
+bool values_ok(const double* v, int64_t count, int64_t* bad) {
+  const double lim = std::ldexp(1.0, 126);
+  for (int64_t i = 0; i < count; i++)
+    if (!(std::fabs(v[i]) < lim)) {
+      *bad = i;
+      return false;
+    }
+  return true;
+}
+
+// every (row leaf, column leaf) pair covered exactly once by a dense block or
+// by a coupling block of an ancestor pair
+h2_status check_cover(const h2_desc* d, int64_t leaves) {
+  const int q = d->depth;
+  std::vector<std::pair<int64_t, int64_t>> iv;
+  for (int64_t i = 0; i < leaves; i++) {
+    iv.clear();
+    for (int32_t b = d->D_rowptr[i]; b < d->D_rowptr[i + 1]; b++) iv.push_back({d->D_colidx[b], d->D_colidx[b] + 1});
+    int64_t node = leaves - 1 + i;
+    for (int l = q;; l--) {
+      for (int32_t b = d->S_rowptr[node]; b < d->S_rowptr[node + 1]; b++) {
+        const int64_t col = d->S_colidx[b];
+        const int64_t first = ((int64_t)1 << l) - 1, span = (int64_t)1 << (q - l);
+        const int64_t lo = (col - first) * span;
+        iv.push_back({lo, lo + span});
+      }
+      if (node == 0) break;
+      node = (node - 1) / 2;
+    }
+    std::sort(iv.begin(), iv.end());
+    int64_t at = 0;
+    for (auto& r : iv) {
+      if (r.first != at) return fail(H2_ERR_INVALID, "block cover: leaf row %lld, columns from leaf %lld %s", (long long)i,
+                                     (long long)std::min(at, r.first), r.first > at ? "are not covered" : "are covered twice");
+      at = r.second;
+    }
+    if (at != leaves) return fail(H2_ERR_INVALID, "block cover: leaf row %lld, columns from leaf %lld are not covered", (long long)i, (long long)at);
+  }
+  return H2_OK;
+}
+
+h2_status validate(const h2_desc* d, int64_t* nS, int64_t* nD, int64_t* nDval, int* m_max) {
+  if (!d) return fail(H2_ERR_INVALID, "desc is NULL");
+  if (d->n < 1) return fail(H2_ERR_INVALID, "n = %lld < 1", (long long)d->n);
+  if (d->depth < 0 || d->depth > 24) return fail(H2_ERR_INVALID, "depth = %d outside 0..24", d->depth);
+  if (d->rank < 1) return fail(H2_ERR_INVALID, "rank = %d < 1", d->rank);
+  if (d->rank > kMaxRank) return fail(H2_ERR_UNSUPPORTED, "rank = %d > %d", d->rank, kMaxRank);
+  if (d->storage != H2_FP64) return fail(H2_ERR_UNSUPPORTED, "storage %d not supported", d->storage);
+  if (!d->leaf_offset || !d->U || !d->E || !d->S_rowptr || !d->D_rowptr)
+    return fail(H2_ERR_INVALID, "NULL array in desc");
+  if (!d->symmetric && (!d->V || !d->F)) return fail(H2_ERR_INVALID, "V/F are NULL but symmetric = 0");
+  const int q = d->depth, k = d->rank;
+  const int64_t leaves = (int64_t)1 << q, n_nodes = ((int64_t)2 << q) - 1;
+  if (d->leaf_offset[0] != 0 || d->leaf_offset[leaves] != d->n)
+    return fail(H2_ERR_INVALID, "leaf_offset must run from 0 to n");
+  int mm = 0;
+  for (int64_t i = 0; i < leaves; i++) {
+    const int64_t s = d->leaf_offset[i + 1] - d->leaf_offset[i];
+    if (s < 1) return fail(H2_ERR_INVALID, "leaf %lld has size %lld < 1", (long long)i, (long long)s);
+    if (s > kMaxLeaf) return fail(H2_ERR_UNSUPPORTED, "leaf %lld has size %lld > %d", (long long)i, (long long)s, kMaxLeaf);
+    mm = std::max(mm, (int)s);
+  }
+  *m_max = mm;
+  if (d->S_rowptr[0] != 0) return fail(H2_ERR_INVALID, "S_rowptr[0] != 0");
+  for (int64_t r = 0; r < n_nodes; r++)
+    if (d->S_rowptr[r + 1] < d->S_rowptr[r]) return fail(H2_ERR_INVALID, "S_rowptr decreases at row %lld", (long long)r);
+  *nS = d->S_rowptr[n_nodes];
+  if (*nS > 0 && (!d->S_colidx || !d->S_val)) return fail(H2_ERR_INVALID, "S_colidx/S_val NULL with %lld blocks", (long long)*nS);
+  for (int64_t r = 0; r < n_nodes; r++) {
+    const int l = level_of(r);
+    const int64_t first = ((int64_t)1 << l) - 1, last = ((int64_t)2 << l) - 2;
+    for (int32_t b = d->S_rowptr[r]; b < d->S_rowptr[r + 1]; b++)
+      if (d->S_colidx[b] < first || d->S_colidx[b] > last)
+        return fail(H2_ERR_INVALID, "S_colidx[%d] = %d is not on the level of row %lld", b, d->S_colidx[b], (long long)r);
+  }
+  if (d->D_rowptr[0] != 0) return fail(H2_ERR_INVALID, "D_rowptr[0] != 0");
+  for (int64_t r = 0; r < leaves; r++)
+    if (d->D_rowptr[r + 1] < d->D_rowptr[r]) return fail(H2_ERR_INVALID, "D_rowptr decreases at row %lld", (long long)r);
+  *nD = d->D_rowptr[leaves];
+  if (*nD > 0 && (!d->D_colidx || !d->D_val)) return fail(H2_ERR_INVALID, "D_colidx/D_val NULL with %lld blocks", (long long)*nD);
+  int64_t dv = 0;
+  for (int64_t r = 0; r < leaves; r++)
+    for (int32_t b = d->D_rowptr[r]; b < d->D_rowptr[r + 1]; b++) {
+      const int32_t j = d->D_colidx[b];
+      if (j < 0 || j >= leaves) return fail(H2_ERR_INVALID, "D_colidx[%d] = %d out of range", b, j);
+      dv += (d->leaf_offset[r + 1] - d->leaf_offset[r]) * (d->leaf_offset[j + 1] - d->leaf_offset[j]);
+    }
+  *nDval = dv;
+  int64_t bad = 0;
+  if (!values_ok(d->U, d->n * k, &bad)) return fail(H2_ERR_INVALID, "U[%lld] is not finite or too large", (long long)bad);
+  if (!values_ok(d->E, (n_nodes - 1) * k * k, &bad)) return fail(H2_ERR_INVALID, "E[%lld] is not finite or too large", (long long)bad);
+  if (!d->symmetric) {
+    if (!values_ok(d->V, d->n * k, &bad)) return fail(H2_ERR_INVALID, "V[%lld] is not finite or too large", (long long)bad);
+    if (!values_ok(d->F, (n_nodes - 1) * k * k, &bad)) return fail(H2_ERR_INVALID, "F[%lld] is not finite or too large", (long long)bad);
+  }
+  if (*nS && !values_ok(d->S_val, *nS * k * k, &bad)) return fail(H2_ERR_INVALID, "S_val[%lld] is not finite or too large", (long long)bad);
+  if (*nD && !values_ok(d->D_val, dv, &bad)) return fail(H2_ERR_INVALID, "D_val[%lld] is not finite or too large", (long long)bad);
+  if (d->check_cover) return check_cover(d, leaves);
+  return H2_OK;
+}
+
+int pow2ceil(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// ------------------------------------------------------------------ launch sequence
+template <int RPL_K, int RPL_M, int NVB>
+h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
+  using namespace h2;
+  const int k = h->k, LR = h->lr;
+  const int64_t ld2 = h->n;
+  const unsigned wb = (unsigned)kWarps * 32;
+  auto grid = [](int64_t items) { return (unsigned)((items + kWarps - 1) / kWarps); };
+  k_project<RPL_K, NVB><<<grid(h->leaves), wb, 0, st>>>(h->Vt, h->leaf_off, k, LR, h->leaves, h->leaf0, x, ldx, nv, h->x2, ld2,
+                                                         h->xhat);
+  for (int l = h->q; l >= 1; l--) {
+    const int64_t pfirst = ((int64_t)1 << (l - 1)) - 1, pcount = (int64_t)1 << (l - 1);
+    k_upsweep<RPL_K, NVB><<<grid(pcount), wb, 0, st>>>(h->Ft, k, LR, pfirst, pcount, nv, h->xhat);
+  }
+  k_coupling<RPL_K, NVB><<<grid(h->n_nodes), wb, 0, st>>>(h->S, h->Srow, h->Scol, k, LR, h->n_nodes, nv, h->xhat, h->yhat);
+  for (int l = 1; l <= h->q; l++) {
+    const int64_t cfirst = ((int64_t)1 << l) - 1, ccount = (int64_t)1 << l;
+    k_downsweep<RPL_K, NVB><<<grid(ccount), wb, 0, st>>>(h->E, k, LR, cfirst, ccount, nv, h->yhat);
+  }
+  k_dense_expand<RPL_M, NVB><<<(unsigned)h->leaves, wb, 0, st>>>(h->D, h->Doff, h->Drow, h->Dcol, h->leaf_off, h->U, k, h->leaf0,
+                                                                   h->x2, ld2, h->yhat, nv, y, ldy);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(H2_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return H2_OK;
+}
+
+template <int RPL_K, int RPL_M>
+h2_status run_pass_nv(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
+  if (nv <= 1) return run_pass<RPL_K, RPL_M, 1>(h, nv, x, ldx, y, ldy, st);
+  if (nv <= 2) return run_pass<RPL_K, RPL_M, 2>(h, nv, x, ldx, y, ldy, st);
+  if (nv <= 4) return run_pass<RPL_K, RPL_M, 4>(h, nv, x, ldx, y, ldy, st);
+  if (nv <= 8) return run_pass<RPL_K, RPL_M, 8>(h, nv, x, ldx, y, ldy, st);
+  return run_pass<RPL_K, RPL_M, 16>(h, nv, x, ldx, y, ldy, st);
+}
+
+h2_status matvec_device(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
+  for (int v0 = 0; v0 < nv; v0 += kPassVectors) {
+    const int nvp = std::min(kPassVectors, nv - v0);
+    const double* xp = x + (int64_t)v0 * ldx;
+    double* yp = y + (int64_t)v0 * ldy;
+    h2_status s;
+    const bool kk2 = h->k > 32, mm2 = h->m_max > 32;
+    if (kk2 && mm2) s = run_pass_nv<2, 2>(h, nvp, xp, ldx, yp, ldy, st);
+    else if (kk2) s = run_pass_nv<2, 1>(h, nvp, xp, ldx, yp, ldy, st);
+    else if (mm2) s = run_pass_nv<1, 2>(h, nvp, xp, ldx, yp, ldy, st);
+    else s = run_pass_nv<1, 1>(h, nvp, xp, ldx, yp, ldy, st);
+    if (s != H2_OK) return s;
+  }
+  return H2_OK;
+}
+
+// transpose every k x k block (or size x k leaf block) into a host buffer
+void transpose_blocks(const double* src, double* dst, int64_t rows, int64_t cols) {
+  for (int64_t c = 0; c < cols; c++)
+    for (int64_t r = 0; r < rows; r++) dst[c + cols * r] = src[r + rows * c];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* h2_last_error(void) { return g_err.c_str(); }
+
+h2_status h2_create(const h2_desc* d, h2_handle* out) {
+  g_err.clear();
+  if (!out) return fail(H2_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int64_t nS = 0, nD = 0, nDval = 0;
+  int m_max = 0;
+  h2_status st = validate(d, &nS, &nD, &nDval, &m_max);
+  if (st != H2_OK) return st;
+  h2_matrix_s* h = new (std::nothrow) h2_matrix_s();
+  if (!h) return fail(H2_ERR_OOM, "host allocation failed");
+  h->n = d->n;
+  h->q = d->depth;
+  h->k = d->rank;
+  h->leaves = (int64_t)1 << h->q;
+  h->n_nodes = ((int64_t)2 << h->q) - 1;
+  h->leaf0 = h->leaves - 1;
+  h->nS = nS;
+  h->nD = nD;
+  h->nDval = nDval;
+  h->m_max = m_max;
+  h->lr = h->k > 32 ? 32 : pow2ceil(h->k);
+  const int k = h->k;
+  const int64_t kk = (int64_t)k * k;
+  const double* V = d->symmetric ? d->U : d->V;
+  const double* F = d->symmetric ? d->E : d->F;
+  std::vector<int64_t> doff((size_t)nD + 1, 0);
+  for (int64_t r = 0, b = 0; r < h->leaves; r++)
+    for (; b < d->D_rowptr[r + 1]; b++) {
+      const int32_t j = d->D_colidx[b];
+      doff[b + 1] = doff[b] + (d->leaf_offset[r + 1] - d->leaf_offset[r]) * (d->leaf_offset[j + 1] - d->leaf_offset[j]);
+    }
+  std::vector<double> tmp;
+  try {
+    tmp.resize((size_t)std::max<int64_t>(h->n * k, (h->n_nodes - 1) * kk));
+  } catch (...) {
+    delete h;
+    return fail(H2_ERR_OOM, "host allocation failed");
+  }
+#define TRY(x)                 \
+  do {                         \
+    st = (x);                  \
+    if (st != H2_OK) {         \
+      free_all(h);             \
+      delete h;                \
+      return st;               \
+    }                          \
+  } while (0)
+  TRY(upload(h, &h->leaf_off, d->leaf_offset, h->leaves + 1));
+  TRY(upload(h, &h->U, d->U, h->n * k));
+  for (int64_t j = 0; j < h->leaves; j++) {
+    const int64_t off = d->leaf_offset[j], s = d->leaf_offset[j + 1] - off;
+    transpose_blocks(V + off * k, tmp.data() + off * k, s, k);
+  }
+  TRY(upload(h, &h->Vt, (const double*)tmp.data(), h->n * k));
+  TRY(upload(h, &h->E, d->E, (h->n_nodes - 1) * kk));
+  for (int64_t c = 0; c < h->n_nodes - 1; c++) transpose_blocks(F + c * kk, tmp.data() + c * kk, k, k);
+  TRY(upload(h, &h->Ft, (const double*)tmp.data(), (h->n_nodes - 1) * kk));
+  TRY(upload(h, &h->Srow, d->S_rowptr, h->n_nodes + 1));
+  TRY(upload(h, &h->Scol, d->S_colidx, nS));
+  TRY(upload(h, &h->S, d->S_val, nS * kk));
+  TRY(upload(h, &h->Drow, d->D_rowptr, h->leaves + 1));
+  TRY(upload(h, &h->Dcol, d->D_colidx, nD));
+  TRY(upload(h, &h->Doff, (const int64_t*)doff.data(), nD + 1));
+  TRY(upload(h, &h->D, d->D_val, nDval));
+  TRY(dalloc(h, &h->x2, h->n * kPassVectors));
+  TRY(dalloc(h, &h->xhat, h->n_nodes * kPassVectors * k));
+  TRY(dalloc(h, &h->yhat, h->n_nodes * kPassVectors * k));
+#undef TRY
+  h->paper_bytes = 8 * (2 * h->n * k + 2 * (h->n_nodes - 1) * kk + nS * kk + nDval);
+  *out = h;
+  return H2_OK;
+}
+
+h2_status h2_matvec(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream) {
+  if (!h || !x || !y) return fail(H2_ERR_INVALID, "NULL handle or vector");
+  if (nv < 1) return fail(H2_ERR_INVALID, "nv = %d < 1", nv);
+  if (ldx < h->n || ldy < h->n) return fail(H2_ERR_INVALID, "leading dimension below n");
+  return matvec_device(h, nv, x, ldx, y, ldy, (cudaStream_t)stream);
+}
+
+h2_status h2_matvec_host(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream) {
+  if (!h || !x || !y) return fail(H2_ERR_INVALID, "NULL handle or vector");
+  if (nv < 1) return fail(H2_ERR_INVALID, "nv = %d < 1", nv);
+  if (ldx < h->n || ldy < h->n) return fail(H2_ERR_INVALID, "leading dimension below n");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t need = h->n * nv;
+  if (need > h->host_cap) {
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (h->hx) cudaFree(h->hx);
+    if (h->hy) cudaFree(h->hy);
+    h->hx = h->hy = nullptr;
+    h->host_cap = 0;
+    CUDA_TRY(cudaMalloc(&h->hx, (size_t)need * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&h->hy, (size_t)need * sizeof(double)));
+    h->host_cap = need;
+  }
+  CUDA_TRY(cudaMemcpy2DAsync(h->hx, (size_t)h->n * 8, x, (size_t)ldx * 8, (size_t)h->n * 8, (size_t)nv, cudaMemcpyHostToDevice, st));
+  h2_status s = matvec_device(h, nv, h->hx, h->n, h->hy, h->n, st);
+  if (s != H2_OK) return s;
+  CUDA_TRY(cudaMemcpy2DAsync(y, (size_t)ldy * 8, h->hy, (size_t)h->n * 8, (size_t)h->n * 8, (size_t)nv, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return H2_OK;
+}
+
+h2_status h2_info(h2_handle h, int64_t info[8]) {
+  if (!h || !info) return fail(H2_ERR_INVALID, "NULL handle or info");
+  info[0] = h->paper_bytes;
+  info[1] = h->device_bytes + 2 * h->host_cap * 8;
+  info[2] = h->nS;
+  info[3] = h->nD;
+  info[4] = h->q;
+  info[5] = h->k;
+  info[6] = h->m_max;
+  info[7] = h->n;
+  return H2_OK;
+}
+
+h2_status h2_destroy(h2_handle h) {
+  if (!h) return H2_OK;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return H2_OK;
+}
+
+}  // extern "C"

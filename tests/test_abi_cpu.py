@@ -1,0 +1,126 @@
+"""The C ABI without a GPU: the library loads, exports every declared symbol, and
+h2_create rejects malformed input before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import h2gen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def h2():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1902_01829_gb300 as mod
+
+    return mod
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "h2.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(h2_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(h2):
+    names = _declared_symbols()
+    assert "h2_create" in names and "h2_matvec" in names
+    lib = ctypes.CDLL(h2.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(h2.EXPORTS) == names
+
+
+@pytest.fixture(scope="module")
+def small():
+    return h2gen.generate(dim=2, n=1024, m=32, p=3, eta=0.9, kernel="exp", ell=0.1, seed=3)
+
+
+def _kw(A):
+    return dict(n=A.n, depth=A.q, rank=A.k, leaf_offset=A.leaf_offset.copy(), U=A.U, E=A.E,
+                S_rowptr=A.S_rowptr.copy(), S_colidx=A.S_colidx.copy(), S_val=A.S_val,
+                D_rowptr=A.D_rowptr.copy(), D_colidx=A.D_colidx.copy(), D_val=A.D_val.copy())
+
+
+def _expect(h2, status, **kw):
+    with pytest.raises(h2.H2Error) as ei:
+        h2.H2Matrix(**kw)
+    assert ei.value.status == status, str(ei.value)
+    return str(ei.value)
+
+
+def test_rejects_bad_leaf_offsets(h2, small):
+    kw = _kw(small)
+    kw["leaf_offset"][-1] += 1
+    _expect(h2, h2.H2_ERR_INVALID, **kw)
+    kw = _kw(small)
+    kw["leaf_offset"][1] = kw["leaf_offset"][2]  # empty leaf
+    _expect(h2, h2.H2_ERR_INVALID, **kw)
+
+
+def test_rejects_coupling_column_off_level(h2, small):
+    kw = _kw(small)
+    kw["S_colidx"][0] = 0  # root is never on the row's level
+    msg = _expect(h2, h2.H2_ERR_INVALID, **kw)
+    assert "level" in msg
+
+
+def test_rejects_decreasing_rowptr(h2, small):
+    kw = _kw(small)
+    r = int(np.flatnonzero(np.diff(kw["D_rowptr"]) > 1)[0])
+    kw["D_rowptr"][r + 1] = kw["D_rowptr"][r] - 1
+    _expect(h2, h2.H2_ERR_INVALID, **kw)
+
+
+def test_rejects_dense_column_out_of_range(h2, small):
+    kw = _kw(small)
+    kw["D_colidx"][5] = small.leaves
+    _expect(h2, h2.H2_ERR_INVALID, **kw)
+
+
+def test_rejects_non_finite_values(h2, small):
+    kw = _kw(small)
+    kw["D_val"][17] = np.nan
+    _expect(h2, h2.H2_ERR_INVALID, **kw)
+    kw = _kw(small)
+    kw["D_val"][3] = 2.0 ** 127
+    _expect(h2, h2.H2_ERR_INVALID, **kw)
+
+
+def test_cover_check_finds_missing_and_doubled_blocks(h2, small):
+    kw = _kw(small)
+    # drop the last dense block of leaf row 0: its column leaf is covered by nothing
+    rp, ci = kw["D_rowptr"], kw["D_colidx"]
+    b = int(rp[1]) - 1
+    keep = np.ones(ci.size, bool)
+    keep[b] = False
+    sizes = np.diff(small.leaf_offset)
+    blk = sizes[0] * sizes[ci[b]]
+    kw["D_colidx"] = ci[keep]
+    kw["D_rowptr"] = np.concatenate([[0], rp[1:] - 1]).astype(np.int32)
+    off = int(small.D_valoff[b])
+    kw["D_val"] = np.concatenate([kw["D_val"][:off], kw["D_val"][off + blk:]])
+    msg = _expect(h2, h2.H2_ERR_INVALID, check_cover=True, **kw)
+    assert "not covered" in msg
+
+
+def test_rejects_unsupported_sizes(h2):
+    A = h2gen.generate(dim=2, n=4096, m=128, p=2, eta=0.9, seed=4, values=True)
+    assert A.leaf_size(0) > 64
+    _expect(h2, h2.H2_ERR_UNSUPPORTED, **_kw(A))
+    B = h2gen.generate(dim=3, n=512, m=64, p=5, eta=0.9, seed=4)
+    assert B.k == 125
+    _expect(h2, h2.H2_ERR_UNSUPPORTED, **_kw(B))
+
+
+def test_rejects_missing_column_basis(h2, small):
+    kw = _kw(small)
+    with pytest.raises(h2.H2Error) as ei:
+        h2.H2Matrix(V=small.U, F=None, **kw)
+    assert ei.value.status == h2.H2_ERR_INVALID

@@ -1,0 +1,164 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerance: relative l2 error <= 1e-12 per column (the FP64 plain form's bar).
+The double-float arithmetic keeps about 46 bits per matrix entry, so errors
+are expected near 1e-14.
+"""
+import numpy as np
+import pytest
+
+import h2gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def h2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1902_01829_gb300 as mod
+
+    return mod
+
+
+def to_dev(x):
+    x = np.asfortranarray(x)
+    if x.ndim == 1:
+        return torch.from_numpy(x.copy()).cuda()
+    return torch.from_numpy(np.ascontiguousarray(x.T)).cuda().t()
+
+
+def gpu_matvec(h2, A, x, **kw):
+    M = h2.H2Matrix.from_generator(A, check_cover=True, **kw)
+    y = M.matvec(to_dev(x))
+    torch.cuda.synchronize()
+    out = y.cpu().numpy()
+    M.close()
+    return out
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return h2gen.generate(**h2gen.CONFIGS["2d_n4096"])
+
+
+@pytest.mark.parametrize("nv", [1, 2, 3, 16, 20, 33])
+def test_c1_parity(h2, c1, nv):
+    """2D n = 4096, m = 32, k = 16: several right-hand-side counts (one and several passes)."""
+    x = h2gen.vectors(200 + nv, c1.n, nv)
+    err = oracle.rel_l2(gpu_matvec(h2, c1, x), oracle.matvec(c1, x))
+    assert err <= TOL, err
+
+
+def test_3d_ragged_leaves_k27(h2):
+    A = h2gen.generate(dim=3, n=6001, m=40, p=3, eta=0.8, kernel="matern32", ell=0.15, seed=7)
+    assert len(set(np.diff(A.leaf_offset).tolist())) > 1
+    x = h2gen.vectors(301, A.n, 3)
+    assert oracle.rel_l2(gpu_matvec(h2, A, x), oracle.matvec(A, x)) <= TOL
+
+
+def test_3d_k64_m64(h2):
+    A = h2gen.generate(dim=3, n=16384, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=8)
+    x = h2gen.vectors(302, A.n, 2)
+    assert oracle.rel_l2(gpu_matvec(h2, A, x), oracle.matvec(A, x)) <= TOL
+
+
+def test_2d_n65536_m64(h2):
+    """Many leaves (1024) and 10 levels: every kernel runs multi-CTA grids with ragged tails."""
+    A = h2gen.generate(dim=2, n=65536, m=64, p=4, eta=0.9, kernel="exp", ell=0.1, seed=9)
+    x = h2gen.vectors(303, A.n, 4)
+    assert oracle.rel_l2(gpu_matvec(h2, A, x), oracle.matvec(A, x)) <= TOL
+
+
+def test_nonsymmetric_bases(h2, c1):
+    """Distinct column basis tree (V != U, F != E): exercises the transposed V^T and F^T paths."""
+    rng = np.random.default_rng(5)
+    V = c1.U * (1 + 0.1 * rng.standard_normal(c1.U.size))
+    F = c1.E * (1 + 0.1 * rng.standard_normal(c1.E.size))
+    M = h2.H2Matrix(n=c1.n, depth=c1.q, rank=c1.k, leaf_offset=c1.leaf_offset, U=c1.U, V=V, E=c1.E, F=F,
+                    S_rowptr=c1.S_rowptr, S_colidx=c1.S_colidx, S_val=c1.S_val, D_rowptr=c1.D_rowptr,
+                    D_colidx=c1.D_colidx, D_val=c1.D_val)
+    x = h2gen.vectors(304, c1.n, 2)
+    y = M.matvec(to_dev(x)).cpu().numpy()
+    M.close()
+    assert oracle.rel_l2(y, oracle.matvec(c1, x, V=V, F=F)) <= TOL
+
+
+@pytest.mark.parametrize("n,m", [(1, 64), (37, 64), (64, 64), (65, 64)])
+def test_tiny_trees(h2, n, m):
+    """q = 0 (a single dense leaf) and q = 1 with n just above m."""
+    A = h2gen.generate(dim=2, n=n, m=m, p=4, eta=0.9, kernel="exp", ell=0.1, seed=10)
+    x = h2gen.vectors(305, A.n, 2)
+    assert oracle.rel_l2(gpu_matvec(h2, A, x), oracle.matvec(A, x)) <= TOL
+
+
+def test_eta_zero_dense_only(h2):
+    A = h2gen.generate(dim=2, n=2048, m=32, p=4, eta=0.0, kernel="exp", ell=0.1, seed=11)
+    assert A.nS == 0
+    x = h2gen.vectors(306, A.n, 1)
+    assert oracle.rel_l2(gpu_matvec(h2, A, x), A.dense_kernel_matrix() @ x) <= TOL
+
+
+def test_polynomial_kernel_closed_form(h2):
+    """Exact interpolation: the GPU product equals the dense kernel matrix product."""
+    A = h2gen.generate(dim=2, n=4096, m=32, p=4, eta=0.9, kernel="poly", seed=12)
+    x = h2gen.vectors(307, A.n, 1)
+    assert oracle.rel_l2(gpu_matvec(h2, A, x), A.dense_kernel_matrix() @ x) <= TOL
+
+
+def test_constant_kernel_closed_form(h2):
+    A = h2gen.generate(dim=2, n=4096, m=32, p=4, eta=0.9, kernel="const", seed=13)
+    x = h2gen.vectors(308, A.n, 1)
+    y = gpu_matvec(h2, A, x)[:, 0]
+    np.testing.assert_allclose(y, np.full(A.n, x.sum()), rtol=1e-12, atol=1e-12 * np.abs(x).sum())
+
+
+def test_uniform_vectors_and_strided_layout(h2, c1):
+    """x ~ U[0,1] (the paper's test vectors) with ldx > n and ldy > n."""
+    M = h2.H2Matrix.from_generator(c1)
+    x = h2gen.vectors(309, c1.n, 3, "uniform")
+    X = torch.zeros((3, c1.n + 7), dtype=torch.float64, device="cuda")
+    X[:, :c1.n] = torch.from_numpy(np.ascontiguousarray(x.T))
+    Y = torch.full((3, c1.n + 5), 7.0, dtype=torch.float64, device="cuda")
+    M.matvec(X.t()[:c1.n], Y.t()[:c1.n])
+    torch.cuda.synchronize()
+    y = Y.t()[:c1.n].cpu().numpy()
+    assert torch.all(Y[:, c1.n:] == 7.0)
+    M.close()
+    assert oracle.rel_l2(y, oracle.matvec(c1, x)) <= TOL
+
+
+def test_host_buffers(h2, c1):
+    M = h2.H2Matrix.from_generator(c1)
+    x = h2gen.vectors(310, c1.n, 5)
+    y = M.matvec_host(x)
+    M.close()
+    assert oracle.rel_l2(y, oracle.matvec(c1, x)) <= TOL
+
+
+def test_repeated_calls_are_stateless(h2, c1):
+    """The workspace is reused: a second product with other vectors must not see the first."""
+    M = h2.H2Matrix.from_generator(c1)
+    x1 = h2gen.vectors(311, c1.n, 16)
+    x2 = h2gen.vectors(312, c1.n, 1)
+    M.matvec(to_dev(x1))
+    y2 = M.matvec(to_dev(x2)).cpu().numpy()
+    M.close()
+    assert oracle.rel_l2(y2, oracle.matvec(c1, x2)) <= TOL
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("nv", [1, 16])
+def test_full_size_2d_n1M(h2, nv):
+    """The measured workload itself (2D, n = 2^20, m = 64, k = 16), every row checked."""
+    A = h2gen.generate(**h2gen.CONFIGS["2d_n1M"])
+    x = h2gen.vectors(400 + nv, A.n, nv)
+    y = gpu_matvec(h2, A, x)
+    assert oracle.rel_l2(y, oracle.matvec(A, x)) <= TOL
