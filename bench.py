@@ -1,0 +1,311 @@
+"""Benchmark of the H^2 matrix-vector product on GB300 (one JSON line on stdout).
+
+Workload (default): 2D exponential covariance exp(-r/0.1), n = 2^20 uniform
+points in the unit square, leaf size m = 64, 4x4 Chebyshev bases (k = 16),
+admissibility eta = 0.9, x ~ N(0,1), FP64 plain form, nv = 1. The matrix
+(about 15 GB) is far larger than the 129 MB L2, so every timed product streams
+it from HBM; no L2 flush is needed between steps.
+
+A step is one y = A^H x through the C ABI (all phases: projection, upsweep,
+coupling, downsweep, dense blocks + expansion). value = paper bytes streamed
+per step (U, V, E, F, S, D; the paper's Sec. 4.6 bandwidth metric) times steps
+on all ranks / max elapsed time over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import h2gen  # noqa: E402
+
+METRIC = "H^2 matvec HBM GB/s & vectors/s at n=2^20 (FP64 vs mixed @ rel err ≤1e-4)"
+WORKLOADS = {
+    "2d_n1M": "2D exp(-r/0.1) covariance H^2 matvec, n=2^20 uniform points, m=64, k=16 (4x4 Chebyshev), eta=0.9, FP64",
+    "2d_n4096": "2D exp(-r/0.1) covariance H^2 matvec, n=4096 uniform points, m=32, k=16, eta=0.9, FP64",
+    "2d_n256k": "2D exp(-r/0.1) covariance H^2 matvec, n=2^18 uniform points, m=64, k=16, eta=0.9, FP64",
+}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dense_kernel_bytes(info: dict, A, nv: int) -> int:
+    """Algorithmic bytes of one dense + expansion launch: D and U once, x read once, y written once,
+    the leaf yhat read once (8-byte values)."""
+    nDval = int(A.D_valoff[-1])
+    return 8 * (nDval + A.n * A.k) + 8 * A.n * nv * 2 + 8 * A.leaves * A.k * nv
+
+
+def run_oracle_baseline(A, x, budget_s: float = 12.0):
+    """Time the FP64 oracle (as it stands) on the host cores over about budget_s seconds."""
+    import oracle
+
+    oracle.matvec(A, x)  # warm
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.matvec(A, x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 200:
+            break
+    return el / reps, reps, oracle.threads()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="h2", choices=["h2", "reference"])
+    ap.add_argument("--workload", default="2d_n1M", choices=sorted(WORKLOADS))
+    ap.add_argument("--nv", type=int, default=1)
+    ap.add_argument("--no-extras", action="store_true", help="skip the nv=16 line, e2e and the CPU baseline")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg = dict(h2gen.CONFIGS[args.workload])
+    hbm, peak_kind = peaks()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        return reference_arm(args, cfg, world)
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_1902_01829_gb300 as h2
+
+    # weak scaling: every rank holds its own independent matrix (replicas of the workload)
+    cfg["seed"] = cfg["seed"] + 1000 * rank
+    A = h2gen.generate(**cfg)
+    M = h2.H2Matrix.from_generator(A)
+    info = M.info()
+    nv = args.nv
+    x_np = h2gen.vectors(77 + rank, A.n, nv)
+    x = torch.from_numpy(np.ascontiguousarray(x_np.T)).to(dev).t()
+    y = torch.empty((nv, A.n), dtype=torch.float64, device=dev).t()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(nvv=None, xx=None, yy=None):
+        M.matvec(x if xx is None else xx, y if yy is None else yy, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # correctness of this run's output (not timed): every row against the oracle
+    import oracle
+
+    y_ref = oracle.matvec(A, x_np)
+    rel_err = oracle.rel_l2(y.cpu().numpy(), y_ref)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    M.profile(True)
+    M.profile_read()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    phase_ms, launches = M.profile_read()
+    M.profile(False)
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    gbs = info["paper_bytes"] * world / (ms_step * 1e-3) / 1e9
+    vps = nv * world / (ms_step * 1e-3)
+
+    # roofline of the dominant kernel (dense blocks + leaf expansion), timed live above
+    dense_ms = phase_ms["dense_expand"] / args.steps
+    dbytes = dense_kernel_bytes(info, A, nv)
+    achieved = dbytes / (dense_ms * 1e-3) / 1e9
+    roofline = {"kernel": "k_dense_expand", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": None, "bytes_per_launch": dbytes,
+                "phase_share": {k: round(v / max(sum(phase_ms.values()), 1e-9), 4) for k, v in phase_ms.items()}}
+
+    out = {"metric": METRIC, "value": round(gbs, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64 (stored) / double-float (computed)", "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.workload], "n": A.n, "nv": nv, "q": A.q, "k": A.k,
+                      "nS": A.nS, "nD": A.nD, "paper_bytes": info["paper_bytes"],
+                      "l2": "matrix (%.1f GB) >> 129 MB L2: no flush needed" % (info["paper_bytes"] / 1e9),
+                      "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+           "vectors_per_s": round(vps, 2), "rel_err_vs_oracle": rel_err,
+           "gpu_launches": int(launches), "roofline": roofline,
+           "frac_of_nominal_8TBs": round(gbs / world / 8000.0, 4)}
+
+    clocks = clk.summary()
+    out["clocks"] = clocks
+
+    if not args.no_extras:
+        # end to end through the public C ABI with host buffers (pinned), copies inside the timed region
+        xh = torch.empty((nv, A.n), dtype=torch.float64, pin_memory=True)
+        xh.copy_(torch.from_numpy(np.ascontiguousarray(x_np.T)))
+        yh = torch.empty((nv, A.n), dtype=torch.float64, pin_memory=True)
+        xh_np, yh_np = xh.numpy().T, yh.numpy().T
+        for _ in range(2):
+            M.matvec_host(xh_np, yh_np, stream=stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            M.matvec_host(xh_np, yh_np, stream=stream)
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e_step = el / args.steps
+        out["e2e"] = {"value": round(info["paper_bytes"] * world / e2e_step / 1e9, 1), "unit": "GB/s",
+                      "ms_per_step": round(e2e_step * 1e3, 4), "vectors_per_s": round(nv * world / e2e_step, 2),
+                      "h2d_bytes_per_step": 8 * A.n * nv, "d2h_bytes_per_step": 8 * A.n * nv,
+                      "rel_err_vs_oracle": oracle.rel_l2(yh_np, y_ref)}
+
+        # 16 right-hand sides per product (the workload's second vector count)
+        x16_np = h2gen.vectors(177 + rank, A.n, 16)
+        x16 = torch.from_numpy(np.ascontiguousarray(x16_np.T)).to(dev).t()
+        y16 = torch.empty((16, A.n), dtype=torch.float64, device=dev).t()
+        for _ in range(3):
+            M.matvec(x16, y16, stream=stream)
+        steps16 = max(3, args.steps // 4)
+        barrier()
+        e0.record(stream)
+        for _ in range(steps16):
+            M.matvec(x16, y16, stream=stream)
+        e1.record(stream)
+        barrier()
+        ms16 = e0.elapsed_time(e1) / steps16
+        out["nv16"] = {"ms_per_step": round(ms16, 4), "vectors_per_s": round(16 * world / (ms16 * 1e-3), 1),
+                       "GBs": round(info["paper_bytes"] * world / (ms16 * 1e-3) / 1e9, 1),
+                       "rel_err_vs_oracle": oracle.rel_l2(y16.cpu().numpy(), oracle.matvec(A, x16_np))}
+
+        if rank == 0 and world == 1:
+            sec, reps, cores = run_oracle_baseline(A, x_np)
+            out["cpu_baseline"] = {"value": round(info["paper_bytes"] / sec / 1e9, 2), "unit": "GB/s",
+                                   "cores": cores, "kind": "oracle",
+                                   "sample": f"full workload, nv={nv}, {reps} products ({sec * 1e3:.1f} ms each)",
+                                   "vectors_per_s": round(nv / sec, 2)}
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    M.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def reference_arm(args, cfg, world):
+    """The FP64 CPU oracle, timed as it stands on the host cores, same workload and metric."""
+    import oracle
+
+    A = h2gen.generate(**cfg)
+    x = h2gen.vectors(77, A.n, args.nv)
+    paper_bytes = 8 * (2 * A.n * A.k + 2 * (A.n_nodes - 1) * A.k * A.k + A.nS * A.k * A.k + int(A.D_valoff[-1]))
+    for _ in range(max(1, min(args.warmup, 2))):
+        oracle.matvec(A, x)
+    steps = args.steps
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.matvec(A, x)
+    el = time.perf_counter() - t0
+    sec = el / steps
+    val = round(paper_bytes / sec / 1e9, 2)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": world, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.workload], "n": A.n, "nv": args.nv, "paper_bytes": paper_bytes},
+           "vectors_per_s": round(args.nv / sec, 2),
+           "cpu_baseline": {"value": val, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+                            "sample": f"full workload, nv={args.nv}, {steps} products"},
+           "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

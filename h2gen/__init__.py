@@ -206,6 +206,8 @@ CONFIGS = {
     "2d_n4096": dict(dim=2, n=4096, m=32, p=4, eta=0.9, kernel="exp", ell=0.1, seed=1),
     # 2D, n=2^20, exp(-r/0.1), m=64, k=16, eta=0.9
     "2d_n1M": dict(dim=2, n=1 << 20, m=64, p=4, eta=0.9, kernel="exp", ell=0.1, seed=2),
+    # 2D, n=2^18 (a few GB, still far larger than L2): the profiling case
+    "2d_n256k": dict(dim=2, n=1 << 18, m=64, p=4, eta=0.9, kernel="exp", ell=0.1, seed=4),
     # 3D, n=2^20, exp(-r/0.2), m=64, 4x4x4 Chebyshev (k=64), eta=0.9
     "3d_n1M": dict(dim=3, n=1 << 20, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=3),
 }

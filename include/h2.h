@@ -145,6 +145,20 @@ h2_status h2_matvec_host(h2_handle h, int32_t nv, const double* x, int64_t ldx, 
  */
 h2_status h2_info(h2_handle h, int64_t info[8]);
 
+/*
+ * Per-phase timing, for profiling (Sec. 4.6 reports a per-phase breakdown).
+ * While enabled, every product records CUDA events on its stream between its
+ * phases; h2_profile_read waits for the last recorded event, returns the
+ * summed milliseconds of each phase since profiling was enabled (or last
+ * read), the number of kernel launches, and starts a new sum.
+ * Phases: 0 leaf projection, 1 upsweep, 2 coupling, 3 downsweep,
+ * 4 dense blocks + leaf expansion. Disabled by default; enabling costs one
+ * event record per phase boundary.
+ */
+#define H2_NPHASES 5
+h2_status h2_profile(h2_handle h, int32_t enable);
+h2_status h2_profile_read(h2_handle h, double ms[H2_NPHASES], int64_t* launches);
+
 /* Free all device memory of the handle (synchronizes the device first). NULL is a no-op. */
 h2_status h2_destroy(h2_handle h);
 

@@ -21,7 +21,9 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
                 5: "H2_ERR_TIMEOUT"}
 
 # every symbol include/h2.h declares
-EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_info", "h2_destroy", "h2_last_error"]
+EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_info", "h2_profile", "h2_profile_read", "h2_destroy",
+           "h2_last_error"]
+PHASES = ["project", "upsweep", "coupling", "downsweep", "dense_expand"]
 
 
 class H2Error(RuntimeError):
@@ -50,8 +52,10 @@ def _load():
     lib.h2_matvec_host.argtypes = [vp, i32, vp, i64, vp, i64, vp]
     lib.h2_info.argtypes = [vp, vp]
     lib.h2_destroy.argtypes = [vp]
+    lib.h2_profile.argtypes = [vp, i32]
+    lib.h2_profile_read.argtypes = [vp, vp, vp]
     lib.h2_last_error.restype = ctypes.c_char_p
-    for name in ("h2_create", "h2_matvec", "h2_matvec_host", "h2_info", "h2_destroy"):
+    for name in ("h2_create", "h2_matvec", "h2_matvec_host", "h2_info", "h2_profile", "h2_profile_read", "h2_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -147,6 +151,17 @@ class H2Matrix:
         _check(_lib.h2_info(self._h, _ptr(a)))
         keys = ["paper_bytes", "device_bytes", "nS", "nD", "q", "k", "m_max", "n"]
         return {key: int(v) for key, v in zip(keys, a)}
+
+    def profile(self, enable: bool = True):
+        """Record per-phase CUDA events in every product while enabled (h2_profile)."""
+        _check(_lib.h2_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> tuple[dict, int]:
+        """Summed milliseconds per phase since the last read, and the kernel launch count."""
+        ms = np.zeros(len(PHASES), dtype=np.float64)
+        n = np.zeros(1, dtype=np.int64)
+        _check(_lib.h2_profile_read(self._h, _ptr(ms), _ptr(n)))
+        return dict(zip(PHASES, ms.tolist())), int(n[0])
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

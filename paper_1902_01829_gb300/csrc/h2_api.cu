@@ -61,6 +61,11 @@ struct h2_matrix_s {
   float2* x2 = nullptr;    // n x kPassVectors
   float2* xhat = nullptr;  // n_nodes x kPassVectors x k
   float2* yhat = nullptr;
+  // per-phase profiling: events recorded at phase boundaries while enabled
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t ev_used = 0;
+  int64_t launches = 0;
   // host-buffer staging (h2_matvec_host)
   double* hx = nullptr;
   double* hy = nullptr;
@@ -95,6 +100,8 @@ h2_status upload(h2_matrix_s* h, T** p, const T* src, int64_t count) {
 }
 
 void free_all(h2_matrix_s* h) {
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  h->events.clear();
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->hx) cudaFree(h->hx);
@@ -217,6 +224,18 @@ int pow2ceil(int v) {
 }
 
 // ------------------------------------------------------------------ launch sequence
+// record a phase-boundary event when profiling (events are pooled per handle)
+cudaError_t mark(h2_matrix_s* h, cudaStream_t st) {
+  if (!h->profiling) return cudaSuccess;
+  if (h->ev_used == h->events.size()) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    h->events.push_back(e);
+  }
+  return cudaEventRecord(h->events[h->ev_used++], st);
+}
+
 template <int RPL_K, int RPL_M, int NVB>
 h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
   using namespace h2;
@@ -224,19 +243,27 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
   const int64_t ld2 = h->n;
   const unsigned wb = (unsigned)kWarps * 32;
   auto grid = [](int64_t items) { return (unsigned)((items + kWarps - 1) / kWarps); };
+  cudaError_t me = mark(h, st);
   k_project<RPL_K, NVB><<<grid(h->leaves), wb, 0, st>>>(h->Vt, h->leaf_off, k, LR, h->leaves, h->leaf0, x, ldx, nv, h->x2, ld2,
                                                          h->xhat);
+  if (me == cudaSuccess) me = mark(h, st);
   for (int l = h->q; l >= 1; l--) {
     const int64_t pfirst = ((int64_t)1 << (l - 1)) - 1, pcount = (int64_t)1 << (l - 1);
     k_upsweep<RPL_K, NVB><<<grid(pcount), wb, 0, st>>>(h->Ft, k, LR, pfirst, pcount, nv, h->xhat);
   }
+  if (me == cudaSuccess) me = mark(h, st);
   k_coupling<RPL_K, NVB><<<grid(h->n_nodes), wb, 0, st>>>(h->S, h->Srow, h->Scol, k, LR, h->n_nodes, nv, h->xhat, h->yhat);
+  if (me == cudaSuccess) me = mark(h, st);
   for (int l = 1; l <= h->q; l++) {
     const int64_t cfirst = ((int64_t)1 << l) - 1, ccount = (int64_t)1 << l;
     k_downsweep<RPL_K, NVB><<<grid(ccount), wb, 0, st>>>(h->E, k, LR, cfirst, ccount, nv, h->yhat);
   }
+  if (me == cudaSuccess) me = mark(h, st);
   k_dense_expand<RPL_M, NVB><<<(unsigned)h->leaves, wb, 0, st>>>(h->D, h->Doff, h->Drow, h->Dcol, h->leaf_off, h->U, k, h->leaf0,
                                                                    h->x2, ld2, h->yhat, nv, y, ldy);
+  if (me == cudaSuccess) me = mark(h, st);
+  h->launches += 2 * h->q + 3;
+  if (me != cudaSuccess) return fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(H2_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
   return H2_OK;
@@ -393,6 +420,31 @@ h2_status h2_info(h2_handle h, int64_t info[8]) {
   info[5] = h->k;
   info[6] = h->m_max;
   info[7] = h->n;
+  return H2_OK;
+}
+
+h2_status h2_profile(h2_handle h, int32_t enable) {
+  if (!h) return fail(H2_ERR_INVALID, "NULL handle");
+  h->profiling = enable != 0;
+  h->ev_used = 0;
+  h->launches = 0;
+  return H2_OK;
+}
+
+h2_status h2_profile_read(h2_handle h, double ms[H2_NPHASES], int64_t* launches) {
+  if (!h || !ms) return fail(H2_ERR_INVALID, "NULL handle or output");
+  for (int p = 0; p < H2_NPHASES; p++) ms[p] = 0.0;
+  const size_t per = H2_NPHASES + 1;
+  if (h->ev_used) CUDA_TRY(cudaEventSynchronize(h->events[h->ev_used - 1]));
+  for (size_t base = 0; base + per <= h->ev_used; base += per)
+    for (int p = 0; p < H2_NPHASES; p++) {
+      float t = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&t, h->events[base + p], h->events[base + p + 1]));
+      ms[p] += t;
+    }
+  if (launches) *launches = h->launches;
+  h->ev_used = 0;
+  h->launches = 0;
   return H2_OK;
 }
 
