@@ -134,6 +134,24 @@ h2_status h2_matvec(h2_handle h, int32_t nv, const double* x, int64_t ldx, doubl
 h2_status h2_matvec_host(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream);
 
 /*
+ * Wait for `stream` to drain and report device-side failures of the products
+ * issued since the last check: H2_ERR_TIMEOUT if a bounded wait inside a
+ * kernel ran out (the kernel then stopped early and its results are invalid;
+ * the CUDA context stays usable). Clears the device error word.
+ */
+h2_status h2_check(h2_handle h, void* stream);
+
+/*
+ * Test hook for the bounded-wait path: in the next product, the streaming
+ * dense kernel's first CTA withholds the copy (and its arrival) of its local
+ * work item `item`, so the consumers' wait for that item runs out after
+ * `wait_budget_cycles` SM clock cycles (0 = the default of about 2 s).
+ * h2_check then returns H2_ERR_TIMEOUT. No fault, trap or endless loop is
+ * involved; later products run normally.
+ */
+h2_status h2_debug_withhold_copy(h2_handle h, int32_t item, int64_t wait_budget_cycles);
+
+/*
  * Sizes of the stored representation.
  *   info[0]  paper_bytes: bytes of U, V, E, F, S and D as streamed by one
  *            single-vector product (V and F counted even when aliased to U and

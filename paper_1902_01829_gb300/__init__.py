@@ -21,8 +21,8 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
                 5: "H2_ERR_TIMEOUT"}
 
 # every symbol include/h2.h declares
-EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_info", "h2_profile", "h2_profile_read", "h2_destroy",
-           "h2_last_error"]
+EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
+           "h2_profile_read", "h2_destroy", "h2_last_error"]
 PHASES = ["project", "upsweep", "coupling", "downsweep", "dense_expand"]
 
 
@@ -53,9 +53,12 @@ def _load():
     lib.h2_info.argtypes = [vp, vp]
     lib.h2_destroy.argtypes = [vp]
     lib.h2_profile.argtypes = [vp, i32]
+    lib.h2_check.argtypes = [vp, vp]
+    lib.h2_debug_withhold_copy.argtypes = [vp, i32, i64]
     lib.h2_profile_read.argtypes = [vp, vp, vp]
     lib.h2_last_error.restype = ctypes.c_char_p
-    for name in ("h2_create", "h2_matvec", "h2_matvec_host", "h2_info", "h2_profile", "h2_profile_read", "h2_destroy"):
+    for name in ("h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
+                 "h2_profile_read", "h2_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -151,6 +154,14 @@ class H2Matrix:
         _check(_lib.h2_info(self._h, _ptr(a)))
         keys = ["paper_bytes", "device_bytes", "nS", "nD", "q", "k", "m_max", "n"]
         return {key: int(v) for key, v in zip(keys, a)}
+
+    def check(self, stream=None):
+        """Wait for the stream and raise H2Error(H2_ERR_TIMEOUT) if a bounded device wait ran out (h2_check)."""
+        _check(_lib.h2_check(self._h, _stream_ptr(stream)))
+
+    def debug_withhold_copy(self, item: int, wait_budget_cycles: int = 0):
+        """Test hook: make the next product's dense kernel withhold one copy (h2_debug_withhold_copy)."""
+        _check(_lib.h2_debug_withhold_copy(self._h, int(item), int(wait_budget_cycles)))
 
     def profile(self, enable: bool = True):
         """Record per-phase CUDA events in every product while enabled (h2_profile)."""

@@ -11,6 +11,9 @@
 
 #include "h2.h"
 #include "hmv_fp64.cuh"
+#include "stream_fp64.cuh"
+
+static_assert(sizeof(h2::StreamItem) == 32, "work items are read as two int4");
 
 namespace {
 
@@ -37,30 +40,41 @@ h2_status fail(h2_status st, const char* fmt, ...) {
 
 constexpr int kMaxLeaf = 64;
 constexpr int kMaxRank = 64;
-constexpr int kPassVectors = 16;  // right-hand sides per pass over the matrix
+constexpr int kPassVectors = 16;                 // right-hand sides per pass over the matrix
+constexpr long long kWaitBudget = 4000000000LL;  // clock64 cycles (about 2 s) a device wait may take
+
+inline int64_t even(int64_t v) { return v + (v & 1); }
+
+struct ItemList {
+  h2::StreamItem* items = nullptr;  // device
+  int* cta_begin = nullptr;         // device [grid + 1]
+  int64_t count = 0;
+};
 
 }  // namespace
 
 struct h2_matrix_s {
   int64_t n = 0, leaves = 0, n_nodes = 0, leaf0 = 0, nS = 0, nD = 0, nDval = 0;
-  int q = 0, k = 0, m_max = 0, lr = 32;
+  int q = 0, k = 0, kp = 0, m_max = 0, lr = 32, grid = 0;
   int64_t paper_bytes = 0, device_bytes = 0;
   std::vector<void*> allocs;
   int64_t* leaf_off = nullptr;
-  double* U = nullptr;   // leaf i: size_i x k col-major (expansion)
-  double* Vt = nullptr;  // leaf j: k x size_j col-major (= V_j^T, projection)
-  double* E = nullptr;   // node h >= 1: k x k col-major (downsweep)
-  double* Ft = nullptr;  // node h >= 1: F_h^T, k x k col-major (upsweep)
+  int64_t* xp_off = nullptr;  // padded leaf offsets of the split x (float2 per vector)
+  double* Vt = nullptr;       // leaf j: k x size_j col-major (= V_j^T, projection)
+  double* E = nullptr;        // node h >= 1: k x k col-major (downsweep)
+  double* Ft = nullptr;       // node h >= 1: F_h^T, k x k col-major (upsweep)
+  char* dmat = nullptr;       // dense blocks then leaf bases U, each padded to an even count of doubles
+  double* smat = nullptr;     // coupling blocks, each padded to an even count of doubles
   int32_t* Srow = nullptr;
   int32_t* Scol = nullptr;
-  double* S = nullptr;
-  int32_t* Drow = nullptr;
-  int32_t* Dcol = nullptr;
-  int64_t* Doff = nullptr;
-  double* D = nullptr;
-  float2* x2 = nullptr;    // n x kPassVectors
-  float2* xhat = nullptr;  // n_nodes x kPassVectors x k
+  ItemList dense_items;
+  bool pair_rows = false;  // k = 2^j (j >= 1): the coupling kernel reads row pairs
+  int* err = nullptr;      // device error word (bounded waits)
+  float2* x2 = nullptr;    // split x, padded leaf layout, kPassVectors slots
+  float2* xhat = nullptr;  // n_nodes x kPassVectors x kp
   float2* yhat = nullptr;
+  long long budget = kWaitBudget;
+  int inject = -1;
   // per-phase profiling: events recorded at phase boundaries while enabled
   bool profiling = false;
   std::vector<cudaEvent_t> events;
@@ -148,11 +162,14 @@ h2_status check_cover(const h2_desc* d, int64_t leaves) {
     std::sort(iv.begin(), iv.end());
     int64_t at = 0;
     for (auto& r : iv) {
-      if (r.first != at) return fail(H2_ERR_INVALID, "block cover: leaf row %lld, columns from leaf %lld %s", (long long)i,
-                                     (long long)std::min(at, r.first), r.first > at ? "are not covered" : "are covered twice");
+      if (r.first != at)
+        return fail(H2_ERR_INVALID, "block cover: leaf row %lld, columns from leaf %lld %s", (long long)i,
+                    (long long)std::min(at, r.first), r.first > at ? "are not covered" : "are covered twice");
       at = r.second;
     }
-    if (at != leaves) return fail(H2_ERR_INVALID, "block cover: leaf row %lld, columns from leaf %lld are not covered", (long long)i, (long long)at);
+    if (at != leaves)
+      return fail(H2_ERR_INVALID, "block cover: leaf row %lld, columns from leaf %lld are not covered", (long long)i,
+                  (long long)at);
   }
   return H2_OK;
 }
@@ -160,17 +177,16 @@ h2_status check_cover(const h2_desc* d, int64_t leaves) {
 h2_status validate(const h2_desc* d, int64_t* nS, int64_t* nD, int64_t* nDval, int* m_max) {
   if (!d) return fail(H2_ERR_INVALID, "desc is NULL");
   if (d->n < 1) return fail(H2_ERR_INVALID, "n = %lld < 1", (long long)d->n);
+  if (d->n >= ((int64_t)1 << 31)) return fail(H2_ERR_UNSUPPORTED, "n = %lld >= 2^31", (long long)d->n);
   if (d->depth < 0 || d->depth > 24) return fail(H2_ERR_INVALID, "depth = %d outside 0..24", d->depth);
   if (d->rank < 1) return fail(H2_ERR_INVALID, "rank = %d < 1", d->rank);
   if (d->rank > kMaxRank) return fail(H2_ERR_UNSUPPORTED, "rank = %d > %d", d->rank, kMaxRank);
   if (d->storage != H2_FP64) return fail(H2_ERR_UNSUPPORTED, "storage %d not supported", d->storage);
-  if (!d->leaf_offset || !d->U || !d->E || !d->S_rowptr || !d->D_rowptr)
-    return fail(H2_ERR_INVALID, "NULL array in desc");
+  if (!d->leaf_offset || !d->U || !d->E || !d->S_rowptr || !d->D_rowptr) return fail(H2_ERR_INVALID, "NULL array in desc");
   if (!d->symmetric && (!d->V || !d->F)) return fail(H2_ERR_INVALID, "V/F are NULL but symmetric = 0");
   const int q = d->depth, k = d->rank;
   const int64_t leaves = (int64_t)1 << q, n_nodes = ((int64_t)2 << q) - 1;
-  if (d->leaf_offset[0] != 0 || d->leaf_offset[leaves] != d->n)
-    return fail(H2_ERR_INVALID, "leaf_offset must run from 0 to n");
+  if (d->leaf_offset[0] != 0 || d->leaf_offset[leaves] != d->n) return fail(H2_ERR_INVALID, "leaf_offset must run from 0 to n");
   int mm = 0;
   for (int64_t i = 0; i < leaves; i++) {
     const int64_t s = d->leaf_offset[i + 1] - d->leaf_offset[i];
@@ -223,6 +239,62 @@ int pow2ceil(int v) {
   return p;
 }
 
+// transpose a rows x cols column-major block into dst (cols x rows column-major)
+void transpose_block(const double* src, double* dst, int64_t rows, int64_t cols) {
+  for (int64_t c = 0; c < cols; c++)
+    for (int64_t r = 0; r < rows; r++) dst[c + cols * r] = src[r + rows * c];
+}
+
+// Split rows (row r weighs row_bytes[r] and starts at item row_item0[r]) into
+// `grid` contiguous ranges of about equal weight; returns each range's first item.
+std::vector<int> balance(const std::vector<int64_t>& row_bytes, const std::vector<int64_t>& row_item0, int grid) {
+  const int64_t rows = (int64_t)row_bytes.size();
+  int64_t total = 0;
+  for (int64_t b : row_bytes) total += b;
+  std::vector<int> begin((size_t)grid + 1, 0);
+  int64_t acc = 0, r = 0;
+  for (int c = 0; c < grid; c++) {
+    begin[c] = (int)row_item0[r];
+    const int64_t target = (total * (c + 1)) / grid;
+    while (r < rows && acc + row_bytes[r] / 2 < target) acc += row_bytes[r++];
+  }
+  begin[grid] = (int)row_item0[rows];
+  for (int c = 1; c <= grid; c++) begin[c] = std::max(begin[c], begin[c - 1]);
+  return begin;
+}
+
+// Every copy a streaming kernel will issue must stay inside its source buffer and
+// its stage slot and be 16-byte aligned; checked once on the host so that a
+// layout bug is an error here, never an out-of-bounds bulk copy on the device.
+//   mat_bytes   size of the matrix buffer the items index
+//   v0, v1      float2 counts per vector slot of the two vector sources
+h2_status audit_items(const std::vector<h2::StreamItem>& items, const std::vector<int>& begin, int64_t mat_bytes,
+                      int64_t v0, int64_t v1) {
+  for (size_t c = 0; c + 1 < begin.size(); c++)
+    if (begin[c] > begin[c + 1]) return fail(H2_ERR_INVALID, "internal: item ranges not monotone");
+  if (begin.front() != 0 || begin.back() != (int)items.size()) return fail(H2_ERR_INVALID, "internal: item ranges do not cover the list");
+  for (size_t i = 0; i < items.size(); i++) {
+    const h2::StreamItem& it = items[i];
+    const int64_t R = it.shape & 0xFF, C = (it.shape >> 8) & 0xFF, vs = (it.shape >> 16) & 0xFF, nb = (it.shape >> 24) & 0xFF;
+    // vector chunk: nv * vs float2 at v_off * nv, nv <= kPassVectors; stage slot: 512 * NVB bytes >= 64 * nv * 8
+    const int64_t lim = (it.flags & h2::kItemFlagSrc1) ? v1 : v0;
+    const bool ok = it.m_off >= 0 && it.m_off % 16 == 0 && it.m_bytes >= 16 && it.m_bytes % 16 == 0 &&
+                    it.m_bytes <= h2::kStageMat && it.m_off + it.m_bytes <= mat_bytes && R >= 1 && R <= 64 && C >= 1 &&
+                    C <= 64 && vs >= C && vs <= 64 && vs % 2 == 0 && nb == 1 && it.v_off >= 0 && it.v_off % 2 == 0 &&
+                    it.v_off + vs <= lim && it.m_bytes == (int64_t)(R * C + ((R * C) & 1)) * 8;
+    if (!ok) return fail(H2_ERR_INVALID, "internal: work item %lld fails the layout audit", (long long)i);
+  }
+  return H2_OK;
+}
+
+h2_status upload_items(h2_matrix_s* h, ItemList* L, const std::vector<h2::StreamItem>& items, const std::vector<int>& begin) {
+  h2_status st = upload(h, &L->items, items.data(), (int64_t)items.size());
+  if (st != H2_OK) return st;
+  st = upload(h, &L->cta_begin, begin.data(), (int64_t)begin.size());
+  L->count = (int64_t)items.size();
+  return st;
+}
+
 // ------------------------------------------------------------------ launch sequence
 // record a phase-boundary event when profiling (events are pooled per handle)
 cudaError_t mark(h2_matrix_s* h, cudaStream_t st) {
@@ -236,46 +308,83 @@ cudaError_t mark(h2_matrix_s* h, cudaStream_t st) {
   return cudaEventRecord(h->events[h->ev_used++], st);
 }
 
-template <int RPL_K, int RPL_M, int NVB>
+template <int NVB>
+cudaError_t set_stream_smem() {
+  static cudaError_t done = cudaErrorNotReady;
+  if (done == cudaErrorNotReady) {
+    constexpr int CW = h2::dense_consumer_warps(NVB);
+    done = cudaFuncSetAttribute(h2::k_dense_stream<NVB, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                h2::stream_smem_bytes(NVB, CW));
+  }
+  return done;
+}
+
+template <int RPL_K, int NVB>
 h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
   using namespace h2;
-  const int k = h->k, LR = h->lr;
-  const int64_t ld2 = h->n;
+  const int k = h->k, kp = h->kp, LR = h->lr;
   const unsigned wb = (unsigned)kWarps * 32;
   auto grid = [](int64_t items) { return (unsigned)((items + kWarps - 1) / kWarps); };
+  cudaError_t e = set_stream_smem<NVB>();
+  if (e != cudaSuccess) return fail(H2_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  constexpr int CW = dense_consumer_warps(NVB);
+  constexpr int smem = stream_smem_bytes(NVB, CW);
+  const int kkp = (int)even((int64_t)k * k);
   cudaError_t me = mark(h, st);
-  k_project<RPL_K, NVB><<<grid(h->leaves), wb, 0, st>>>(h->Vt, h->leaf_off, k, LR, h->leaves, h->leaf0, x, ldx, nv, h->x2, ld2,
-                                                         h->xhat);
+  k_project<RPL_K, NVB><<<grid(h->leaves), wb, 0, st>>>(h->Vt, h->leaf_off, h->xp_off, k, kp, LR, h->leaves, h->leaf0, x,
+                                                         ldx, nv, h->x2, h->xhat);
   if (me == cudaSuccess) me = mark(h, st);
   for (int l = h->q; l >= 1; l--) {
     const int64_t pfirst = ((int64_t)1 << (l - 1)) - 1, pcount = (int64_t)1 << (l - 1);
-    k_upsweep<RPL_K, NVB><<<grid(pcount), wb, 0, st>>>(h->Ft, k, LR, pfirst, pcount, nv, h->xhat);
+    k_upsweep<RPL_K, NVB><<<grid(pcount), wb, 0, st>>>(h->Ft, k, kp, LR, pfirst, pcount, nv, h->xhat);
   }
   if (me == cudaSuccess) me = mark(h, st);
-  k_coupling<RPL_K, NVB><<<grid(h->n_nodes), wb, 0, st>>>(h->S, h->Srow, h->Scol, k, LR, h->n_nodes, nv, h->xhat, h->yhat);
+  if (h->pair_rows) {
+    constexpr int CB = NVB <= 2 ? 4 : (NVB <= 4 ? 2 : 1);
+    k_coupling<NVB, CB><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, h->n_nodes, nv, h->xhat,
+                                                          h->yhat);
+  } else {
+    k_coupling_generic<RPL_K, NVB><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, LR, h->n_nodes,
+                                                                     nv, h->xhat, h->yhat);
+  }
   if (me == cudaSuccess) me = mark(h, st);
   for (int l = 1; l <= h->q; l++) {
     const int64_t cfirst = ((int64_t)1 << l) - 1, ccount = (int64_t)1 << l;
-    k_downsweep<RPL_K, NVB><<<grid(ccount), wb, 0, st>>>(h->E, k, LR, cfirst, ccount, nv, h->yhat);
+    k_downsweep<RPL_K, NVB><<<grid(ccount), wb, 0, st>>>(h->E, k, kp, LR, cfirst, ccount, nv, h->yhat);
   }
   if (me == cudaSuccess) me = mark(h, st);
-  k_dense_expand<RPL_M, NVB><<<(unsigned)h->leaves, wb, 0, st>>>(h->D, h->Doff, h->Drow, h->Dcol, h->leaf_off, h->U, k, h->leaf0,
-                                                                   h->x2, ld2, h->yhat, nv, y, ldy);
+  StreamParams P{};
+  P.items = h->dense_items.items;
+  P.cta_begin = h->dense_items.cta_begin;
+  P.mat = h->dmat;
+  P.vsrc0 = h->x2;
+  P.vsrc1 = h->yhat;
+  P.nv = nv;
+  P.y = y;
+  P.ldy = ldy;
+  P.err = h->err;
+  P.budget = h->budget;
+  P.inject = h->inject;
+  k_dense_stream<NVB, CW><<<h->grid, (CW + 1) * 32, smem, st>>>(P);
+  if (h->inject >= 0) {  // the test hook applies to one product only
+    h->inject = -1;
+    h->budget = kWaitBudget;
+  }
   if (me == cudaSuccess) me = mark(h, st);
   h->launches += 2 * h->q + 3;
   if (me != cudaSuccess) return fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return fail(H2_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
   return H2_OK;
 }
 
-template <int RPL_K, int RPL_M>
+template <int RPL_K>
 h2_status run_pass_nv(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
-  if (nv <= 1) return run_pass<RPL_K, RPL_M, 1>(h, nv, x, ldx, y, ldy, st);
-  if (nv <= 2) return run_pass<RPL_K, RPL_M, 2>(h, nv, x, ldx, y, ldy, st);
-  if (nv <= 4) return run_pass<RPL_K, RPL_M, 4>(h, nv, x, ldx, y, ldy, st);
-  if (nv <= 8) return run_pass<RPL_K, RPL_M, 8>(h, nv, x, ldx, y, ldy, st);
-  return run_pass<RPL_K, RPL_M, 16>(h, nv, x, ldx, y, ldy, st);
+  if (nv <= 1) return run_pass<RPL_K, 1>(h, nv, x, ldx, y, ldy, st);
+  if (nv <= 2) return run_pass<RPL_K, 2>(h, nv, x, ldx, y, ldy, st);
+  if (nv <= 4) return run_pass<RPL_K, 4>(h, nv, x, ldx, y, ldy, st);
+  if (nv <= 8) return run_pass<RPL_K, 8>(h, nv, x, ldx, y, ldy, st);
+  return run_pass<RPL_K, 16>(h, nv, x, ldx, y, ldy, st);
 }
 
 h2_status matvec_device(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
@@ -283,21 +392,139 @@ h2_status matvec_device(h2_matrix_s* h, int nv, const double* x, int64_t ldx, do
     const int nvp = std::min(kPassVectors, nv - v0);
     const double* xp = x + (int64_t)v0 * ldx;
     double* yp = y + (int64_t)v0 * ldy;
-    h2_status s;
-    const bool kk2 = h->k > 32, mm2 = h->m_max > 32;
-    if (kk2 && mm2) s = run_pass_nv<2, 2>(h, nvp, xp, ldx, yp, ldy, st);
-    else if (kk2) s = run_pass_nv<2, 1>(h, nvp, xp, ldx, yp, ldy, st);
-    else if (mm2) s = run_pass_nv<1, 2>(h, nvp, xp, ldx, yp, ldy, st);
-    else s = run_pass_nv<1, 1>(h, nvp, xp, ldx, yp, ldy, st);
+    h2_status s = (h->k > 32) ? run_pass_nv<2>(h, nvp, xp, ldx, yp, ldy, st) : run_pass_nv<1>(h, nvp, xp, ldx, yp, ldy, st);
     if (s != H2_OK) return s;
   }
   return H2_OK;
 }
 
-// transpose every k x k block (or size x k leaf block) into a host buffer
-void transpose_blocks(const double* src, double* dst, int64_t rows, int64_t cols) {
-  for (int64_t c = 0; c < cols; c++)
-    for (int64_t r = 0; r < rows; r++) dst[c + cols * r] = src[r + rows * c];
+// ------------------------------------------------------------------ device layout
+h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
+  const int k = h->k;
+  const int64_t kk = (int64_t)k * k, kkp = even(kk);
+  const double* V = d->symmetric ? d->U : d->V;
+  const double* F = d->symmetric ? d->E : d->F;
+  const int64_t* lo = d->leaf_offset;
+  h2_status st;
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&h->grid, cudaDevAttrMultiProcessorCount, dev));
+
+  if ((st = upload(h, &h->leaf_off, lo, h->leaves + 1)) != H2_OK) return st;
+  // padded leaf offsets of the split x
+  std::vector<int64_t> xp((size_t)h->leaves + 1, 0);
+  for (int64_t j = 0; j < h->leaves; j++) xp[j + 1] = xp[j] + even(lo[j + 1] - lo[j]);
+  if ((st = upload(h, &h->xp_off, xp.data(), h->leaves + 1)) != H2_OK) return st;
+
+  {  // leaf bases V^T (projection), transfers F^T (upsweep), E (downsweep)
+    std::vector<double> tmp((size_t)std::max<int64_t>(h->n * k, (h->n_nodes - 1) * kk));
+    for (int64_t j = 0; j < h->leaves; j++) transpose_block(V + lo[j] * k, tmp.data() + lo[j] * k, lo[j + 1] - lo[j], k);
+    if ((st = upload(h, &h->Vt, (const double*)tmp.data(), h->n * k)) != H2_OK) return st;
+    for (int64_t c = 0; c < h->n_nodes - 1; c++) transpose_block(F + c * kk, tmp.data() + c * kk, k, k);
+    if ((st = upload(h, &h->Ft, (const double*)tmp.data(), (h->n_nodes - 1) * kk)) != H2_OK) return st;
+    if ((st = upload(h, &h->E, d->E, (h->n_nodes - 1) * kk)) != H2_OK) return st;
+  }
+
+  {  // dense blocks + U, each padded to an even count of doubles, and their item list
+    std::vector<int64_t> doff((size_t)h->nD + 1, 0), dpo((size_t)h->nD + 1, 0), upo((size_t)h->leaves + 1, 0);
+    for (int64_t r = 0, b = 0; r < h->leaves; r++)
+      for (; b < d->D_rowptr[r + 1]; b++) {
+        const int64_t sz = (lo[r + 1] - lo[r]) * (lo[d->D_colidx[b] + 1] - lo[d->D_colidx[b]]);
+        doff[b + 1] = doff[b] + sz;
+        dpo[b + 1] = dpo[b] + even(sz);
+      }
+    for (int64_t i = 0; i < h->leaves; i++) upo[i + 1] = upo[i] + even((lo[i + 1] - lo[i]) * k);
+    const int64_t dtot = dpo[h->nD], total = dtot + upo[h->leaves];
+    double* dm = nullptr;
+    if ((st = dalloc(h, &dm, total)) != H2_OK) return st;
+    h->dmat = (char*)dm;
+    // copy through a host staging buffer, inserting the padding
+    const int64_t chunk = (int64_t)1 << 24;
+    std::vector<double> stage((size_t)chunk);
+    int64_t fill = 0, dst0 = 0;
+    auto flush = [&]() -> h2_status {
+      if (fill) CUDA_TRY(cudaMemcpy(dm + dst0, stage.data(), (size_t)fill * 8, cudaMemcpyHostToDevice));
+      dst0 += fill;
+      fill = 0;
+      return H2_OK;
+    };
+    auto put = [&](const double* src, int64_t cnt, int64_t padded) -> h2_status {
+      if (fill + padded > chunk) {
+        h2_status s2 = flush();
+        if (s2 != H2_OK) return s2;
+      }
+      std::memcpy(stage.data() + fill, src, (size_t)cnt * 8);
+      if (padded > cnt) stage[fill + cnt] = 0.0;
+      fill += padded;
+      return H2_OK;
+    };
+    for (int64_t b = 0; b < h->nD; b++)
+      if ((st = put(d->D_val + doff[b], doff[b + 1] - doff[b], dpo[b + 1] - dpo[b])) != H2_OK) return st;
+    for (int64_t i = 0; i < h->leaves; i++)
+      if ((st = put(d->U + lo[i] * k, (lo[i + 1] - lo[i]) * k, upo[i + 1] - upo[i])) != H2_OK) return st;
+    if ((st = flush()) != H2_OK) return st;
+
+    std::vector<h2::StreamItem> items;
+    items.reserve((size_t)(h->nD + h->leaves));
+    std::vector<int64_t> row_bytes((size_t)h->leaves), row_item0((size_t)h->leaves + 1);
+    for (int64_t i = 0; i < h->leaves; i++) {
+      row_item0[i] = (int64_t)items.size();
+      const int si = (int)(lo[i + 1] - lo[i]);
+      int64_t bytes = 0;
+      for (int32_t b = d->D_rowptr[i]; b < d->D_rowptr[i + 1]; b++) {
+        const int j = d->D_colidx[b];
+        const int sj = (int)(lo[j + 1] - lo[j]);
+        h2::StreamItem it{};
+        it.m_off = dpo[b] * 8;
+        it.m_bytes = (int)((dpo[b + 1] - dpo[b]) * 8);
+        it.shape = (unsigned)si | ((unsigned)sj << 8) | ((unsigned)even(sj) << 16) | (1u << 24);
+        it.v_off = xp[j];
+        it.row = (int)lo[i];
+        it.flags = 0;
+        items.push_back(it);
+        bytes += it.m_bytes + 8 * sj;
+      }
+      h2::StreamItem it{};
+      it.m_off = (dtot + upo[i]) * 8;
+      it.m_bytes = (int)((upo[i + 1] - upo[i]) * 8);
+      it.shape = (unsigned)si | ((unsigned)k << 8) | ((unsigned)h->kp << 16) | (1u << 24);
+      it.v_off = (h->leaf0 + i) * h->kp;
+      it.row = (int)lo[i];
+      it.flags = h2::kItemFlagLast | h2::kItemFlagSrc1;
+      items.push_back(it);
+      row_bytes[i] = bytes + it.m_bytes + 8 * h->kp + 16 * si;
+    }
+    row_item0[h->leaves] = (int64_t)items.size();
+    const std::vector<int> begin = balance(row_bytes, row_item0, h->grid);
+    // vector sources per slot: split x (padded leaf layout) and yhat (n_nodes x kp)
+    if ((st = audit_items(items, begin, total * 8, xp[h->leaves], h->n_nodes * h->kp)) != H2_OK) return st;
+    if ((st = upload_items(h, &h->dense_items, items, begin)) != H2_OK) return st;
+  }
+
+  {  // coupling blocks, each padded to an even count of doubles
+    double* sm = nullptr;
+    if ((st = dalloc(h, &sm, h->nS * kkp)) != H2_OK) return st;
+    h->smat = sm;
+    if (h->nS > 0) {
+      if (kkp == kk) {
+        CUDA_TRY(cudaMemcpy(sm, d->S_val, (size_t)(h->nS * kk) * 8, cudaMemcpyHostToDevice));
+      } else {
+        CUDA_TRY(cudaMemset(sm, 0, (size_t)(h->nS * kkp) * 8));
+        CUDA_TRY(cudaMemcpy2D(sm, (size_t)kkp * 8, d->S_val, (size_t)kk * 8, (size_t)kk * 8, (size_t)h->nS,
+                              cudaMemcpyHostToDevice));
+      }
+    }
+    if ((st = upload(h, &h->Srow, d->S_rowptr, h->n_nodes + 1)) != H2_OK) return st;
+    if ((st = upload(h, &h->Scol, d->S_colidx, h->nS)) != H2_OK) return st;
+    h->pair_rows = k >= 2 && k <= 64 && (k & (k - 1)) == 0;
+  }
+
+  if ((st = dalloc(h, &h->err, 1)) != H2_OK) return st;
+  CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
+  if ((st = dalloc(h, &h->x2, xp[h->leaves] * kPassVectors)) != H2_OK) return st;
+  if ((st = dalloc(h, &h->xhat, h->n_nodes * kPassVectors * h->kp)) != H2_OK) return st;
+  if ((st = dalloc(h, &h->yhat, h->n_nodes * kPassVectors * h->kp)) != H2_OK) return st;
+  return H2_OK;
 }
 
 }  // namespace
@@ -319,6 +546,7 @@ h2_status h2_create(const h2_desc* d, h2_handle* out) {
   h->n = d->n;
   h->q = d->depth;
   h->k = d->rank;
+  h->kp = (int)even(h->k);
   h->leaves = (int64_t)1 << h->q;
   h->n_nodes = ((int64_t)2 << h->q) - 1;
   h->leaf0 = h->leaves - 1;
@@ -327,54 +555,18 @@ h2_status h2_create(const h2_desc* d, h2_handle* out) {
   h->nDval = nDval;
   h->m_max = m_max;
   h->lr = h->k > 32 ? 32 : pow2ceil(h->k);
-  const int k = h->k;
-  const int64_t kk = (int64_t)k * k;
-  const double* V = d->symmetric ? d->U : d->V;
-  const double* F = d->symmetric ? d->E : d->F;
-  std::vector<int64_t> doff((size_t)nD + 1, 0);
-  for (int64_t r = 0, b = 0; r < h->leaves; r++)
-    for (; b < d->D_rowptr[r + 1]; b++) {
-      const int32_t j = d->D_colidx[b];
-      doff[b + 1] = doff[b] + (d->leaf_offset[r + 1] - d->leaf_offset[r]) * (d->leaf_offset[j + 1] - d->leaf_offset[j]);
-    }
-  std::vector<double> tmp;
   try {
-    tmp.resize((size_t)std::max<int64_t>(h->n * k, (h->n_nodes - 1) * kk));
-  } catch (...) {
+    st = build_device(h, d);
+  } catch (const std::bad_alloc&) {
+    st = fail(H2_ERR_OOM, "host allocation failed");
+  }
+  if (st != H2_OK) {
+    free_all(h);
     delete h;
-    return fail(H2_ERR_OOM, "host allocation failed");
+    return st;
   }
-#define TRY(x)                 \
-  do {                         \
-    st = (x);                  \
-    if (st != H2_OK) {         \
-      free_all(h);             \
-      delete h;                \
-      return st;               \
-    }                          \
-  } while (0)
-  TRY(upload(h, &h->leaf_off, d->leaf_offset, h->leaves + 1));
-  TRY(upload(h, &h->U, d->U, h->n * k));
-  for (int64_t j = 0; j < h->leaves; j++) {
-    const int64_t off = d->leaf_offset[j], s = d->leaf_offset[j + 1] - off;
-    transpose_blocks(V + off * k, tmp.data() + off * k, s, k);
-  }
-  TRY(upload(h, &h->Vt, (const double*)tmp.data(), h->n * k));
-  TRY(upload(h, &h->E, d->E, (h->n_nodes - 1) * kk));
-  for (int64_t c = 0; c < h->n_nodes - 1; c++) transpose_blocks(F + c * kk, tmp.data() + c * kk, k, k);
-  TRY(upload(h, &h->Ft, (const double*)tmp.data(), (h->n_nodes - 1) * kk));
-  TRY(upload(h, &h->Srow, d->S_rowptr, h->n_nodes + 1));
-  TRY(upload(h, &h->Scol, d->S_colidx, nS));
-  TRY(upload(h, &h->S, d->S_val, nS * kk));
-  TRY(upload(h, &h->Drow, d->D_rowptr, h->leaves + 1));
-  TRY(upload(h, &h->Dcol, d->D_colidx, nD));
-  TRY(upload(h, &h->Doff, (const int64_t*)doff.data(), nD + 1));
-  TRY(upload(h, &h->D, d->D_val, nDval));
-  TRY(dalloc(h, &h->x2, h->n * kPassVectors));
-  TRY(dalloc(h, &h->xhat, h->n_nodes * kPassVectors * k));
-  TRY(dalloc(h, &h->yhat, h->n_nodes * kPassVectors * k));
-#undef TRY
-  h->paper_bytes = 8 * (2 * h->n * k + 2 * (h->n_nodes - 1) * kk + nS * kk + nDval);
+  const int64_t kk = (int64_t)h->k * h->k;
+  h->paper_bytes = 8 * (2 * h->n * h->k + 2 * (h->n_nodes - 1) * kk + nS * kk + nDval);
   *out = h;
   return H2_OK;
 }
@@ -402,11 +594,32 @@ h2_status h2_matvec_host(h2_handle h, int32_t nv, const double* x, int64_t ldx, 
     CUDA_TRY(cudaMalloc(&h->hy, (size_t)need * sizeof(double)));
     h->host_cap = need;
   }
-  CUDA_TRY(cudaMemcpy2DAsync(h->hx, (size_t)h->n * 8, x, (size_t)ldx * 8, (size_t)h->n * 8, (size_t)nv, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpy2DAsync(h->hx, (size_t)h->n * 8, x, (size_t)ldx * 8, (size_t)h->n * 8, (size_t)nv,
+                             cudaMemcpyHostToDevice, st));
   h2_status s = matvec_device(h, nv, h->hx, h->n, h->hy, h->n, st);
   if (s != H2_OK) return s;
-  CUDA_TRY(cudaMemcpy2DAsync(y, (size_t)ldy * 8, h->hy, (size_t)h->n * 8, (size_t)h->n * 8, (size_t)nv, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpy2DAsync(y, (size_t)ldy * 8, h->hy, (size_t)h->n * 8, (size_t)h->n * 8, (size_t)nv,
+                             cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  return H2_OK;
+}
+
+h2_status h2_check(h2_handle h, void* stream) {
+  if (!h) return fail(H2_ERR_INVALID, "NULL handle");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int e = 0;
+  CUDA_TRY(cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
+    return fail(H2_ERR_TIMEOUT, "a bounded device wait ran out; products since the last check are invalid");
+  }
+  return H2_OK;
+}
+
+h2_status h2_debug_withhold_copy(h2_handle h, int32_t item, int64_t wait_budget_cycles) {
+  if (!h) return fail(H2_ERR_INVALID, "NULL handle");
+  h->inject = item;
+  h->budget = wait_budget_cycles > 0 ? wait_budget_cycles : kWaitBudget;
   return H2_OK;
 }
 

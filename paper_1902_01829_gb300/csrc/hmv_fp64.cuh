@@ -1,18 +1,18 @@
-// FP64 plain-form kernels of the H^2 matrix-vector product (Sec. 4), one per phase.
+// FP64 plain-form kernels for the tree phases of the H^2 matrix-vector
+// product (Sec. 4.2 and 4.4): leaf projection, upsweep and downsweep.
 //
-// Every phase is a sum of column-major block products "rows += A_block * x_cols":
+// Each phase is a sum of column-major block products "rows += A_block * x_cols":
 //   leaf projection  xhat_j  = V_j^T x(j)            A = V_j^T (stored transposed)
 //   upsweep          xhat_p  = sum_c F_c^T xhat_c    A = F_c^T (stored transposed)   Eq. 2
-//   coupling         yhat_i  = sum_j S_ij xhat_j     A = S_ij                        Eq. 3
 //   downsweep        yhat_c += E_c yhat_p            A = E_c                         Eq. 5
-//   dense + expand   y(i)    = U_i yhat_i + sum_j D_ij x(j)                          Eq. 4, Sec. 2.2
-// so one warp routine serves all of them: a lane owns output rows, consecutive
-// lanes read consecutive rows of a column (coalesced), the input vector entry
-// of the column is a broadcast, and products accumulate in double-float.
+// One warp owns one output node: a lane owns output rows, consecutive lanes read
+// consecutive rows of a column (coalesced), the column's input entry is a
+// broadcast, and products accumulate in double-float. Loads of several columns
+// are issued before any of them is used, so a warp keeps many in flight.
 //
-// Workspace layouts (float2 = double-float hi, lo):
-//   x2    [v * ld2 + point]              the pass's x, split once
-//   xhat  [(node * nv + v) * k + row]    vector trees of Sec. 4.2 - 4.4
+// Workspace layouts (float2 = double-float hi, lo; kp = k rounded up to even):
+//   x2    leaf j's chunk at xp_off[j] * nv: [v][spad_j] (spad = leaf size rounded up to even)
+//   xhat  [(node * nv + v) * kp + row]   vector trees of Sec. 4.2 - 4.4
 //   yhat  same as xhat
 #pragma once
 #include "df64.cuh"
@@ -25,27 +25,33 @@ constexpr int kWarps = 4;  // warps per CTA for the per-node kernels
 // rl + 32 r (r < RPL) and columns col = g, g + G, ... with G = 32 / LR groups.
 // RPL = 2 requires LR = 32 (R <= 64); RPL = 1 allows LR = 1 .. 32 (R <= LR).
 template <int RPL, int NVB>
-__device__ __forceinline__ void warp_mv(const double* __restrict__ A, int R, int C, int LR,
-                                        const float2* xin, int64_t xstride, int nv,
-                                        float (&s)[RPL][NVB], float (&c)[RPL][NVB], int lane) {
+__device__ __forceinline__ void warp_mv(const double* __restrict__ A, int R, int C, int LR, const float2* __restrict__ xin,
+                                        int64_t xstride, int nv, float (&s)[RPL][NVB], float (&c)[RPL][NVB], int lane) {
+  constexpr int UB = (NVB <= 2) ? 8 : (NVB <= 4 ? 4 : 2);  // columns whose loads are issued together
   const int G = 32 / LR;
   const int g = lane / LR, rl = lane - g * LR;
-  for (int col = g; col < C; col += G) {
-    float xh[NVB], xl[NVB];
+  for (int col0 = g; col0 < C; col0 += UB * G) {
+    double a[UB][RPL];
+    float2 xv[UB][NVB];
 #pragma unroll
-    for (int v = 0; v < NVB; v++) {
-      const float2 t = (v < nv) ? xin[v * xstride + col] : make_float2(0.f, 0.f);
-      xh[v] = t.x;
-      xl[v] = t.y;
+    for (int u = 0; u < UB; u++) {
+      const int col = col0 + u * G;
+#pragma unroll
+      for (int r = 0; r < RPL; r++) {
+        const int row = rl + 32 * r;
+        a[u][r] = (col < C && row < R) ? __ldg(A + row + (int64_t)R * col) : 0.0;
+      }
+#pragma unroll
+      for (int v = 0; v < NVB; v++) xv[u][v] = (col < C && v < nv) ? xin[v * xstride + col] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int r = 0; r < RPL; r++) {
-      const int row = rl + 32 * r;
-      if (row < R) {
-        float ah, al;
-        split_f64(__ldg(A + row + (int64_t)R * col), ah, al);
+    for (int u = 0; u < UB; u++) {
 #pragma unroll
-        for (int v = 0; v < NVB; v++) df_fma(s[r][v], c[r][v], ah, al, xh[v], xl[v]);
+      for (int r = 0; r < RPL; r++) {
+        float ah, al;
+        split_f64(a[u][r], ah, al);
+#pragma unroll
+        for (int v = 0; v < NVB; v++) df_fma(s[r][v], c[r][v], ah, al, xv[u][v].x, xv[u][v].y);
       }
     }
   }
@@ -74,10 +80,10 @@ __device__ __forceinline__ void group_reduce(float (&s)[RPL][NVB], float (&c)[RP
   }
 }
 
-// write rows of a node vector (k x nv) from lanes of group 0; optionally add the old value
+// write a node's k x nv vector (stride kp per vector) from lanes of group 0; optionally add the old value
 template <int RPL, int NVB, bool ACCUM>
-__device__ __forceinline__ void store_node(float2* __restrict__ dst, int k, int LR, int nv,
-                                           float (&s)[RPL][NVB], float (&c)[RPL][NVB], int lane) {
+__device__ __forceinline__ void store_node(float2* __restrict__ dst, int k, int kp, int LR, int nv, float (&s)[RPL][NVB],
+                                           float (&c)[RPL][NVB], int lane) {
   if (lane >= LR) return;
 #pragma unroll
   for (int r = 0; r < RPL; r++) {
@@ -88,10 +94,10 @@ __device__ __forceinline__ void store_node(float2* __restrict__ dst, int k, int 
       if (v >= nv) continue;
       float ss = s[r][v], cc = c[r][v];
       if (ACCUM) {
-        const float2 old = dst[v * k + row];
+        const float2 old = dst[v * kp + row];
         df_add(ss, cc, old.x, old.y);
       }
-      dst[v * k + row] = df_norm(ss, cc);
+      dst[v * kp + row] = df_norm(ss, cc);
     }
   }
 }
@@ -100,34 +106,37 @@ __device__ __forceinline__ void store_node(float2* __restrict__ dst, int k, int 
 // one warp per leaf: x2(j) = split(x(j)); xhat_j = V_j^T x(j)   (Alg. 2, first step)
 template <int RPL, int NVB>
 __global__ void __launch_bounds__(kWarps * 32) k_project(const double* __restrict__ Vt, const int64_t* __restrict__ leaf_off,
-                                                       int k, int LR, int64_t leaves, int64_t leaf0,
-                                                       const double* __restrict__ x, int64_t ldx, int nv,
-                                                       float2* __restrict__ x2, int64_t ld2, float2* __restrict__ xhat) {
+                                                       const int64_t* __restrict__ xp_off, int k, int kp, int LR,
+                                                       int64_t leaves, int64_t leaf0, const double* __restrict__ x,
+                                                       int64_t ldx, int nv, float2* __restrict__ x2,
+                                                       float2* __restrict__ xhat) {
   __shared__ float2 xs[kWarps][NVB][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * kWarps + warp;
   if (j >= leaves) return;
   const int64_t off = leaf_off[j];
   const int sj = (int)(leaf_off[j + 1] - off);
+  const int spad = sj + (sj & 1);
+  float2* x2j = x2 + xp_off[j] * nv;
   for (int v = 0; v < nv; v++)
     for (int a = lane; a < sj; a += 32) {
       const float2 t = f64_to_df(x[v * ldx + off + a]);
       xs[warp][v][a] = t;
-      x2[v * ld2 + off + a] = t;
+      x2j[v * spad + a] = t;
     }
   __syncwarp();
   float s[RPL][NVB], c[RPL][NVB];
   acc_zero(s, c);
   warp_mv<RPL, NVB>(Vt + off * k, k, sj, LR, &xs[warp][0][0], 64, nv, s, c, lane);
   group_reduce(s, c, LR);
-  store_node<RPL, NVB, false>(xhat + (leaf0 + j) * nv * k, k, LR, nv, s, c, lane);
+  store_node<RPL, NVB, false>(xhat + (leaf0 + j) * nv * kp, k, kp, LR, nv, s, c, lane);
 }
 
 // ---------------------------------------------------------------- upsweep, one level
 // one warp per parent p on level l-1: xhat_p = F_c1^T xhat_c1 + F_c2^T xhat_c2   (Eq. 2)
 template <int RPL, int NVB>
-__global__ void __launch_bounds__(kWarps * 32) k_upsweep(const double* __restrict__ Ft, int k, int LR, int64_t pfirst,
-                                                       int64_t pcount, int nv, float2* __restrict__ xhat) {
+__global__ void __launch_bounds__(kWarps * 32) k_upsweep(const double* __restrict__ Ft, int k, int kp, int LR,
+                                                       int64_t pfirst, int64_t pcount, int nv, float2* __restrict__ xhat) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * kWarps + warp;
   if (t >= pcount) return;
@@ -136,87 +145,130 @@ __global__ void __launch_bounds__(kWarps * 32) k_upsweep(const double* __restric
   acc_zero(s, c);
   for (int ci = 1; ci <= 2; ci++) {
     const int64_t ch = 2 * p + ci;
-    warp_mv<RPL, NVB>(Ft + (ch - 1) * k * k, k, k, LR, xhat + ch * nv * k, k, nv, s, c, lane);
+    warp_mv<RPL, NVB>(Ft + (ch - 1) * k * k, k, k, LR, xhat + ch * nv * kp, kp, nv, s, c, lane);
   }
   group_reduce(s, c, LR);
-  store_node<RPL, NVB, false>(xhat + p * nv * k, k, LR, nv, s, c, lane);
+  store_node<RPL, NVB, false>(xhat + p * nv * kp, k, kp, LR, nv, s, c, lane);
 }
 
 // ---------------------------------------------------------------- coupling, all levels
-// one warp per node row i: yhat_i = sum_{b in row i} S_b xhat_{col(b)}   (Eq. 3, Alg. 3)
+// One warp per node row i: yhat_i = sum_{b in row i} S_b xhat_{col(b)}   (Eq. 3, Alg. 3)
+// k = 2H with H a power of two: lane = g * H + h owns rows 2h, 2h + 1 of every block,
+// read as one 16-byte load per column; column groups g = 0 .. G-1 (G = 32 / H)
+// take columns g, g + G, ... The row's blocks are walked in batches of CB
+// columns per lane, two batches in flight: the next batch's matrix and xhat
+// loads are issued before the current batch is multiplied. Blocks are padded
+// to kkp doubles. Every node row is written (zero when it has no blocks).
+template <int NVB, int CB>
+__global__ void __launch_bounds__(kWarps * 32) k_coupling(const double* __restrict__ S, int kkp,
+                                                        const int32_t* __restrict__ Srow, const int32_t* __restrict__ Scol,
+                                                        int k, int kp, int64_t n_nodes, int nv,
+                                                        const float2* __restrict__ xhat, float2* __restrict__ yhat) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * kWarps + warp;
+  if (i >= n_nodes) return;
+  const int H = k >> 1, G = 32 / H;
+  const int g = lane / H, h = lane - g * H;
+  const bool active = g < G;            // lanes beyond G * H idle
+  const int cpl = (k + G - 1) / G;      // columns per lane per block
+  const int ncb = (cpl + CB - 1) / CB;  // batches per block
+  const int32_t b0 = Srow[i];
+  const int nbatch = (Srow[i + 1] - b0) * ncb;
+  float s[2][NVB], c[2][NVB];
+#pragma unroll
+  for (int r = 0; r < 2; r++)
+#pragma unroll
+    for (int v = 0; v < NVB; v++) s[r][v] = c[r][v] = 0.f;
+
+  double2 a0[CB], a1[CB];
+  float2 x0[CB][NVB], x1[CB][NVB];
+  auto load = [&](int bt, double2(&a)[CB], float2(&xv)[CB][NVB]) {
+    const int b = bt / ncb, cb = bt - b * ncb;
+    const double* A = S + (int64_t)(b0 + b) * kkp;
+    const float2* X = xhat + (int64_t)__ldg(Scol + b0 + b) * nv * kp;
+#pragma unroll
+    for (int u = 0; u < CB; u++) {
+      const int col = g + G * (cb * CB + u);
+      const bool ok = active && col < k;
+      a[u] = ok ? __ldg(reinterpret_cast<const double2*>(A + 2 * h + k * col)) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int v = 0; v < NVB; v++) xv[u][v] = (ok && v < nv) ? __ldg(X + v * kp + col) : make_float2(0.f, 0.f);
+    }
+  };
+  auto compute = [&](const double2(&a)[CB], const float2(&xv)[CB][NVB]) {
+#pragma unroll
+    for (int u = 0; u < CB; u++) {
+      float h0, l0, h1, l1;
+      split_f64(a[u].x, h0, l0);
+      split_f64(a[u].y, h1, l1);
+#pragma unroll
+      for (int v = 0; v < NVB; v++) {
+        df_fma(s[0][v], c[0][v], h0, l0, xv[u][v].x, xv[u][v].y);
+        df_fma(s[1][v], c[1][v], h1, l1, xv[u][v].x, xv[u][v].y);
+      }
+    }
+  };
+  if (nbatch > 0) load(0, a0, x0);
+  for (int bt = 0; bt < nbatch; bt += 2) {
+    if (bt + 1 < nbatch) load(bt + 1, a1, x1);
+    compute(a0, x0);
+    if (bt + 2 < nbatch) load(bt + 2, a0, x0);
+    if (bt + 1 < nbatch) compute(a1, x1);
+  }
+  // sum the column groups (lanes h, h + H, ...)
+  for (int off = H; off < 32; off <<= 1) {
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+      for (int v = 0; v < NVB; v++) {
+        const float s2 = __shfl_xor_sync(0xFFFFFFFFu, s[r][v], off);
+        const float c2 = __shfl_xor_sync(0xFFFFFFFFu, c[r][v], off);
+        df_add(s[r][v], c[r][v], s2, c2);
+      }
+  }
+  if (g == 0) {
+    float2* dst = yhat + i * nv * kp;
+#pragma unroll
+    for (int v = 0; v < NVB; v++)
+      if (v < nv) {
+        if (2 * h < k) dst[v * kp + 2 * h] = df_norm(s[0][v], c[0][v]);
+        if (2 * h + 1 < k) dst[v * kp + 2 * h + 1] = df_norm(s[1][v], c[1][v]);
+      }
+  }
+}
+
+// Any other k: the generic row mapping of warp_mv, one block at a time.
 template <int RPL, int NVB>
-__global__ void __launch_bounds__(kWarps * 32) k_coupling(const double* __restrict__ S, const int32_t* __restrict__ Srow,
-                                                        const int32_t* __restrict__ Scol, int k, int LR, int64_t n_nodes,
-                                                        int nv, const float2* __restrict__ xhat, float2* __restrict__ yhat) {
+__global__ void __launch_bounds__(kWarps * 32) k_coupling_generic(const double* __restrict__ S, int kkp,
+                                                            const int32_t* __restrict__ Srow,
+                                                            const int32_t* __restrict__ Scol, int k, int kp, int LR,
+                                                            int64_t n_nodes, int nv, const float2* __restrict__ xhat,
+                                                            float2* __restrict__ yhat) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * kWarps + warp;
   if (i >= n_nodes) return;
   float s[RPL][NVB], c[RPL][NVB];
   acc_zero(s, c);
-  const int32_t b0 = Srow[i], b1 = Srow[i + 1];
-  for (int32_t b = b0; b < b1; b++)
-    warp_mv<RPL, NVB>(S + (int64_t)b * k * k, k, k, LR, xhat + (int64_t)Scol[b] * nv * k, k, nv, s, c, lane);
+  for (int32_t b = Srow[i]; b < Srow[i + 1]; b++)
+    warp_mv<RPL, NVB>(S + (int64_t)b * kkp, k, k, LR, xhat + (int64_t)Scol[b] * nv * kp, kp, nv, s, c, lane);
   group_reduce(s, c, LR);
-  store_node<RPL, NVB, false>(yhat + i * nv * k, k, LR, nv, s, c, lane);
+  store_node<RPL, NVB, false>(yhat + i * nv * kp, k, kp, LR, nv, s, c, lane);
 }
 
 // ---------------------------------------------------------------- downsweep, one level
 // one warp per node c on level l: yhat_c += E_c yhat_parent   (Eq. 5, Alg. 4)
 template <int RPL, int NVB>
-__global__ void __launch_bounds__(kWarps * 32) k_downsweep(const double* __restrict__ E, int k, int LR, int64_t cfirst,
-                                                         int64_t ccount, int nv, float2* __restrict__ yhat) {
+__global__ void __launch_bounds__(kWarps * 32) k_downsweep(const double* __restrict__ E, int k, int kp, int LR,
+                                                         int64_t cfirst, int64_t ccount, int nv, float2* __restrict__ yhat) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t = (int64_t)blockIdx.x * kWarps + warp;
   if (t >= ccount) return;
   const int64_t ch = cfirst + t, par = (ch - 1) / 2;
   float s[RPL][NVB], c[RPL][NVB];
   acc_zero(s, c);
-  warp_mv<RPL, NVB>(E + (ch - 1) * k * k, k, k, LR, yhat + par * nv * k, k, nv, s, c, lane);
+  warp_mv<RPL, NVB>(E + (ch - 1) * k * k, k, k, LR, yhat + par * nv * kp, kp, nv, s, c, lane);
   group_reduce(s, c, LR);
-  store_node<RPL, NVB, true>(yhat + ch * nv * k, k, LR, nv, s, c, lane);
-}
-
-// ---------------------------------------------------------------- dense near field + leaf expansion
-// one CTA per leaf row i: y(i) = U_i yhat_i + sum_j D_ij x(j)   (Eq. 4, Sec. 2.2)
-// Warps take the row's dense blocks round-robin and a quarter of U_i's columns
-// each; partial rows meet in shared memory. RPL rows per lane cover leaf sizes <= 32 * RPL.
-template <int RPL, int NVB>
-__global__ void __launch_bounds__(kWarps * 32) k_dense_expand(const double* __restrict__ Dval, const int64_t* __restrict__ Doff,
-                                                            const int32_t* __restrict__ Drow, const int32_t* __restrict__ Dcol,
-                                                            const int64_t* __restrict__ leaf_off, const double* __restrict__ U,
-                                                            int k, int64_t leaf0, const float2* __restrict__ x2, int64_t ld2,
-                                                            const float2* __restrict__ yhat, int nv, double* __restrict__ y,
-                                                            int64_t ldy) {
-  __shared__ float2 red[kWarps][NVB][32 * RPL];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = blockIdx.x;
-  const int64_t off = leaf_off[i];
-  const int si = (int)(leaf_off[i + 1] - off);
-  float s[RPL][NVB], c[RPL][NVB];
-  acc_zero(s, c);
-  const int32_t b0 = Drow[i], b1 = Drow[i + 1];
-  for (int32_t b = b0 + warp; b < b1; b += kWarps) {
-    const int32_t j = Dcol[b];
-    const int64_t offj = leaf_off[j];
-    const int sj = (int)(leaf_off[j + 1] - offj);
-    warp_mv<RPL, NVB>(Dval + Doff[b], si, sj, 32, x2 + offj, ld2, nv, s, c, lane);
-  }
-  const int nu0 = (k * warp) / kWarps, nu1 = (k * (warp + 1)) / kWarps;
-  if (nu1 > nu0)
-    warp_mv<RPL, NVB>(U + off * k + (int64_t)si * nu0, si, nu1 - nu0, 32, yhat + (leaf0 + i) * nv * k + nu0, k, nv, s, c,
-                      lane);
-#pragma unroll
-  for (int r = 0; r < RPL; r++)
-#pragma unroll
-    for (int v = 0; v < NVB; v++) red[warp][v][lane + 32 * r] = make_float2(s[r][v], c[r][v]);
-  __syncthreads();
-  for (int t = threadIdx.x; t < si * nv; t += blockDim.x) {
-    const int row = t % si, v = t / si;
-    float ss = 0.f, cc = 0.f;
-#pragma unroll
-    for (int w = 0; w < kWarps; w++) df_add(ss, cc, red[w][v][row].x, red[w][v][row].y);
-    y[v * ldy + off + row] = df_to_f64(ss, cc);
-  }
+  store_node<RPL, NVB, true>(yhat + ch * nv * kp, k, kp, LR, nv, s, c, lane);
 }
 
 }  // namespace h2

@@ -38,7 +38,7 @@ def to_dev(x):
 def gpu_matvec(h2, A, x, **kw):
     M = h2.H2Matrix.from_generator(A, check_cover=True, **kw)
     y = M.matvec(to_dev(x))
-    torch.cuda.synchronize()
+    M.check()
     out = y.cpu().numpy()
     M.close()
     return out
@@ -162,3 +162,21 @@ def test_full_size_2d_n1M(h2, nv):
     x = h2gen.vectors(400 + nv, A.n, nv)
     y = gpu_matvec(h2, A, x)
     assert oracle.rel_l2(y, oracle.matvec(A, x)) <= TOL
+
+
+def test_bounded_wait_reports_timeout(h2, c1):
+    """A withheld copy makes the dense kernel's consumers wait on a stage that never
+    fills; the bounded wait runs out (about 10 ms here), the kernel ends early and
+    h2_check reports H2_ERR_TIMEOUT. The context and the handle stay usable."""
+    M = h2.H2Matrix.from_generator(c1)
+    x_np = h2gen.vectors(313, c1.n, 1)
+    x = to_dev(x_np)
+    M.debug_withhold_copy(item=1, wait_budget_cycles=20_000_000)
+    M.matvec(x)
+    with pytest.raises(h2.H2Error) as ei:
+        M.check()
+    assert ei.value.status == h2.H2_ERR_TIMEOUT
+    y = M.matvec(x)
+    M.check()
+    assert oracle.rel_l2(y.cpu().numpy(), oracle.matvec(c1, x_np)) <= TOL
+    M.close()
