@@ -18,19 +18,26 @@
 
 namespace h2 {
 
-// |a| >= 2^-103 keeps both halves normal floats; smaller magnitudes (and zero)
-// become 0. h2_create rejects |a| >= 2^126, so the exponent never overflows.
-__device__ __forceinline__ void split_f64(double a, float& h, float& l) {
+// FP64 -> hi + lo (float pair) with integer ops: hi holds the leading 24
+// mantissa bits (truncated), lo the next 23, so |a - (hi + lo)| < 2^-46 |a|.
+// Requires 2^-103 <= |a| < 2^126 (both halves are then normal floats).
+__device__ __forceinline__ void split_f64_fast(double a, float& h, float& l) {
   const uint32_t hi = (uint32_t)__double2hiint(a);
   const uint32_t lo = (uint32_t)__double2loint(a);
   const uint32_t t = hi - 0x38000000u;                       // exponent bias 1023 -> 127
   const uint32_t u = __funnelshift_l(lo, t, 3);              // 20 + 3 mantissa bits
   const uint32_t hb = (u & 0x7FFFFFFFu) | (hi & 0x80000000u);
   const uint32_t fb = (hb - (23u << 23)) & 0xFF800000u;      // sign, exponent of hi - 23
-  const uint32_t r = (lo >> 6) & 0x7FFFFFu;                  // next 23 mantissa bits
-  const float hv = __uint_as_float(hb);
-  const float lv = __fsub_rn(__uint_as_float(fb | r), __uint_as_float(fb));
-  const bool ok = (hi & 0x7FFFFFFFu) >= 0x39800000u;         // biased exponent >= 920
+  const uint32_t r = (lo << 3) >> 9;                         // next 23 mantissa bits
+  h = __uint_as_float(hb);
+  l = __fsub_rn(__uint_as_float(fb | r), __uint_as_float(fb));
+}
+
+// Same for any finite |a| < 2^126: magnitudes below 2^-103 (and zero) become 0.
+__device__ __forceinline__ void split_f64(double a, float& h, float& l) {
+  float hv, lv;
+  split_f64_fast(a, hv, lv);
+  const bool ok = ((uint32_t)__double2hiint(a) & 0x7FFFFFFFu) >= 0x39800000u;  // biased exponent >= 920
   h = ok ? hv : 0.0f;
   l = ok ? lv : 0.0f;
 }
@@ -48,17 +55,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// (s, c) += (ah + al) * (xh + xl)
+// (s, c) += (ah + al) * (xh + xl). The small terms are gathered in t first,
+// so c sees one dependent add per product.
 __device__ __forceinline__ void df_fma(float& s, float& c, float ah, float al, float xh, float xl) {
   const float p = __fmul_rn(ah, xh);
   const float e = __fmaf_rn(ah, xh, -p);
-  c = __fmaf_rn(ah, xl, c);
-  c = __fmaf_rn(al, xh, c);
-  float t, err;
-  two_sum(s, p, t, err);
-  s = t;
-  c = __fadd_rn(c, e);
-  c = __fadd_rn(c, err);
+  float t = __fmaf_rn(ah, xl, e);
+  t = __fmaf_rn(al, xh, t);
+  float sn, err;
+  two_sum(s, p, sn, err);
+  s = sn;
+  c = __fadd_rn(c, __fadd_rn(t, err));
 }
 
 // (s1, c1) += (s2, c2)

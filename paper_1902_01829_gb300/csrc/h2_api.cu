@@ -69,6 +69,7 @@ struct h2_matrix_s {
   int32_t* Scol = nullptr;
   ItemList dense_items;
   bool pair_rows = false;  // k = 2^j (j >= 1): the coupling kernel reads row pairs
+  bool s_tiny = true;      // some coupling entry is zero or below 2^-103
   int* err = nullptr;      // device error word (bounded waits)
   float2* x2 = nullptr;    // split x, padded leaf layout, kPassVectors slots
   float2* xhat = nullptr;  // n_nodes x kPassVectors x kp
@@ -127,6 +128,14 @@ int level_of(int64_t node) {
   int l = 0;
   while (((int64_t)2 << l) - 1 <= node) l++;
   return l;
+}
+
+// true if some entry is zero or below 2^-103 in magnitude (the fast split needs 2^-103 <= |v|)
+bool has_tiny(const double* v, int64_t count) {
+  const double lim = std::ldexp(1.0, -103);
+  for (int64_t i = 0; i < count; i++)
+    if (!(std::fabs(v[i]) >= lim)) return true;
+  return false;
 }
 
 // values must be finite with |v| < 2^126 (the double-float split keeps the exponent in float range)
@@ -341,8 +350,12 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
   if (me == cudaSuccess) me = mark(h, st);
   if (h->pair_rows) {
     constexpr int CB = NVB <= 2 ? 4 : (NVB <= 4 ? 2 : 1);
-    k_coupling<NVB, CB><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, h->n_nodes, nv, h->xhat,
-                                                          h->yhat);
+    if (h->s_tiny)
+      k_coupling<NVB, CB, true><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, h->n_nodes, nv,
+                                                                  h->xhat, h->yhat);
+    else
+      k_coupling<NVB, CB, false><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, h->n_nodes, nv,
+                                                                   h->xhat, h->yhat);
   } else {
     k_coupling_generic<RPL_K, NVB><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, LR, h->n_nodes,
                                                                      nv, h->xhat, h->yhat);
@@ -480,7 +493,7 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
         it.shape = (unsigned)si | ((unsigned)sj << 8) | ((unsigned)even(sj) << 16) | (1u << 24);
         it.v_off = xp[j];
         it.row = (int)lo[i];
-        it.flags = 0;
+        it.flags = has_tiny(d->D_val + doff[b], doff[b + 1] - doff[b]) ? h2::kItemFlagSafe : 0;
         items.push_back(it);
         bytes += it.m_bytes + 8 * sj;
       }
@@ -490,7 +503,7 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
       it.shape = (unsigned)si | ((unsigned)k << 8) | ((unsigned)h->kp << 16) | (1u << 24);
       it.v_off = (h->leaf0 + i) * h->kp;
       it.row = (int)lo[i];
-      it.flags = h2::kItemFlagLast | h2::kItemFlagSrc1;
+      it.flags = h2::kItemFlagLast | h2::kItemFlagSrc1 | h2::kItemFlagSafe;
       items.push_back(it);
       row_bytes[i] = bytes + it.m_bytes + 8 * h->kp + 16 * si;
     }
@@ -517,6 +530,7 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
     if ((st = upload(h, &h->Srow, d->S_rowptr, h->n_nodes + 1)) != H2_OK) return st;
     if ((st = upload(h, &h->Scol, d->S_colidx, h->nS)) != H2_OK) return st;
     h->pair_rows = k >= 2 && k <= 64 && (k & (k - 1)) == 0;
+    h->s_tiny = h->nS > 0 && has_tiny(d->S_val, h->nS * kk);
   }
 
   if ((st = dalloc(h, &h->err, 1)) != H2_OK) return st;

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_upsweep(const double* __restric
 // columns per lane, two batches in flight: the next batch's matrix and xhat
 // loads are issued before the current batch is multiplied. Blocks are padded
 // to kkp doubles. Every node row is written (zero when it has no blocks).
-template <int NVB, int CB>
+// SAFE: some coupling entry is zero or below 2^-103 (zero-safe split).
+template <int NVB, int CB, bool SAFE>
 __global__ void __launch_bounds__(kWarps * 32) k_coupling(const double* __restrict__ S, int kkp,
                                                         const int32_t* __restrict__ Srow, const int32_t* __restrict__ Scol,
                                                         int k, int kp, int64_t n_nodes, int nv,
@@ -199,8 +200,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_coupling(const double* __restri
 #pragma unroll
     for (int u = 0; u < CB; u++) {
       float h0, l0, h1, l1;
-      split_f64(a[u].x, h0, l0);
-      split_f64(a[u].y, h1, l1);
+      if (SAFE) {
+        split_f64(a[u].x, h0, l0);
+        split_f64(a[u].y, h1, l1);
+      } else {
+        split_f64_fast(a[u].x, h0, l0);
+        split_f64_fast(a[u].y, h1, l1);
+      }
 #pragma unroll
       for (int v = 0; v < NVB; v++) {
         df_fma(s[0][v], c[0][v], h0, l0, xv[u][v].x, xv[u][v].y);

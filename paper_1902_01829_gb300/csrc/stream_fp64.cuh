@@ -28,13 +28,14 @@ struct __align__(16) StreamItem {
   unsigned shape;   // R | C << 8 | vstride << 16 | nb << 24   (nb = 1)
   long long v_off;  // vector chunk offset, in float2 per vector slot
   int row;          // first point of the row leaf (y offset)
-  int flags;        // bit 0: last item of its row; bit 1: vector chunk from the second source (yhat)
+  int flags;        // bit 0: last item of its row; bit 1: vector chunk from the second source (yhat);
+                    // bit 2: the block holds zeros or magnitudes below 2^-103 (zero-safe split needed)
 };
 
 constexpr int kStageHeader = 128;
 constexpr int kStageMat = 32768;
 constexpr int kSmemLimit = 232448;  // opt-in shared memory per CTA on sm_103a
-constexpr int kItemFlagLast = 1, kItemFlagSrc1 = 2;
+constexpr int kItemFlagLast = 1, kItemFlagSrc1 = 2, kItemFlagSafe = 4;
 
 // a stage holds one item: header, matrix block (<= 64 x 64 doubles), vector chunk (<= 64 x NVB float2)
 __host__ __device__ constexpr int stage_vec_bytes(int nvb) { return 512 * nvb; }
@@ -50,7 +51,7 @@ __host__ __device__ constexpr int stream_smem_bytes(int nvb, int cw) {
 }
 // consumer warps per CTA for a vector-slot count (more warps hide more latency;
 // wide vector slots need the registers of fewer warps)
-__host__ __device__ constexpr int dense_consumer_warps(int nvb) { return nvb <= 2 ? 16 : 8; }
+__host__ __device__ constexpr int dense_consumer_warps(int nvb) { return 8; }
 
 struct StreamParams {
   const StreamItem* items;
@@ -218,7 +219,25 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream(StreamParams 
     const double* A = reinterpret_cast<const double*>(stage + kStageHeader);
     const float2* X = reinterpret_cast<const float2*>(stage + kStageHeader + kStageMat);
     const int c0 = (C * warp) / CW, c1 = (C * (warp + 1)) / CW;
-    if (r0 < R) {
+    if (R == 64 && C == 64 && !(flags & kItemFlagSafe)) {
+      // full block without tiny entries: fixed strides, fast split
+      constexpr int CPW = 64 / CW;
+      const double* Ab = A + r0 + 64 * c0;
+      const float2* Xb = X + c0;
+#pragma unroll
+      for (int u = 0; u < CPW; u++) {
+        const double2 a = *reinterpret_cast<const double2*>(Ab + 64 * u);
+        float h0, l0, h1, l1;
+        split_f64_fast(a.x, h0, l0);
+        split_f64_fast(a.y, h1, l1);
+#pragma unroll
+        for (int v = 0; v < NVB; v++) {
+          const float2 xv = (v < nv) ? Xb[v * 64 + u] : make_float2(0.f, 0.f);
+          df_fma(s[u % SETS][0][v], c[u % SETS][0][v], h0, l0, xv.x, xv.y);
+          df_fma(s[u % SETS][1][v], c[u % SETS][1][v], h1, l1, xv.x, xv.y);
+        }
+      }
+    } else if (r0 < R) {
       const bool even = (R & 1) == 0;
       for (int col0 = c0; col0 < c1; col0 += SETS) {
 #pragma unroll
