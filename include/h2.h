@@ -169,11 +169,11 @@ h2_status h2_info(h2_handle h, int64_t info[8]);
  * phases; h2_profile_read waits for the last recorded event, returns the
  * summed milliseconds of each phase since profiling was enabled (or last
  * read), the number of kernel launches, and starts a new sum.
- * Phases: 0 leaf projection, 1 upsweep, 2 coupling, 3 downsweep,
- * 4 dense blocks + leaf expansion. Disabled by default; enabling costs one
+ * Phases: 0 leaf projection + upsweep, 1 coupling, 2 downsweep,
+ * 3 dense blocks + leaf expansion. Disabled by default; enabling costs one
  * event record per phase boundary.
  */
-#define H2_NPHASES 5
+#define H2_NPHASES 4
 h2_status h2_profile(h2_handle h, int32_t enable);
 h2_status h2_profile_read(h2_handle h, double ms[H2_NPHASES], int64_t* launches);
 

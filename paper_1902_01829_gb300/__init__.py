@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
 # every symbol include/h2.h declares
 EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
            "h2_profile_read", "h2_destroy", "h2_last_error"]
-PHASES = ["project", "upsweep", "coupling", "downsweep", "dense_expand"]
+PHASES = ["upsweep", "coupling", "downsweep", "dense_expand"]
 
 
 class H2Error(RuntimeError):

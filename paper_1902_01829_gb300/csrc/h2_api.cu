@@ -71,6 +71,8 @@ struct h2_matrix_s {
   bool pair_rows = false;  // k = 2^j (j >= 1): the coupling kernel reads row pairs
   bool s_tiny = true;      // some coupling entry is zero or below 2^-103
   int* err = nullptr;      // device error word (bounded waits)
+  int* ticket = nullptr;   // upsweep climb counters, one per node
+  int tree_L = 0;          // subtree root level of the fused tree kernels
   float2* x2 = nullptr;    // split x, padded leaf layout, kPassVectors slots
   float2* xhat = nullptr;  // n_nodes x kPassVectors x kp
   float2* yhat = nullptr;
@@ -339,14 +341,27 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
   constexpr int CW = dense_consumer_warps(NVB);
   constexpr int smem = stream_smem_bytes(NVB, CW);
   const int kkp = (int)even((int64_t)k * k);
+  TreeParams T{};
+  T.Vt = h->Vt;
+  T.Ft = h->Ft;
+  T.E = h->E;
+  T.leaf_off = h->leaf_off;
+  T.xp_off = h->xp_off;
+  T.x = x;
+  T.ldx = ldx;
+  T.x2 = h->x2;
+  T.xhat = h->xhat;
+  T.yhat = h->yhat;
+  T.ticket = h->ticket;
+  T.k = k;
+  T.kp = kp;
+  T.LR = LR;
+  T.q = h->q;
+  T.L = h->tree_L;
+  T.nv = nv;
+  const unsigned tree_grid = 1u << h->tree_L, tree_threads = kTreeWarps * 32;
   cudaError_t me = mark(h, st);
-  k_project<RPL_K, NVB><<<grid(h->leaves), wb, 0, st>>>(h->Vt, h->leaf_off, h->xp_off, k, kp, LR, h->leaves, h->leaf0, x,
-                                                         ldx, nv, h->x2, h->xhat);
-  if (me == cudaSuccess) me = mark(h, st);
-  for (int l = h->q; l >= 1; l--) {
-    const int64_t pfirst = ((int64_t)1 << (l - 1)) - 1, pcount = (int64_t)1 << (l - 1);
-    k_upsweep<RPL_K, NVB><<<grid(pcount), wb, 0, st>>>(h->Ft, k, kp, LR, pfirst, pcount, nv, h->xhat);
-  }
+  k_upsweep_tree<RPL_K, NVB><<<tree_grid, tree_threads, 0, st>>>(T);
   if (me == cudaSuccess) me = mark(h, st);
   if (h->pair_rows) {
     constexpr int CB = NVB <= 2 ? 4 : (NVB <= 4 ? 2 : 1);
@@ -361,10 +376,7 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
                                                                      nv, h->xhat, h->yhat);
   }
   if (me == cudaSuccess) me = mark(h, st);
-  for (int l = 1; l <= h->q; l++) {
-    const int64_t cfirst = ((int64_t)1 << l) - 1, ccount = (int64_t)1 << l;
-    k_downsweep<RPL_K, NVB><<<grid(ccount), wb, 0, st>>>(h->E, k, kp, LR, cfirst, ccount, nv, h->yhat);
-  }
+  k_downsweep_tree<RPL_K, NVB><<<tree_grid, tree_threads, 0, st>>>(T);
   if (me == cudaSuccess) me = mark(h, st);
   StreamParams P{};
   P.items = h->dense_items.items;
@@ -384,7 +396,7 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
     h->budget = kWaitBudget;
   }
   if (me == cudaSuccess) me = mark(h, st);
-  h->launches += 2 * h->q + 3;
+  h->launches += 4;
   if (me != cudaSuccess) return fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(H2_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
@@ -535,6 +547,12 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
 
   if ((st = dalloc(h, &h->err, 1)) != H2_OK) return st;
   CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
+  if ((st = dalloc(h, &h->ticket, h->n_nodes)) != H2_OK) return st;
+  CUDA_TRY(cudaMemset(h->ticket, 0, (size_t)h->n_nodes * sizeof(int)));
+  // subtree roots of the fused tree kernels: at least two CTAs per SM when the tree is deep enough
+  int lmax = 0;
+  while (((int64_t)1 << lmax) < 2 * (int64_t)h->grid) lmax++;
+  h->tree_L = std::min(h->q, lmax);
   if ((st = dalloc(h, &h->x2, xp[h->leaves] * kPassVectors)) != H2_OK) return st;
   if ((st = dalloc(h, &h->xhat, h->n_nodes * kPassVectors * h->kp)) != H2_OK) return st;
   if ((st = dalloc(h, &h->yhat, h->n_nodes * kPassVectors * h->kp)) != H2_OK) return st;

@@ -24,9 +24,9 @@ constexpr int kWarps = 4;  // warps per CTA for the per-node kernels
 // Row mapping of a warp over an R-row block: lane = g * LR + rl owns rows
 // rl + 32 r (r < RPL) and columns col = g, g + G, ... with G = 32 / LR groups.
 // RPL = 2 requires LR = 32 (R <= 64); RPL = 1 allows LR = 1 .. 32 (R <= LR).
-template <int RPL, int NVB>
-__device__ __forceinline__ void warp_mv(const double* __restrict__ A, int R, int C, int LR, const float2* __restrict__ xin,
-                                        int64_t xstride, int nv, float (&s)[RPL][NVB], float (&c)[RPL][NVB], int lane) {
+template <int RPL, int NVB, bool CG = false>
+__device__ __forceinline__ void warp_mv_impl(const double* __restrict__ A, int R, int C, int LR, const float2* xin,
+                                             int64_t xstride, int nv, float (&s)[RPL][NVB], float (&c)[RPL][NVB], int lane) {
   constexpr int UB = (NVB <= 2) ? 8 : (NVB <= 4 ? 4 : 2);  // columns whose loads are issued together
   const int G = 32 / LR;
   const int g = lane / LR, rl = lane - g * LR;
@@ -42,7 +42,9 @@ __device__ __forceinline__ void warp_mv(const double* __restrict__ A, int R, int
         a[u][r] = (col < C && row < R) ? __ldg(A + row + (int64_t)R * col) : 0.0;
       }
 #pragma unroll
-      for (int v = 0; v < NVB; v++) xv[u][v] = (col < C && v < nv) ? xin[v * xstride + col] : make_float2(0.f, 0.f);
+      for (int v = 0; v < NVB; v++)
+        xv[u][v] = (col < C && v < nv) ? (CG ? __ldcg(xin + v * xstride + col) : xin[v * xstride + col])
+                                       : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < UB; u++) {
@@ -55,6 +57,13 @@ __device__ __forceinline__ void warp_mv(const double* __restrict__ A, int R, int
       }
     }
   }
+}
+
+// xin is read with plain loads: it may have been written earlier in the same kernel by this CTA
+template <int RPL, int NVB>
+__device__ __forceinline__ void warp_mv(const double* __restrict__ A, int R, int C, int LR, const float2* xin, int64_t xstride,
+                                        int nv, float (&s)[RPL][NVB], float (&c)[RPL][NVB], int lane) {
+  warp_mv_impl<RPL, NVB, false>(A, R, C, LR, xin, xstride, nv, s, c, lane);
 }
 
 template <int RPL, int NVB>
@@ -102,53 +111,158 @@ __device__ __forceinline__ void store_node(float2* __restrict__ dst, int k, int 
   }
 }
 
-// ---------------------------------------------------------------- leaf projection
-// one warp per leaf: x2(j) = split(x(j)); xhat_j = V_j^T x(j)   (Alg. 2, first step)
+// ---------------------------------------------------------------- tree phases, one launch each
+// CTA b owns the subtree rooted at node 2^L - 1 + b on level L (its T = q - L
+// levels below hold leaves [b 2^T, (b + 1) 2^T)). One warp computes one node.
+constexpr int kTreeWarps = 8;
+
+struct TreeParams {
+  const double* Vt;        // leaf j: k x size_j (V_j^T)
+  const double* Ft;        // node h >= 1: F_h^T
+  const double* E;         // node h >= 1: E_h
+  const int64_t* leaf_off;
+  const int64_t* xp_off;
+  const double* x;         // pass input, ldx
+  int64_t ldx;
+  float2* x2;              // split x (padded leaf layout)
+  float2* xhat;
+  float2* yhat;
+  int* ticket;             // one counter per node above level L, zero between products
+  int k, kp, LR, q, L, nv;
+};
+
+// leaf projection of leaf j: x2(j) = split(x(j)); xhat_j = V_j^T x(j)   (Alg. 2, first step)
 template <int RPL, int NVB>
-__global__ void __launch_bounds__(kWarps * 32) k_project(const double* __restrict__ Vt, const int64_t* __restrict__ leaf_off,
-                                                       const int64_t* __restrict__ xp_off, int k, int kp, int LR,
-                                                       int64_t leaves, int64_t leaf0, const double* __restrict__ x,
-                                                       int64_t ldx, int nv, float2* __restrict__ x2,
-                                                       float2* __restrict__ xhat) {
-  __shared__ float2 xs[kWarps][NVB][64];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t j = (int64_t)blockIdx.x * kWarps + warp;
-  if (j >= leaves) return;
-  const int64_t off = leaf_off[j];
-  const int sj = (int)(leaf_off[j + 1] - off);
+__device__ __forceinline__ void project_leaf(const TreeParams& P, int64_t j, int lane) {
+  const int64_t leaf0 = ((int64_t)1 << P.q) - 1;
+  const int64_t off = P.leaf_off[j];
+  const int sj = (int)(P.leaf_off[j + 1] - off);
   const int spad = sj + (sj & 1);
-  float2* x2j = x2 + xp_off[j] * nv;
-  for (int v = 0; v < nv; v++)
-    for (int a = lane; a < sj; a += 32) {
-      const float2 t = f64_to_df(x[v * ldx + off + a]);
-      xs[warp][v][a] = t;
-      x2j[v * spad + a] = t;
-    }
+  float2* x2j = P.x2 + P.xp_off[j] * P.nv;
+  for (int v = 0; v < P.nv; v++)
+    for (int a = lane; a < sj; a += 32) x2j[v * spad + a] = f64_to_df(P.x[v * P.ldx + off + a]);
   __syncwarp();
   float s[RPL][NVB], c[RPL][NVB];
   acc_zero(s, c);
-  warp_mv<RPL, NVB>(Vt + off * k, k, sj, LR, &xs[warp][0][0], 64, nv, s, c, lane);
-  group_reduce(s, c, LR);
-  store_node<RPL, NVB, false>(xhat + (leaf0 + j) * nv * kp, k, kp, LR, nv, s, c, lane);
+  warp_mv<RPL, NVB>(P.Vt + off * P.k, P.k, sj, P.LR, x2j, spad, P.nv, s, c, lane);
+  group_reduce(s, c, P.LR);
+  store_node<RPL, NVB, false>(P.xhat + (leaf0 + j) * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, s, c, lane);
 }
 
-// ---------------------------------------------------------------- upsweep, one level
-// one warp per parent p on level l-1: xhat_p = F_c1^T xhat_c1 + F_c2^T xhat_c2   (Eq. 2)
-template <int RPL, int NVB>
-__global__ void __launch_bounds__(kWarps * 32) k_upsweep(const double* __restrict__ Ft, int k, int kp, int LR,
-                                                       int64_t pfirst, int64_t pcount, int nv, float2* __restrict__ xhat) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * kWarps + warp;
-  if (t >= pcount) return;
-  const int64_t p = pfirst + t;
+// Eq. 2 at parent p: xhat_p = F_c1^T xhat_c1 + F_c2^T xhat_c2 (CG: read the children through L2)
+template <int RPL, int NVB, bool CG>
+__device__ __forceinline__ void up_node(const TreeParams& P, int64_t p, int lane) {
   float s[RPL][NVB], c[RPL][NVB];
   acc_zero(s, c);
   for (int ci = 1; ci <= 2; ci++) {
     const int64_t ch = 2 * p + ci;
-    warp_mv<RPL, NVB>(Ft + (ch - 1) * k * k, k, k, LR, xhat + ch * nv * kp, kp, nv, s, c, lane);
+    warp_mv_impl<RPL, NVB, CG>(P.Ft + (ch - 1) * P.k * P.k, P.k, P.k, P.LR, P.xhat + ch * P.nv * P.kp, P.kp, P.nv, s, c,
+                               lane);
   }
-  group_reduce(s, c, LR);
-  store_node<RPL, NVB, false>(xhat + p * nv * kp, k, kp, LR, nv, s, c, lane);
+  group_reduce(s, c, P.LR);
+  store_node<RPL, NVB, false>(P.xhat + p * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, s, c, lane);
+}
+
+// Leaf projection and the whole upsweep (Alg. 2, Eq. 2) in one launch. Inside
+// a subtree the levels are separated by __syncthreads. Above level L, the
+// second CTA of a sibling pair to finish (atomic ticket) computes the parent,
+// so the climb needs no waiting: a CTA that arrives first simply stops.
+template <int RPL, int NVB>
+__global__ void __launch_bounds__(kTreeWarps * 32) k_upsweep_tree(TreeParams P) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int T = P.q - P.L;
+  const int64_t sub = blockIdx.x;
+  for (int64_t t = warp; t < ((int64_t)1 << T); t += kTreeWarps) project_leaf<RPL, NVB>(P, (sub << T) + t, lane);
+  __syncthreads();
+  for (int lvl = P.q - 1; lvl >= P.L; lvl--) {
+    const int64_t node0 = ((int64_t)1 << lvl) - 1 + (sub << (lvl - P.L));
+    for (int64_t t = warp; t < ((int64_t)1 << (lvl - P.L)); t += kTreeWarps) up_node<RPL, NVB, false>(P, node0 + t, lane);
+    __syncthreads();
+  }
+  __threadfence();  // every writer orders its xhat stores before the ticket below
+  __syncthreads();
+  if (warp != 0) return;
+  int64_t node = ((int64_t)1 << P.L) - 1 + sub;
+  while (node > 0) {
+    const int64_t par = (node - 1) / 2;
+    int second = 0;
+    if (lane == 0) {
+      second = atomicAdd(P.ticket + par, 1) == 1;
+      if (second) P.ticket[par] = 0;  // both arrivals are in: reset for the next product
+    }
+    second = __shfl_sync(0xFFFFFFFFu, second, 0);
+    if (!second) break;
+    __threadfence();  // order the sibling's xhat (published before its ticket) before our reads
+    up_node<RPL, NVB, true>(P, par, lane);
+    __threadfence();
+    __syncwarp();
+    node = par;
+  }
+}
+
+// Eq. 5 at node c: yhat_c += E_c yhat_parent (parent given explicitly)
+template <int RPL, int NVB>
+__device__ __forceinline__ void down_node(const TreeParams& P, int64_t ch, const float2* ypar, int lane) {
+  float s[RPL][NVB], c[RPL][NVB];
+  acc_zero(s, c);
+  warp_mv<RPL, NVB>(P.E + (ch - 1) * P.k * P.k, P.k, P.k, P.LR, ypar, P.kp, P.nv, s, c, lane);
+  group_reduce(s, c, P.LR);
+  store_node<RPL, NVB, true>(P.yhat + ch * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, s, c, lane);
+}
+
+// The whole downsweep (Alg. 4, Eq. 5) in one launch. Warp 0 first carries the
+// parents' sums from the root down the path to this CTA's subtree root (the
+// path's nodes are shared with other CTAs, so their partial sums live only in
+// this CTA's shared memory; only the subtree root is written back). Then the
+// subtree is swept top-down, levels separated by __syncthreads.
+template <int RPL, int NVB>
+__global__ void __launch_bounds__(kTreeWarps * 32) k_downsweep_tree(TreeParams P) {
+  __shared__ float2 path[2][NVB][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t sub = blockIdx.x;
+  const int64_t root = ((int64_t)1 << P.L) - 1 + sub;
+  if (warp == 0 && P.L > 0) {
+    // path nodes a_0 = 0, ..., a_L = root: a_l = (root + 1) >> (L - l) minus 1
+    int cur = 0;
+    for (int v = 0; v < P.nv; v++)
+      for (int r = lane; r < P.k; r += 32) path[cur][v][r] = P.yhat[(int64_t)v * P.kp + r];  // node 0
+    __syncwarp();
+    for (int l = 1; l <= P.L; l++) {
+      const int64_t a = ((root + 1) >> (P.L - l)) - 1;
+      float s[RPL][NVB], c[RPL][NVB];
+      acc_zero(s, c);
+      warp_mv<RPL, NVB>(P.E + (a - 1) * P.k * P.k, P.k, P.k, P.LR, &path[cur][0][0], 64, P.nv, s, c, lane);
+      group_reduce(s, c, P.LR);
+      if (lane < P.LR) {
+#pragma unroll
+        for (int rr = 0; rr < RPL; rr++) {
+          const int row = lane + 32 * rr;
+          if (row >= P.k) continue;
+#pragma unroll
+          for (int v = 0; v < NVB; v++) {
+            if (v >= P.nv) continue;
+            float ss = s[rr][v], cc = c[rr][v];
+            const float2 own = P.yhat[(a * P.nv + v) * P.kp + row];
+            df_add(ss, cc, own.x, own.y);
+            const float2 val = df_norm(ss, cc);
+            if (l == P.L) P.yhat[(a * P.nv + v) * P.kp + row] = val;
+            else path[cur ^ 1][v][row] = val;
+          }
+        }
+      }
+      __syncwarp();
+      cur ^= 1;
+    }
+  }
+  __syncthreads();
+  for (int lvl = P.L + 1; lvl <= P.q; lvl++) {
+    const int64_t node0 = ((int64_t)1 << lvl) - 1 + (sub << (lvl - P.L));
+    for (int64_t t = warp; t < ((int64_t)1 << (lvl - P.L)); t += kTreeWarps) {
+      const int64_t ch = node0 + t;
+      down_node<RPL, NVB>(P, ch, P.yhat + ((ch - 1) / 2) * P.nv * P.kp, lane);
+    }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------- coupling, all levels
@@ -259,22 +373,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_coupling_generic(const double* 
     warp_mv<RPL, NVB>(S + (int64_t)b * kkp, k, k, LR, xhat + (int64_t)Scol[b] * nv * kp, kp, nv, s, c, lane);
   group_reduce(s, c, LR);
   store_node<RPL, NVB, false>(yhat + i * nv * kp, k, kp, LR, nv, s, c, lane);
-}
-
-// ---------------------------------------------------------------- downsweep, one level
-// one warp per node c on level l: yhat_c += E_c yhat_parent   (Eq. 5, Alg. 4)
-template <int RPL, int NVB>
-__global__ void __launch_bounds__(kWarps * 32) k_downsweep(const double* __restrict__ E, int k, int kp, int LR,
-                                                         int64_t cfirst, int64_t ccount, int nv, float2* __restrict__ yhat) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t t = (int64_t)blockIdx.x * kWarps + warp;
-  if (t >= ccount) return;
-  const int64_t ch = cfirst + t, par = (ch - 1) / 2;
-  float s[RPL][NVB], c[RPL][NVB];
-  acc_zero(s, c);
-  warp_mv<RPL, NVB>(E + (ch - 1) * k * k, k, k, LR, yhat + par * nv * kp, kp, nv, s, c, lane);
-  group_reduce(s, c, LR);
-  store_node<RPL, NVB, true>(yhat + ch * nv * kp, k, kp, LR, nv, s, c, lane);
 }
 
 }  // namespace h2
