@@ -222,9 +222,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream(StreamParams 
     if (R == 64 && C == 64 && !(flags & kItemFlagSafe)) {
       // full block without tiny entries: fixed strides, fast split
       constexpr int CPW = 64 / CW;
+      constexpr int UNR = NVB >= 4 ? 2 : CPW;  // wide vector slots: keep the loop body small
       const double* Ab = A + r0 + 64 * c0;
       const float2* Xb = X + c0;
-#pragma unroll
+#pragma unroll UNR
       for (int u = 0; u < CPW; u++) {
         const double2 a = *reinterpret_cast<const double2*>(Ab + 64 * u);
         float h0, l0, h1, l1;
