@@ -177,6 +177,34 @@ h2_status h2_info(h2_handle h, int64_t info[8]);
 h2_status h2_profile(h2_handle h, int32_t enable);
 h2_status h2_profile_read(h2_handle h, double ms[H2_NPHASES], int64_t* launches);
 
+/*
+ * y = A^H x without allocating anything. (The paper has no counterpart: this
+ * serves callers that may not allocate device memory, e.g. code inside a
+ * host framework that owns all device memory through its own allocator, or
+ * code on a latency-critical path where cudaMalloc / cudaFree could
+ * synchronize the device.)
+ *   d               the matrix in the h2_desc format above, but every array
+ *                   pointer is DEVICE memory owned by the caller; the
+ *                   structure is not validated (build it as for h2_create)
+ *   n_dense_blocks  D_rowptr[2^q], the number of dense blocks
+ *   x, y            device FP64, n x nv column-major (ldx, ldy >= n); y is
+ *                   overwritten; x and y must not overlap
+ * The working memory is one static 16 MiB device array in the library, held
+ * by every GPU that loads it until the process exits. The call is rejected
+ * with H2_ERR_UNSUPPORTED unless
+ *   2 * (2^(q+1) - 1) * nv * k * 8 + (n_dense_blocks + 1) * 8 <= 16 MiB.
+ * Every call shares that array; each word is written before it is read in
+ * the same call, so nothing carries over, but calls that overlap on the GPU
+ * (different streams, different threads) race and corrupt each other.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. One single-CTA kernel does all phases: it is
+ * meant for small matrices, not for speed. FP64 storage only. Errors:
+ * H2_ERR_INVALID, H2_ERR_UNSUPPORTED, H2_ERR_CUDA; message via h2_last_error.
+ */
+h2_status h2_matvec_static(const h2_desc* d, int64_t n_dense_blocks, int32_t nv, const double* x, int64_t ldx, double* y,
+                           int64_t ldy, void* stream);
+
 /* Free all device memory of the handle (synchronizes the device first). NULL is a no-op. */
 h2_status h2_destroy(h2_handle h);
 

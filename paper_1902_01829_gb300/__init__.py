@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
 
 # every symbol include/h2.h declares
 EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
-           "h2_profile_read", "h2_destroy", "h2_last_error"]
+           "h2_profile_read", "h2_matvec_static", "h2_destroy", "h2_last_error"]
 PHASES = ["upsweep", "coupling", "downsweep", "dense_expand"]
 
 
@@ -54,11 +54,12 @@ def _load():
     lib.h2_destroy.argtypes = [vp]
     lib.h2_profile.argtypes = [vp, i32]
     lib.h2_check.argtypes = [vp, vp]
+    lib.h2_matvec_static.argtypes = [ctypes.POINTER(h2_desc), i64, i32, vp, i64, vp, i64, vp]
     lib.h2_debug_withhold_copy.argtypes = [vp, i32, i64]
     lib.h2_profile_read.argtypes = [vp, vp, vp]
     lib.h2_last_error.restype = ctypes.c_char_p
     for name in ("h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
-                 "h2_profile_read", "h2_destroy"):
+                 "h2_profile_read", "h2_matvec_static", "h2_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -184,3 +185,28 @@ class H2Matrix:
             self.close()
         except Exception:
             pass
+
+
+def matvec_static(n, depth, rank, leaf_offset, U, E, S_rowptr, S_colidx, S_val, D_rowptr, D_colidx, D_val, x, y,
+                  V=None, F=None, stream=None):
+    """y = A^H x through h2_matvec_static, which allocates nothing.
+
+    For callers that may not allocate device memory: every array is a torch
+    CUDA tensor the caller already owns (int64 leaf_offset, int32 index arrays,
+    float64 values); x and y are (n, nv) column-major float64 CUDA tensors.
+    The library's only working memory is a static 16 MiB device array.
+    """
+    sym = V is None and F is None
+    d = h2_desc(n=int(n), depth=int(depth), rank=int(rank), symmetric=1 if sym else 0, storage=STORAGE["fp64"],
+                check_cover=0, leaf_offset=_ptr(leaf_offset), U=_ptr(U), V=_ptr(V), E=_ptr(E), F=_ptr(F),
+                S_rowptr=_ptr(S_rowptr), S_colidx=_ptr(S_colidx), S_val=_ptr(S_val), D_rowptr=_ptr(D_rowptr),
+                D_colidx=_ptr(D_colidx), D_val=_ptr(D_val))
+    X = x.unsqueeze(1) if x.dim() == 1 else x
+    Y = y.unsqueeze(1) if y.dim() == 1 else y
+    assert X.stride(0) == 1 and Y.stride(0) == 1
+    nv = X.shape[1]
+    ldx = X.stride(1) if nv > 1 else int(n)
+    ldy = Y.stride(1) if nv > 1 else int(n)
+    _check(_lib.h2_matvec_static(ctypes.byref(d), int(D_colidx.numel()), nv, _ptr(X), ldx, _ptr(Y), ldy,
+                                 _stream_ptr(stream)))
+    return y

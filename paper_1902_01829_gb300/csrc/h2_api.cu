@@ -53,6 +53,8 @@ struct ItemList {
 
 }  // namespace
 
+void h2_internal_set_error(const char* msg) { g_err = msg; }
+
 struct h2_matrix_s {
   int64_t n = 0, leaves = 0, n_nodes = 0, leaf0 = 0, nS = 0, nD = 0, nDval = 0;
   int q = 0, k = 0, kp = 0, m_max = 0, lr = 32, grid = 0;
