@@ -44,10 +44,21 @@ typedef enum {
   H2_ERR_TIMEOUT = 5       /* a bounded device-side wait ran out */
 } h2_status;
 
-/* How h2_create stores the matrix on the device. */
+/*
+ * How h2_create stores the matrix on the device.
+ * The scaled forms store every block (each U_i, V_j, E_c, F_c, S_ij, D_ij)
+ * as 16-bit values q with one FP32 scale sigma per block, a' = sigma * q;
+ * products accumulate in FP32. With m = max |a| over the block:
+ *   fp16, bf16: sigma = fl32(m),         q = round-to-nearest-even(a / sigma)
+ *   int16:      sigma = fl32(m / 32767), q = clamp(rint(a / sigma), -32767, 32767)
+ * (a / sigma evaluated in FP64).
+ */
 typedef enum {
-  H2_FP64 = 0  /* plain form: FP64 storage; products in double-float
-                  (pairs of FP32 with error-free transformations, 46+ bits) */
+  H2_FP64 = 0,          /* plain form: FP64 storage; products in double-float
+                           (pairs of FP32 with error-free transformations, 46+ bits) */
+  H2_FP16_SCALED = 2,   /* IEEE binary16 codes + per-block FP32 scale, FP32 arithmetic */
+  H2_BF16_SCALED = 3,   /* bfloat16 codes + per-block FP32 scale, FP32 arithmetic */
+  H2_INT16_SCALED = 4   /* int16 codes + per-block FP32 scale, FP32 arithmetic */
 } h2_storage;
 
 typedef struct h2_matrix_s* h2_handle;
@@ -79,6 +90,10 @@ typedef struct h2_matrix_s* h2_handle;
  *   check_cover  nonzero: also verify that the coupling and dense blocks
  *                together cover every (row leaf, column leaf) pair exactly
  *                once (O(leaves * (q * row length)) host work)
+ *   bases_fp32   scaled forms only: keep U, V, E and F as FP32 entries (S and
+ *                D stay 16-bit). The bases and transfers are about 1% of the
+ *                entries but their rounding errors compound along the tree's
+ *                transfer chains, so this cuts the storage error several-fold.
  */
 typedef struct {
   int64_t n;
@@ -98,6 +113,7 @@ typedef struct {
   const int32_t* D_colidx;
   const double* D_val;
   int32_t check_cover;
+  int32_t bases_fp32;
 } h2_desc;
 
 /*
@@ -155,7 +171,8 @@ h2_status h2_debug_withhold_copy(h2_handle h, int32_t item, int64_t wait_budget_
  * Sizes of the stored representation.
  *   info[0]  paper_bytes: bytes of U, V, E, F, S and D as streamed by one
  *            single-vector product (V and F counted even when aliased to U and
- *            E, since each is read in its own phase; Sec. 4.6 metric)
+ *            E, since each is read in its own phase; Sec. 4.6 metric); for the
+ *            scaled forms 2 bytes per entry plus 4 per block scale
  *   info[1]  total device bytes held by the handle (matrix + workspace)
  *   info[2]  number of coupling blocks     info[3] number of dense blocks
  *   info[4]  q                             info[5] k

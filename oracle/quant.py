@@ -70,22 +70,51 @@ def quantize_block(a: np.ndarray, form: str) -> tuple[np.ndarray, float]:
     return q, sigma
 
 
+def _dequantize_equal(blocks: np.ndarray, form: str) -> np.ndarray:
+    """The same rule applied to many blocks of one size at once (rows of `blocks`)."""
+    m = np.max(np.abs(blocks), axis=1)
+    sigma = ((m / 32767.0) if form == "int16" else m).astype(np.float32).astype(np.float64)
+    safe = np.where(sigma == 0.0, 1.0, sigma)
+    r = blocks / safe[:, None]
+    if form == "fp16":
+        q = round_fp16(r)
+    elif form == "bf16":
+        q = round_bf16(r)
+    else:
+        q = np.clip(np.rint(r), -32767, 32767)
+    q[sigma == 0.0] = 0.0
+    return sigma[:, None] * q
+
+
 def dequantize_blocks(vals: np.ndarray, offsets: np.ndarray, form: str) -> np.ndarray:
     """a' = sigma * q for every block [offsets[b], offsets[b+1]) of a flat FP64 array."""
     out = np.empty_like(vals)
-    for b in range(offsets.size - 1):
-        lo, hi = int(offsets[b]), int(offsets[b + 1])
-        q, sigma = quantize_block(vals[lo:hi], form)
-        out[lo:hi] = sigma * q
+    offsets = np.asarray(offsets, dtype=np.int64)
+    sizes = np.diff(offsets)
+    for size in np.unique(sizes):
+        idx = np.flatnonzero(sizes == size)
+        if size == 0:
+            continue
+        for c0 in range(0, idx.size, 1 << 14):  # bounded temporaries
+            sel = idx[c0:c0 + (1 << 14)]
+            gather = offsets[sel][:, None] + np.arange(size)[None, :]
+            out[gather] = _dequantize_equal(vals[gather], form)
     return out
 
 
-def dequantized_arrays(A, form: str) -> dict:
-    """Dequantized U, E, S_val, D_val of a generator matrix (V = U and F = E share the rule)."""
+def dequantized_arrays(A, form: str, bases_fp32: bool = False) -> dict:
+    """Dequantized U, E, S_val, D_val of a generator matrix (V = U and F = E share the rule).
+
+    bases_fp32: U, V, E and F are kept as FP32 values (round to nearest) instead of 16-bit codes."""
     k = A.k
     leaf_blocks = np.asarray(A.leaf_offset) * k
     node_blocks = np.arange(A.n_nodes, dtype=np.int64) * k * k
     s_blocks = np.arange(A.nS + 1, dtype=np.int64) * k * k
-    return dict(U=dequantize_blocks(A.U, leaf_blocks, form), E=dequantize_blocks(A.E, node_blocks, form),
-                S_val=dequantize_blocks(A.S_val, s_blocks, form),
+    if bases_fp32:
+        U = A.U.astype(np.float32).astype(np.float64)
+        E = A.E.astype(np.float32).astype(np.float64)
+    else:
+        U = dequantize_blocks(A.U, leaf_blocks, form)
+        E = dequantize_blocks(A.E, node_blocks, form)
+    return dict(U=U, E=E, S_val=dequantize_blocks(A.S_val, s_blocks, form),
                 D_val=dequantize_blocks(A.D_val, np.asarray(A.D_valoff), form))

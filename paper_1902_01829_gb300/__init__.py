@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libh2gb300.so")
 
 H2_OK, H2_ERR_INVALID, H2_ERR_OOM, H2_ERR_CUDA, H2_ERR_UNSUPPORTED, H2_ERR_TIMEOUT = range(6)
-STORAGE = {"fp64": 0}
+STORAGE = {"fp64": 0, "fp16": 2, "bf16": 3, "int16": 4}
 STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUDA", 4: "H2_ERR_UNSUPPORTED",
                 5: "H2_ERR_TIMEOUT"}
 
@@ -39,7 +39,7 @@ class h2_desc(ctypes.Structure):
                 ("E", ctypes.c_void_p), ("F", ctypes.c_void_p),
                 ("S_rowptr", ctypes.c_void_p), ("S_colidx", ctypes.c_void_p), ("S_val", ctypes.c_void_p),
                 ("D_rowptr", ctypes.c_void_p), ("D_colidx", ctypes.c_void_p), ("D_val", ctypes.c_void_p),
-                ("check_cover", ctypes.c_int32)]
+                ("check_cover", ctypes.c_int32), ("bases_fp32", ctypes.c_int32)]
 
 
 def _load():
@@ -96,7 +96,7 @@ class H2Matrix:
     """An H^2 matrix resident on the current CUDA device (h2_create / h2_destroy)."""
 
     def __init__(self, *, n, depth, rank, leaf_offset, U, E, S_rowptr, S_colidx, S_val, D_rowptr, D_colidx, D_val,
-                 V=None, F=None, storage="fp64", check_cover=False):
+                 V=None, F=None, storage="fp64", check_cover=False, bases_fp32=False):
         sym = V is None and F is None
         keep = dict(leaf_offset=np.ascontiguousarray(leaf_offset, dtype=np.int64),
                     U=np.ascontiguousarray(U, dtype=np.float64), E=np.ascontiguousarray(E, dtype=np.float64),
@@ -109,18 +109,18 @@ class H2Matrix:
                     D_colidx=np.ascontiguousarray(D_colidx, dtype=np.int32),
                     D_val=np.ascontiguousarray(D_val, dtype=np.float64))
         d = h2_desc(n=int(n), depth=int(depth), rank=int(rank), symmetric=1 if sym else 0, storage=STORAGE[storage],
-                    check_cover=1 if check_cover else 0,
+                    check_cover=1 if check_cover else 0, bases_fp32=1 if bases_fp32 else 0,
                     **{key: _ptr(val) for key, val in keep.items()})
         self._h = ctypes.c_void_p()
         _check(_lib.h2_create(ctypes.byref(d), ctypes.byref(self._h)))
         self.n = int(n)
 
     @classmethod
-    def from_generator(cls, A, storage="fp64", check_cover=False) -> "H2Matrix":
+    def from_generator(cls, A, storage="fp64", check_cover=False, bases_fp32=False) -> "H2Matrix":
         """From an object with the generator's arrays (h2gen.H2Matrix)."""
         return cls(n=A.n, depth=A.q, rank=A.k, leaf_offset=A.leaf_offset, U=A.U, E=A.E, S_rowptr=A.S_rowptr,
                    S_colidx=A.S_colidx, S_val=A.S_val, D_rowptr=A.D_rowptr, D_colidx=A.D_colidx, D_val=A.D_val,
-                   storage=storage, check_cover=check_cover)
+                   storage=storage, check_cover=check_cover, bases_fp32=bases_fp32)
 
     def matvec(self, x, y=None, stream=None):
         """y = A^H x on the device. x, y: torch float64 CUDA tensors, shape (n,) or (n, nv) column-major."""

@@ -11,6 +11,7 @@
 
 #include "h2.h"
 #include "hmv_fp64.cuh"
+#include "h2_internal.h"
 #include "stream_fp64.cuh"
 
 static_assert(sizeof(h2::StreamItem) == 32, "work items are read as two int4");
@@ -19,7 +20,9 @@ namespace {
 
 thread_local std::string g_err;
 
-h2_status fail(h2_status st, const char* fmt, ...) {
+}  // namespace
+
+h2_status h2_fail(h2_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -29,94 +32,13 @@ h2_status fail(h2_status st, const char* fmt, ...) {
   return st;
 }
 
-#define CUDA_TRY(call)                                                                                 \
-  do {                                                                                                 \
-    cudaError_t e_ = (call);                                                                           \
-    if (e_ != cudaSuccess) {                                                                           \
-      if (e_ == cudaErrorMemoryAllocation) return fail(H2_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_)); \
-      return fail(H2_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                               \
-    }                                                                                                  \
-  } while (0)
-
-constexpr int kMaxLeaf = 64;
-constexpr int kMaxRank = 64;
-constexpr int kPassVectors = 16;                 // right-hand sides per pass over the matrix
-constexpr long long kWaitBudget = 4000000000LL;  // clock64 cycles (about 2 s) a device wait may take
-
-inline int64_t even(int64_t v) { return v + (v & 1); }
-
-struct ItemList {
-  h2::StreamItem* items = nullptr;  // device
-  int* cta_begin = nullptr;         // device [grid + 1]
-  int64_t count = 0;
-};
-
-}  // namespace
-
 void h2_internal_set_error(const char* msg) { g_err = msg; }
 
-struct h2_matrix_s {
-  int64_t n = 0, leaves = 0, n_nodes = 0, leaf0 = 0, nS = 0, nD = 0, nDval = 0;
-  int q = 0, k = 0, kp = 0, m_max = 0, lr = 32, grid = 0;
-  int64_t paper_bytes = 0, device_bytes = 0;
-  std::vector<void*> allocs;
-  int64_t* leaf_off = nullptr;
-  int64_t* xp_off = nullptr;  // padded leaf offsets of the split x (float2 per vector)
-  double* Vt = nullptr;       // leaf j: k x size_j col-major (= V_j^T, projection)
-  double* E = nullptr;        // node h >= 1: k x k col-major (downsweep)
-  double* Ft = nullptr;       // node h >= 1: F_h^T, k x k col-major (upsweep)
-  char* dmat = nullptr;       // dense blocks then leaf bases U, each padded to an even count of doubles
-  double* smat = nullptr;     // coupling blocks, each padded to an even count of doubles
-  int32_t* Srow = nullptr;
-  int32_t* Scol = nullptr;
-  ItemList dense_items;
-  bool pair_rows = false;  // k = 2^j (j >= 1): the coupling kernel reads row pairs
-  bool s_tiny = true;      // some coupling entry is zero or below 2^-103
-  int* err = nullptr;      // device error word (bounded waits)
-  int* ticket = nullptr;   // upsweep climb counters, one per node
-  int tree_L = 0;          // subtree root level of the fused tree kernels
-  float2* x2 = nullptr;    // split x, padded leaf layout, kPassVectors slots
-  float2* xhat = nullptr;  // n_nodes x kPassVectors x kp
-  float2* yhat = nullptr;
-  long long budget = kWaitBudget;
-  int inject = -1;
-  // per-phase profiling: events recorded at phase boundaries while enabled
-  bool profiling = false;
-  std::vector<cudaEvent_t> events;
-  size_t ev_used = 0;
-  int64_t launches = 0;
-  // host-buffer staging (h2_matvec_host)
-  double* hx = nullptr;
-  double* hy = nullptr;
-  int64_t host_cap = 0;
-};
+using namespace h2i;
 
 namespace {
 
-template <class T>
-h2_status dalloc(h2_matrix_s* h, T** p, int64_t count) {
-  *p = nullptr;
-  if (count <= 0) count = 1;
-  void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(e == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA, "cudaMalloc of %lld bytes failed: %s",
-                (long long)(count * sizeof(T)), cudaGetErrorString(e));
-  }
-  h->allocs.push_back(q);
-  h->device_bytes += count * (int64_t)sizeof(T);
-  *p = (T*)q;
-  return H2_OK;
-}
-
-template <class T>
-h2_status upload(h2_matrix_s* h, T** p, const T* src, int64_t count) {
-  h2_status st = dalloc(h, p, count);
-  if (st != H2_OK) return st;
-  if (count > 0) CUDA_TRY(cudaMemcpy(*p, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice));
-  return H2_OK;
-}
+h2_status (&fail)(h2_status, const char*, ...) = h2_fail;
 
 void free_all(h2_matrix_s* h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
@@ -194,7 +116,9 @@ h2_status validate(const h2_desc* d, int64_t* nS, int64_t* nD, int64_t* nDval, i
   if (d->depth < 0 || d->depth > 24) return fail(H2_ERR_INVALID, "depth = %d outside 0..24", d->depth);
   if (d->rank < 1) return fail(H2_ERR_INVALID, "rank = %d < 1", d->rank);
   if (d->rank > kMaxRank) return fail(H2_ERR_UNSUPPORTED, "rank = %d > %d", d->rank, kMaxRank);
-  if (d->storage != H2_FP64) return fail(H2_ERR_UNSUPPORTED, "storage %d not supported", d->storage);
+  if (d->storage != H2_FP64 && d->storage != H2_FP16_SCALED && d->storage != H2_BF16_SCALED &&
+      d->storage != H2_INT16_SCALED)
+    return fail(H2_ERR_UNSUPPORTED, "storage %d not supported", d->storage);
   if (!d->leaf_offset || !d->U || !d->E || !d->S_rowptr || !d->D_rowptr) return fail(H2_ERR_INVALID, "NULL array in desc");
   if (!d->symmetric && (!d->V || !d->F)) return fail(H2_ERR_INVALID, "V/F are NULL but symmetric = 0");
   const int q = d->depth, k = d->rank;
@@ -258,6 +182,10 @@ void transpose_block(const double* src, double* dst, int64_t rows, int64_t cols)
     for (int64_t r = 0; r < rows; r++) dst[c + cols * r] = src[r + rows * c];
 }
 
+}  // namespace
+
+namespace h2i {
+
 // Split rows (row r weighs row_bytes[r] and starts at item row_item0[r]) into
 // `grid` contiguous ranges of about equal weight; returns each range's first item.
 std::vector<int> balance(const std::vector<int64_t>& row_bytes, const std::vector<int64_t>& row_item0, int grid) {
@@ -275,6 +203,10 @@ std::vector<int> balance(const std::vector<int64_t>& row_bytes, const std::vecto
   for (int c = 1; c <= grid; c++) begin[c] = std::max(begin[c], begin[c - 1]);
   return begin;
 }
+
+}  // namespace h2i
+
+namespace {
 
 // Every copy a streaming kernel will issue must stay inside its source buffer and
 // its stage slot and be 16-byte aligned; checked once on the host so that a
@@ -309,6 +241,10 @@ h2_status upload_items(h2_matrix_s* h, ItemList* L, const std::vector<h2::Stream
 }
 
 // ------------------------------------------------------------------ launch sequence
+}  // namespace
+
+namespace h2i {
+
 // record a phase-boundary event when profiling (events are pooled per handle)
 cudaError_t mark(h2_matrix_s* h, cudaStream_t st) {
   if (!h->profiling) return cudaSuccess;
@@ -320,6 +256,10 @@ cudaError_t mark(h2_matrix_s* h, cudaStream_t st) {
   }
   return cudaEventRecord(h->events[h->ev_used++], st);
 }
+
+}  // namespace h2i
+
+namespace {
 
 template <int NVB>
 cudaError_t set_stream_smem() {
@@ -419,7 +359,9 @@ h2_status matvec_device(h2_matrix_s* h, int nv, const double* x, int64_t ldx, do
     const int nvp = std::min(kPassVectors, nv - v0);
     const double* xp = x + (int64_t)v0 * ldx;
     double* yp = y + (int64_t)v0 * ldy;
-    h2_status s = (h->k > 32) ? run_pass_nv<2>(h, nvp, xp, ldx, yp, ldy, st) : run_pass_nv<1>(h, nvp, xp, ldx, yp, ldy, st);
+    h2_status s = (h->storage != H2_FP64) ? mixed_pass(h, nvp, xp, ldx, yp, ldy, st)
+                  : (h->k > 32)             ? run_pass_nv<2>(h, nvp, xp, ldx, yp, ldy, st)
+                                            : run_pass_nv<1>(h, nvp, xp, ldx, yp, ldy, st);
     if (s != H2_OK) return s;
   }
   return H2_OK;
@@ -438,6 +380,18 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
   CUDA_TRY(cudaDeviceGetAttribute(&h->grid, cudaDevAttrMultiProcessorCount, dev));
 
   if ((st = upload(h, &h->leaf_off, lo, h->leaves + 1)) != H2_OK) return st;
+  if ((st = upload(h, &h->Srow, d->S_rowptr, h->n_nodes + 1)) != H2_OK) return st;
+  if ((st = upload(h, &h->Scol, d->S_colidx, h->nS)) != H2_OK) return st;
+  if ((st = dalloc(h, &h->err, 1)) != H2_OK) return st;
+  CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
+  if ((st = dalloc(h, &h->ticket, h->n_nodes)) != H2_OK) return st;
+  CUDA_TRY(cudaMemset(h->ticket, 0, (size_t)h->n_nodes * sizeof(int)));
+  // subtree roots of the fused tree kernels: at least two CTAs per SM when the tree is deep enough
+  int lmax = 0;
+  while (((int64_t)1 << lmax) < 2 * (int64_t)h->grid) lmax++;
+  h->tree_L = std::min(h->q, lmax);
+  if (h->storage != H2_FP64) return mixed_build(h, d);
+
   // padded leaf offsets of the split x
   std::vector<int64_t> xp((size_t)h->leaves + 1, 0);
   for (int64_t j = 0; j < h->leaves; j++) xp[j + 1] = xp[j] + even(lo[j + 1] - lo[j]);
@@ -541,20 +495,10 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
                               cudaMemcpyHostToDevice));
       }
     }
-    if ((st = upload(h, &h->Srow, d->S_rowptr, h->n_nodes + 1)) != H2_OK) return st;
-    if ((st = upload(h, &h->Scol, d->S_colidx, h->nS)) != H2_OK) return st;
     h->pair_rows = k >= 2 && k <= 64 && (k & (k - 1)) == 0;
     h->s_tiny = h->nS > 0 && has_tiny(d->S_val, h->nS * kk);
   }
 
-  if ((st = dalloc(h, &h->err, 1)) != H2_OK) return st;
-  CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
-  if ((st = dalloc(h, &h->ticket, h->n_nodes)) != H2_OK) return st;
-  CUDA_TRY(cudaMemset(h->ticket, 0, (size_t)h->n_nodes * sizeof(int)));
-  // subtree roots of the fused tree kernels: at least two CTAs per SM when the tree is deep enough
-  int lmax = 0;
-  while (((int64_t)1 << lmax) < 2 * (int64_t)h->grid) lmax++;
-  h->tree_L = std::min(h->q, lmax);
   if ((st = dalloc(h, &h->x2, xp[h->leaves] * kPassVectors)) != H2_OK) return st;
   if ((st = dalloc(h, &h->xhat, h->n_nodes * kPassVectors * h->kp)) != H2_OK) return st;
   if ((st = dalloc(h, &h->yhat, h->n_nodes * kPassVectors * h->kp)) != H2_OK) return st;
@@ -589,6 +533,7 @@ h2_status h2_create(const h2_desc* d, h2_handle* out) {
   h->nDval = nDval;
   h->m_max = m_max;
   h->lr = h->k > 32 ? 32 : pow2ceil(h->k);
+  h->storage = d->storage;
   try {
     st = build_device(h, d);
   } catch (const std::bad_alloc&) {
@@ -599,8 +544,12 @@ h2_status h2_create(const h2_desc* d, h2_handle* out) {
     delete h;
     return st;
   }
-  const int64_t kk = (int64_t)h->k * h->k;
-  h->paper_bytes = 8 * (2 * h->n * h->k + 2 * (h->n_nodes - 1) * kk + nS * kk + nDval);
+  const int64_t kk = (int64_t)h->k * h->k, entries = 2 * h->n * h->k + 2 * (h->n_nodes - 1) * kk + nS * kk + nDval;
+  if (h->storage == H2_FP64)
+    h->paper_bytes = 8 * entries;
+  else  // 16-bit codes plus one FP32 scale per block of U, V, E, F, S and D
+    h->paper_bytes = d->bases_fp32 ? 2 * (nS * kk + nDval) + 4 * (nS + nD) + 4 * (2 * h->n * h->k + 2 * (h->n_nodes - 1) * kk)
+                                   : 2 * entries + 4 * (2 * h->leaves + 2 * (h->n_nodes - 1) + nS + nD);
   *out = h;
   return H2_OK;
 }

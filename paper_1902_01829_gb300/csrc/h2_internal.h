@@ -1,0 +1,136 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "h2.h"
+#include "stream_fp64.cuh"
+
+// error message of the calling thread's last failed call (h2_last_error)
+h2_status h2_fail(h2_status st, const char* fmt, ...);
+void h2_internal_set_error(const char* msg);
+
+#define CUDA_TRY(call)                                                                                        \
+  do {                                                                                                        \
+    cudaError_t e_ = (call);                                                                                  \
+    if (e_ != cudaSuccess) {                                                                                  \
+      if (e_ == cudaErrorMemoryAllocation) return h2_fail(H2_ERR_OOM, "%s: %s", #call, cudaGetErrorString(e_)); \
+      return h2_fail(H2_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));                                   \
+    }                                                                                                         \
+  } while (0)
+
+namespace h2i {
+
+constexpr int kMaxLeaf = 64;
+constexpr int kMaxRank = 64;
+constexpr int kPassVectors = 16;                 // right-hand sides per pass over the matrix
+constexpr long long kWaitBudget = 4000000000LL;  // clock64 cycles (about 2 s) a device wait may take
+
+inline int64_t even(int64_t v) { return v + (v & 1); }
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+struct ItemList {
+  h2::StreamItem* items = nullptr;  // device
+  int* cta_begin = nullptr;         // device [grid + 1]
+  int64_t count = 0;
+};
+
+// device copy of the precision form (per-block scaled 16-bit storage, FP32 arithmetic)
+struct MixedData {
+  void* dmat = nullptr;       // per leaf row: its dense blocks then U_i, each padded to 16 bytes
+  void* dblk = nullptr;       // per dense-stream block: h2::MixedBlock
+  ItemList dense_items;
+  uint16_t* smat = nullptr;   // coupling blocks, k*k padded to a multiple of 8 codes each
+  float* sscale = nullptr;
+  bool bases_fp32 = false;   // U, V, E, F kept as FP32 entries (scale 1) instead of codes
+  void* Vt = nullptr;         // leaf j: V_j^T (k x size_j), at vt_off[j] entries
+  float* vscale = nullptr;
+  int64_t* vt_off = nullptr;
+  void* Ft = nullptr;         // node h >= 1: F_h^T at (h-1) * kk8 entries
+  float* fscale = nullptr;
+  void* E = nullptr;          // node h >= 1: E_h at (h-1) * kk8 entries
+  float* escale = nullptr;
+  int64_t* xp4_off = nullptr; // leaf offsets of the FP32 x copy, padded to multiples of 4
+  float* x4 = nullptr;        // FP32 copy of the pass's x (padded leaf layout)
+  float* xhat = nullptr;      // [node][v][kp4]
+  float* yhat = nullptr;
+  int kp4 = 0;                // k rounded up to a multiple of 4
+  int64_t kk8 = 0;            // k*k rounded up to a multiple of 8
+};
+
+}  // namespace h2i
+
+struct h2_matrix_s {
+  int64_t n = 0, leaves = 0, n_nodes = 0, leaf0 = 0, nS = 0, nD = 0, nDval = 0;
+  int q = 0, k = 0, kp = 0, m_max = 0, lr = 32, grid = 0;
+  int storage = H2_FP64;
+  int64_t paper_bytes = 0, device_bytes = 0;
+  std::vector<void*> allocs;
+  int64_t* leaf_off = nullptr;
+  int64_t* xp_off = nullptr;  // padded leaf offsets of the split x (float2 per vector)
+  double* Vt = nullptr;       // leaf j: k x size_j col-major (= V_j^T, projection)
+  double* E = nullptr;        // node h >= 1: k x k col-major (downsweep)
+  double* Ft = nullptr;       // node h >= 1: F_h^T, k x k col-major (upsweep)
+  char* dmat = nullptr;       // dense blocks then leaf bases U, each padded to an even count of doubles
+  double* smat = nullptr;     // coupling blocks, each padded to an even count of doubles
+  int32_t* Srow = nullptr;
+  int32_t* Scol = nullptr;
+  h2i::ItemList dense_items;
+  h2i::MixedData mx;          // precision form (storage != H2_FP64)
+  bool pair_rows = false;     // k = 2^j (j >= 1): the coupling kernel reads row pairs
+  bool s_tiny = true;         // some coupling entry is zero or below 2^-103
+  int* err = nullptr;         // device error word (bounded waits)
+  int* ticket = nullptr;      // upsweep climb counters, one per node
+  int tree_L = 0;             // subtree root level of the fused tree kernels
+  float2* x2 = nullptr;       // split x, padded leaf layout, kPassVectors slots
+  float2* xhat = nullptr;     // n_nodes x kPassVectors x kp
+  float2* yhat = nullptr;
+  long long budget = h2i::kWaitBudget;
+  int inject = -1;
+  // per-phase profiling: events recorded at phase boundaries while enabled
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t ev_used = 0;
+  int64_t launches = 0;
+  // host-buffer staging (h2_matvec_host)
+  double* hx = nullptr;
+  double* hy = nullptr;
+  int64_t host_cap = 0;
+};
+
+namespace h2i {
+
+template <class T>
+h2_status dalloc(h2_matrix_s* h, T** p, int64_t count) {
+  *p = nullptr;
+  if (count <= 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return h2_fail(e == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA, "cudaMalloc of %lld bytes failed: %s",
+                   (long long)(count * sizeof(T)), cudaGetErrorString(e));
+  }
+  h->allocs.push_back(q);
+  h->device_bytes += count * (int64_t)sizeof(T);
+  *p = (T*)q;
+  return H2_OK;
+}
+
+template <class T>
+h2_status upload(h2_matrix_s* h, T** p, const T* src, int64_t count) {
+  h2_status st = dalloc(h, p, count);
+  if (st != H2_OK) return st;
+  if (count > 0) CUDA_TRY(cudaMemcpy(*p, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice));
+  return H2_OK;
+}
+
+// rows weighed by bytes -> first item of each of `grid` contiguous, about equal ranges
+std::vector<int> balance(const std::vector<int64_t>& row_bytes, const std::vector<int64_t>& row_item0, int grid);
+// record a phase-boundary event when profiling
+cudaError_t mark(h2_matrix_s* h, cudaStream_t st);
+// precision form: device layout (h2_create) and one product pass of up to kPassVectors vectors
+h2_status mixed_build(h2_matrix_s* h, const h2_desc* d);
+h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st);
+
+}  // namespace h2i

@@ -1,0 +1,7 @@
+// Precision-form kernels for fp16 storage (see h2_mixed_launch.cuh).
+#include "h2_mixed_launch.cuh"
+
+namespace h2i {
+template h2_status mixed_pass_form<h2::kFormFp16>(h2_matrix_s*, int, const double*, int64_t, double*, int64_t,
+                                                 cudaStream_t);
+}  // namespace h2i

@@ -66,3 +66,18 @@ def test_storage_error_of_the_precision_forms():
     y = oracle.matvec(A, x)
     err = {f: oracle.rel_l2(oracle.matvec(A, x, **quant.dequantized_arrays(A, f)), y) for f in quant.FORMS}
     assert 1e-6 < err["int16"] < 1e-4 < err["fp16"] < 1e-3 < err["bf16"] < 1e-2, err
+
+
+def test_vectorized_rule_equals_blockwise_rule():
+    """dequantize_blocks (vectorized over equal-sized blocks) equals quantize_block one block at a time."""
+    rng = np.random.default_rng(9)
+    sizes = rng.choice([7, 16, 64], size=60)
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    vals = rng.normal(size=offsets[-1]) * np.repeat(10.0 ** rng.uniform(-5, 2, sizes.size), sizes)
+    vals[offsets[3]:offsets[4]] = 0.0
+    for form in quant.FORMS:
+        parts = []
+        for a, b in zip(offsets[:-1], offsets[1:]):
+            q, sigma = quant.quantize_block(vals[a:b], form)
+            parts.append(sigma * q)
+        np.testing.assert_array_equal(quant.dequantize_blocks(vals, offsets, form), np.concatenate(parts))
