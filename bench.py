@@ -96,11 +96,15 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def dense_kernel_bytes(info: dict, A, nv: int) -> int:
-    """Algorithmic bytes of one dense + expansion launch: D and U once, x read once, y written once,
-    the leaf yhat read once (8-byte values)."""
+def dense_kernel_bytes(info: dict, A, nv: int, storage: str = "fp64", bases_fp32: bool = False) -> int:
+    """Algorithmic bytes of one dense + expansion launch: D and U once (plus one 4-byte scale per block
+    in the scaled forms), x read once, y written once (8 bytes), the leaf yhat read once."""
     nDval = int(A.D_valoff[-1])
-    return 8 * (nDval + A.n * A.k) + 8 * A.n * nv * 2 + 8 * A.leaves * A.k * nv
+    if storage == "fp64":
+        return 8 * (nDval + A.n * A.k) + 8 * A.n * nv * 2 + 8 * A.leaves * A.k * nv
+    u_bytes = 4 if bases_fp32 else 2
+    return (2 * nDval + u_bytes * A.n * A.k + 4 * (A.nD + A.leaves) + 4 * A.n * nv + 8 * A.n * nv
+            + 4 * A.leaves * A.k * nv)
 
 
 def run_oracle_baseline(A, x, budget_s: float = 12.0):
@@ -127,6 +131,9 @@ def main():
     ap.add_argument("--workload", default="2d_n1M", choices=sorted(WORKLOADS))
     ap.add_argument("--nv", type=int, default=1)
     ap.add_argument("--no-extras", action="store_true", help="skip the nv=16 line, e2e and the CPU baseline")
+    ap.add_argument("--storage", default="fp64", choices=["fp64", "fp16", "bf16", "int16"],
+                    help="storage form of the timed product (the extras always use fp64 and list the scaled forms)")
+    ap.add_argument("--bases-fp32", action="store_true", help="scaled forms: keep U, V, E, F in FP32")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -155,7 +162,7 @@ def main():
     # weak scaling: every rank holds its own independent matrix (replicas of the workload)
     cfg["seed"] = cfg["seed"] + 1000 * rank
     A = h2gen.generate(**cfg)
-    M = h2.H2Matrix.from_generator(A)
+    M = h2.H2Matrix.from_generator(A, storage=args.storage, bases_fp32=args.bases_fp32)
     info = M.info()
     nv = args.nv
     x_np = h2gen.vectors(77 + rank, A.n, nv)
@@ -204,7 +211,7 @@ def main():
 
     # roofline of the dominant kernel (dense blocks + leaf expansion), timed live above
     dense_ms = phase_ms["dense_expand"] / args.steps
-    dbytes = dense_kernel_bytes(info, A, nv)
+    dbytes = dense_kernel_bytes(info, A, nv, args.storage, args.bases_fp32)
     achieved = dbytes / (dense_ms * 1e-3) / 1e9
     roofline = {"kernel": "k_dense_expand", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
@@ -213,7 +220,10 @@ def main():
 
     out = {"metric": METRIC, "value": round(gbs, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64 (stored) / double-float (computed)", "data": "synthetic",
+           "vs_baseline": None,
+           "dtype": ("f64 (stored) / double-float (computed)" if args.storage == "fp64" else
+                     f"{args.storage} + per-block f32 scale (stored{', f32 bases' if args.bases_fp32 else ''}) / f32 (computed)"),
+           "data": "synthetic",
            "config": {"workload": WORKLOADS[args.workload], "n": A.n, "nv": nv, "q": A.q, "k": A.k,
                       "nS": A.nS, "nD": A.nD, "paper_bytes": info["paper_bytes"],
                       "l2": "matrix (%.1f GB) >> 129 MB L2: no flush needed" % (info["paper_bytes"] / 1e9),
@@ -266,6 +276,9 @@ def main():
                        "GBs": round(info["paper_bytes"] * world / (ms16 * 1e-3) / 1e9, 1),
                        "rel_err_vs_oracle": oracle.rel_l2(y16.cpu().numpy(), oracle.matvec(A, x16_np))}
 
+        # precision form (per-block scaled 16-bit S and D; U, V, E, F in FP32 or 16-bit) at several vector counts
+        out["mixed"] = mixed_lines(h2, A, info, dev, stream, y_ref, x_np, args.steps, world, rank)
+
         if rank == 0 and world == 1:
             sec, reps, cores = run_oracle_baseline(A, x_np)
             out["cpu_baseline"] = {"value": round(info["paper_bytes"] / sec / 1e9, 2), "unit": "GB/s",
@@ -278,6 +291,47 @@ def main():
     M.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+MIXED_FORMS = [("int16", True), ("fp16", True), ("bf16", False)]
+MIXED_NV = [1, 8, 32, 64]
+
+
+def mixed_lines(h2, A, info64, dev, stream, y_ref, x_np, steps, world, rank):
+    """Time the precision form on the same matrix: GB/s of its own stored bytes, vectors/s, error vs the FP64 oracle."""
+    import oracle
+    import torch
+
+    xw_np = np.asfortranarray(np.concatenate([x_np, h2gen.vectors(911 + rank, A.n, max(MIXED_NV) - 1)], axis=1))
+    ref2 = np.concatenate([y_ref, oracle.matvec(A, xw_np[:, 1:2])], axis=1)  # FP64 oracle, first two columns
+    xw = torch.from_numpy(np.ascontiguousarray(xw_np.T)).to(dev).t()
+    lines = []
+    for form, bases in MIXED_FORMS:
+        M = h2.H2Matrix.from_generator(A, storage=form, bases_fp32=bases)
+        mb = M.info()["paper_bytes"]
+        for nv in MIXED_NV:
+            X = xw[:, :nv]
+            Y = torch.empty((nv, A.n), dtype=torch.float64, device=dev).t()
+            for _ in range(3):
+                M.matvec(X, Y, stream=stream)
+            M.check(stream)
+            k = max(3, steps // (1 + nv // 8))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(k):
+                M.matvec(X, Y, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            yy = Y[:, :min(nv, 2)].cpu().numpy()
+            err = oracle.rel_l2(yy, ref2[:, :yy.shape[1]])
+            lines.append({"storage": form, "bases_fp32": bases, "nv": nv, "ms_per_step": round(ms, 4),
+                          "GBs": round(mb * world / (ms * 1e-3) / 1e9, 1),
+                          "vectors_per_s": round(nv * world / (ms * 1e-3), 1),
+                          "stored_bytes": mb, "rel_err_vs_fp64_oracle": err})
+        M.close()
+    return lines
 
 
 def reference_arm(args, cfg, world):

@@ -52,7 +52,7 @@ h2_status mixed_pass_t(h2_matrix_s* h, int nv, const double* x, int64_t ldx, dou
   k_upsweep_tree_m<FB, RPL, NVB><<<tree_grid, tree_threads, 0, st>>>(T);
   if (me == cudaSuccess) me = mark(h, st);
   if (k >= 4 && k <= 64 && (k & (k - 1)) == 0) {
-    constexpr int CB = NVB <= 2 ? 4 : (NVB <= 4 ? 2 : 1);
+    constexpr int CB = NVB <= 2 ? 8 : (NVB <= 4 ? 4 : 2);
     k_coupling_m<F, NVB, CB><<<cgrid, 128, 0, st>>>(M.smat, M.sscale, M.kk8, h->Srow, h->Scol, k, M.kp4, h->n_nodes, nv,
                                                      M.xhat, M.yhat);
   } else {

@@ -287,9 +287,10 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(TreeParam
 // ---------------------------------------------------------------- coupling, all levels
 // One warp per node row. k = 4 * H with H a power of two (k = 4 .. 64): lane
 // = g * H + h owns rows 4h .. 4h + 3, read as one 8-byte load per column;
-// column groups g = 0 .. 31 / H take columns g, g + G, ... Blocks are padded
-// to kk8 codes; each block's partial sum is scaled once. Two batches of CB
-// columns per lane are in flight.
+// column groups g = 0 .. G-1 (G = 32 / H) take columns g, g + G, ... The
+// row's (block, column) slots are walked CB at a time, two batches in
+// flight; a block's partial sum is scaled once, after its last column.
+// Blocks are padded to kk8 codes.
 template <int F, int NVB, int CB>
 __global__ void __launch_bounds__(128) k_coupling_m(const uint16_t* __restrict__ S, const float* __restrict__ sscale,
                                                    int64_t kk8, const int32_t* __restrict__ Srow,
@@ -300,35 +301,43 @@ __global__ void __launch_bounds__(128) k_coupling_m(const uint16_t* __restrict__
   if (i >= n_nodes) return;
   const int H = k >> 2, G = 32 / H;
   const int g = lane / H, h = lane - g * H;
-  const int cpl = k / G;                // columns per lane per block
-  const int ncb = (cpl + CB - 1) / CB;  // batches per block
+  const int cpl = max(1, k / G);  // columns per lane per block, a power of two (lanes with col >= k idle)
+  const int lcpl = __ffs(cpl) - 1;
   const int32_t b0 = Srow[i];
-  const int nbatch = (Srow[i + 1] - b0) * ncb;
+  const int nslot = (Srow[i + 1] - b0) * cpl;
   float acc[4][NVB], p[4][NVB];
 #pragma unroll
   for (int r = 0; r < 4; r++)
 #pragma unroll
     for (int v = 0; v < NVB; v++) acc[r][v] = p[r][v] = 0.f;
   uint2 a0[CB], a1[CB];
-  float x0[CB][NVB], x1[CB][NVB];
-  float s0 = 0.f, s1 = 0.f;
-  auto load = [&](int bt, uint2(&a)[CB], float(&xv)[CB][NVB], float& sc) {
-    const int b = bt / ncb, cb = bt - b * ncb;
-    const uint16_t* A = S + (int64_t)(b0 + b) * kk8;
-    const float* X = xhat + (int64_t)__ldg(Scol + b0 + b) * nv * kp;
-    sc = __ldg(sscale + b0 + b);
+  float x0[CB][NVB], x1[CB][NVB], s0[CB], s1[CB];
+  auto load = [&](int bt, uint2(&a)[CB], float(&xv)[CB][NVB], float(&sc)[CB]) {
 #pragma unroll
     for (int u = 0; u < CB; u++) {
-      const int col = g + G * (cb * CB + u);
-      const bool ok = col < k;
-      a[u] = ok ? __ldg(reinterpret_cast<const uint2*>(A + 4 * h + k * col)) : make_uint2(0u, 0u);
+      const int slot = bt * CB + u;
+      const int b = slot >> lcpl, c = slot & (cpl - 1);
+      const int col = g + G * c;
+      const bool ok = slot < nslot && col < k;
+      sc[u] = 0.f;
+      a[u] = make_uint2(0u, 0u);
 #pragma unroll
-      for (int v = 0; v < NVB; v++) xv[u][v] = (ok && v < nv) ? __ldg(X + v * kp + col) : 0.f;
+      for (int v = 0; v < NVB; v++) xv[u][v] = 0.f;
+      if (slot < nslot) {
+        sc[u] = __ldg(sscale + b0 + b);
+        if (ok) {
+          a[u] = __ldg(reinterpret_cast<const uint2*>(S + (int64_t)(b0 + b) * kk8 + 4 * h + k * col));
+          const float* X = xhat + (int64_t)__ldg(Scol + b0 + b) * nv * kp;
+#pragma unroll
+          for (int v = 0; v < NVB; v++) xv[u][v] = (v < nv) ? __ldg(X + v * kp + col) : 0.f;
+        }
+      }
     }
   };
-  auto compute = [&](int bt, const uint2(&a)[CB], const float(&xv)[CB][NVB], float sc) {
+  auto compute = [&](int bt, const uint2(&a)[CB], const float(&xv)[CB][NVB], const float(&sc)[CB]) {
 #pragma unroll
     for (int u = 0; u < CB; u++) {
+      const int slot = bt * CB + u;
       const float2 lo = codes_to_f2<F>(a[u].x), hi = codes_to_f2<F>(a[u].y);
 #pragma unroll
       for (int v = 0; v < NVB; v++) {
@@ -337,17 +346,18 @@ __global__ void __launch_bounds__(128) k_coupling_m(const uint16_t* __restrict__
         p[2][v] = fmaf(hi.x, xv[u][v], p[2][v]);
         p[3][v] = fmaf(hi.y, xv[u][v], p[3][v]);
       }
-    }
-    if ((bt + 1) % ncb == 0) {  // block done: scale its partial sum once
+      if (slot < nslot && (slot & (cpl - 1)) == cpl - 1) {  // last column of a block: scale its partial sum
 #pragma unroll
-      for (int r = 0; r < 4; r++)
+        for (int r = 0; r < 4; r++)
 #pragma unroll
-        for (int v = 0; v < NVB; v++) {
-          acc[r][v] = fmaf(sc, p[r][v], acc[r][v]);
-          p[r][v] = 0.f;
-        }
+          for (int v = 0; v < NVB; v++) {
+            acc[r][v] = fmaf(sc[u], p[r][v], acc[r][v]);
+            p[r][v] = 0.f;
+          }
+      }
     }
   };
+  const int nbatch = (nslot + CB - 1) / CB;
   if (nbatch > 0) load(0, a0, x0, s0);
   for (int bt = 0; bt < nbatch; bt += 2) {
     if (bt + 1 < nbatch) load(bt + 1, a1, x1, s1);
@@ -410,13 +420,14 @@ __host__ __device__ constexpr int mixed_stage_bytes(int nvb) {
   return kMixedHeader + kStageMat + kMixedMaxBlocks * mixed_vec_slot(nvb);
 }
 __host__ __device__ constexpr int mixed_red_bytes(int nvb, int cw) { return cw * nvb * 64 * 4; }
+constexpr int kMixedBlkBuf = 32 * 4 * 16;  // block records of one producer batch (32 items x 4 blocks)
 __host__ __device__ constexpr int mixed_stages(int nvb, int cw) {
-  return (kSmemLimit - 256 - mixed_red_bytes(nvb, cw)) / mixed_stage_bytes(nvb) < 6
-             ? (kSmemLimit - 256 - mixed_red_bytes(nvb, cw)) / mixed_stage_bytes(nvb)
+  return (kSmemLimit - 256 - kMixedBlkBuf - mixed_red_bytes(nvb, cw)) / mixed_stage_bytes(nvb) < 6
+             ? (kSmemLimit - 256 - kMixedBlkBuf - mixed_red_bytes(nvb, cw)) / mixed_stage_bytes(nvb)
              : 6;
 }
 __host__ __device__ constexpr int mixed_smem_bytes(int nvb, int cw) {
-  return mixed_stages(nvb, cw) * mixed_stage_bytes(nvb) + 256 + mixed_red_bytes(nvb, cw);
+  return mixed_stages(nvb, cw) * mixed_stage_bytes(nvb) + 256 + mixed_red_bytes(nvb, cw) + kMixedBlkBuf;
 }
 constexpr int kMixedCW = 8;
 
@@ -437,7 +448,8 @@ struct MixedStreamParams {
 // Stage header: [0] R, [1] nb, [2] row, [3] flags; block t at int index 8 + 4 t:
 // cols | FP32-entries flag << 16, vs, matrix offset in bytes, scale (bits).
 template <int NST, int SB, int VSLOT>
-__device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const StreamShared& S, int ib, int ie) {
+__device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const StreamShared& S, int ib, int ie,
+                                              MixedBlock* blkbuf) {
   const int lane = threadIdx.x & 31;
   const uint64_t pol = policy_evict_first();
   int issued = 0;
@@ -454,6 +466,16 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
       d1 = __ldg(src + 1);
     }
     const int cnt = min(32, ie - base);
+    // the batch's items cover a contiguous range of blocks: stage their records in shared memory
+    const long long bfirst = (long long)(((unsigned long long)(unsigned)__shfl_sync(0xFFFFFFFFu, d1.y, 0) << 32) |
+                                         (unsigned)__shfl_sync(0xFFFFFFFFu, d1.x, 0));
+    const unsigned lshape = (unsigned)__shfl_sync(0xFFFFFFFFu, d0.w, cnt - 1);
+    const long long blast = (long long)(((unsigned long long)(unsigned)__shfl_sync(0xFFFFFFFFu, d1.y, cnt - 1) << 32) |
+                                        (unsigned)__shfl_sync(0xFFFFFFFFu, d1.x, cnt - 1)) +
+                            min((int)((lshape >> 8) & 0xFF), kMixedMaxBlocks);
+    const int nbatch = (int)min(blast - bfirst, (long long)(32 * kMixedMaxBlocks));
+    for (int u = lane; u < nbatch; u += 32) blkbuf[u] = P.blk[bfirst + u];
+    __syncwarp();
     for (int t = 0; t < cnt; t++) {
       const int it = base + t - ib;
       const int s = it % NST, use = it / NST;
@@ -479,7 +501,8 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
       int* hd = reinterpret_cast<int*>(stage);
       // per-block side information, one lane per block
       MixedBlock mb{};
-      if (lane < nb) mb = P.blk[b0 + lane];
+      const long long bi = b0 - bfirst + lane;
+      if (lane < nb && bi >= 0 && bi < nbatch) mb = blkbuf[bi];
       const int esize = (mb.src & 2) ? 4 : 2;
       const int codes = (R * (int)mb.cols * esize + 15) & ~15;  // padded bytes of this block
       int moff = codes;  // inclusive prefix of the blocks' padded byte counts
@@ -544,7 +567,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
   const int ib = P.cta_begin[blockIdx.x], ie = P.cta_begin[blockIdx.x + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == CW) {
-    mixed_produce<NST, SB, VSLOT>(P, S, ib, ie);
+    // producer-private block records: smem after the row reduction buffer
+    MixedBlock* blkbuf = reinterpret_cast<MixedBlock*>(smem + NST * SB + 256 + mixed_red_bytes(NVB, CW));
+    mixed_produce<NST, SB, VSLOT>(P, S, ib, ie, blkbuf);
     return;
   }
   StreamParams W{};
@@ -582,30 +607,50 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
         for (int r = 0; r < 2; r++)
 #pragma unroll
           for (int v = 0; v < NVB; v++) p[u][r][v] = 0.f;
-      if (r0 < R) {
+      if (!f32 && R == 64 && C == 64 && vs == 64) {
+        // full 64 x 64 block of codes: fixed strides, every column loaded up front
+        constexpr int CPW = 64 / CW;
+        const uint32_t* Aw = reinterpret_cast<const uint32_t*>(A + r0 + 64 * c0);
+        uint32_t w[CPW];
+#pragma unroll
+        for (int u = 0; u < CPW; u++) w[u] = Aw[32 * u];
+#pragma unroll
+        for (int v = 0; v < NVB; v++) {
+          if (v >= nv) continue;
+          float xv[CPW];
+#pragma unroll
+          for (int u = 0; u < CPW; u += 4) {
+            const float4 t4 = *reinterpret_cast<const float4*>(X + v * 64 + c0 + u);
+            xv[u] = t4.x;
+            xv[u + 1] = t4.y;
+            xv[u + 2] = t4.z;
+            xv[u + 3] = t4.w;
+          }
+#pragma unroll
+          for (int u = 0; u < CPW; u++) {
+            const float2 a = codes_to_f2<F>(w[u]);
+            p[u % SETS][0][v] = fmaf(a.x, xv[u], p[u % SETS][0][v]);
+            p[u % SETS][1][v] = fmaf(a.y, xv[u], p[u % SETS][1][v]);
+          }
+        }
+      } else if (r0 < R) {
         const bool even = (R & 1) == 0;
-        for (int col0 = c0; col0 < c1; col0 += SETS) {
+        for (int col = c0; col < c1; col++) {
+          float2 a;
+          if (f32) {
+            a.x = A32[r0 + R * col];
+            a.y = (r0 + 1 < R) ? A32[r0 + 1 + R * col] : 0.f;
+          } else if (even) {
+            a = codes_to_f2<F>(*reinterpret_cast<const uint32_t*>(A + r0 + R * col));
+          } else {
+            a.x = code_to_f<F>(A[r0 + R * col]);
+            a.y = (r0 + 1 < R) ? code_to_f<F>(A[r0 + 1 + R * col]) : 0.f;
+          }
 #pragma unroll
-          for (int u = 0; u < SETS; u++) {
-            const int col = col0 + u;
-            if (col < c1) {
-              float2 a;
-              if (f32) {
-                a.x = A32[r0 + R * col];
-                a.y = (r0 + 1 < R) ? A32[r0 + 1 + R * col] : 0.f;
-              } else if (even) {
-                a = codes_to_f2<F>(*reinterpret_cast<const uint32_t*>(A + r0 + R * col));
-              } else {
-                a.x = code_to_f<F>(A[r0 + R * col]);
-                a.y = (r0 + 1 < R) ? code_to_f<F>(A[r0 + 1 + R * col]) : 0.f;
-              }
-#pragma unroll
-              for (int v = 0; v < NVB; v++) {
-                const float xv = (v < nv) ? X[v * vs + col] : 0.f;
-                p[u][0][v] = fmaf(a.x, xv, p[u][0][v]);
-                p[u][1][v] = fmaf(a.y, xv, p[u][1][v]);
-              }
-            }
+          for (int v = 0; v < NVB; v++) {
+            const float xv = (v < nv) ? X[v * vs + col] : 0.f;
+            p[0][0][v] = fmaf(a.x, xv, p[0][0][v]);
+            p[0][1][v] = fmaf(a.y, xv, p[0][1][v]);
           }
         }
       }
