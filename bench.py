@@ -38,6 +38,29 @@ WORKLOADS = {
 }
 
 
+def replica_config(workload: str, rank: int) -> dict:
+    """Weak scaling: every rank multiplies its own independent matrix of the same workload (seed per rank)."""
+    cfg = dict(h2gen.CONFIGS[workload])
+    cfg["seed"] = cfg["seed"] + 1000 * rank
+    return cfg
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (the job's time); identity without a process group."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -139,7 +162,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    cfg = dict(h2gen.CONFIGS[args.workload])
+    cfg = replica_config(args.workload, rank)
     hbm, peak_kind = peaks()
 
     if args.impl == "reference":
@@ -159,8 +182,6 @@ def main():
     torch.cuda.set_device(dev)
     import paper_1902_01829_gb300 as h2
 
-    # weak scaling: every rank holds its own independent matrix (replicas of the workload)
-    cfg["seed"] = cfg["seed"] + 1000 * rank
     A = h2gen.generate(**cfg)
     M = h2.H2Matrix.from_generator(A, storage=args.storage, bases_fp32=args.bases_fp32)
     info = M.info()
@@ -200,14 +221,10 @@ def main():
         barrier()
     phase_ms, launches = M.profile_read()
     M.profile(False)
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_step = ms / args.steps
-    gbs = info["paper_bytes"] * world / (ms_step * 1e-3) / 1e9
-    vps = nv * world / (ms_step * 1e-3)
+    gbs = job_rate(info["paper_bytes"], world, ms_step * 1e-3) / 1e9
+    vps = job_rate(nv, world, ms_step * 1e-3)
 
     # roofline of the dominant kernel (dense blocks + leaf expansion), timed live above
     dense_ms = phase_ms["dense_expand"] / args.steps
@@ -247,11 +264,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             M.matvec_host(xh_np, yh_np, stream=stream)
-        el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, dist, dev)
         e2e_step = el / args.steps
         out["e2e"] = {"value": round(info["paper_bytes"] * world / e2e_step / 1e9, 1), "unit": "GB/s",
                       "ms_per_step": round(e2e_step * 1e3, 4), "vectors_per_s": round(nv * world / e2e_step, 2),
@@ -338,7 +351,7 @@ def reference_arm(args, cfg, world):
     """The FP64 CPU oracle, timed as it stands on the host cores, same workload and metric."""
     import oracle
 
-    A = h2gen.generate(**cfg)
+    A = h2gen.generate(**dict(h2gen.CONFIGS[args.workload]))
     x = h2gen.vectors(77, A.n, args.nv)
     paper_bytes = 8 * (2 * A.n * A.k + 2 * (A.n_nodes - 1) * A.k * A.k + A.nS * A.k * A.k + int(A.D_valoff[-1]))
     for _ in range(max(1, min(args.warmup, 2))):

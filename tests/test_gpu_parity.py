@@ -180,3 +180,28 @@ def test_bounded_wait_reports_timeout(h2, c1):
     M.check()
     assert oracle.rel_l2(y.cpu().numpy(), oracle.matvec(c1, x_np)) <= TOL
     M.close()
+
+
+@pytest.mark.parametrize("storage", ["fp64", "int16"])
+def test_cuda_graph_capture_and_replay(h2, c1, storage):
+    """A product captured into a CUDA graph (no host synchronization inside h2_matvec) replays
+    correctly with new vector contents; the first product of a vector count runs before capture."""
+    M = h2.H2Matrix.from_generator(c1, storage=storage, bases_fp32=True)
+    x = torch.zeros((2, c1.n), dtype=torch.float64, device="cuda").t()
+    y = torch.zeros((2, c1.n), dtype=torch.float64, device="cuda").t()
+    M.matvec(x, y)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        M.matvec(x, y)
+    from oracle import quant
+    deq = quant.dequantized_arrays(c1, storage, True) if storage != "fp64" else {}
+    for seed in (701, 702):
+        xs = h2gen.vectors(seed, c1.n, 2)
+        x.copy_(torch.from_numpy(np.ascontiguousarray(xs.T)).cuda().t())
+        g.replay()
+        torch.cuda.synchronize()
+        tol = TOL if storage == "fp64" else 2e-5
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.matvec(c1, xs, **deq)) <= tol
+    M.check()
+    M.close()
