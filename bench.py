@@ -35,11 +35,15 @@ WORKLOADS = {
     "2d_n1M": "2D exp(-r/0.1) covariance H^2 matvec, n=2^20 uniform points, m=64, k=16 (4x4 Chebyshev), eta=0.9, FP64",
     "2d_n4096": "2D exp(-r/0.1) covariance H^2 matvec, n=4096 uniform points, m=32, k=16, eta=0.9, FP64",
     "2d_n256k": "2D exp(-r/0.1) covariance H^2 matvec, n=2^18 uniform points, m=64, k=16, eta=0.9, FP64",
+    "batch256": "256 independent 2D exp(-r/0.1) covariance H^2 matvecs, n log-uniform in [2^12, 2^17], m=32, k=16, "
+                "eta=0.9, nv in {1, 4, 16}, fp16 storage + f32 arithmetic, one graph-captured batched product",
 }
 
 
 def replica_config(workload: str, rank: int) -> dict:
     """Weak scaling: every rank multiplies its own independent matrix of the same workload (seed per rank)."""
+    if workload not in h2gen.CONFIGS:
+        return {}
     cfg = dict(h2gen.CONFIGS[workload])
     cfg["seed"] = cfg["seed"] + 1000 * rank
     return cfg
@@ -182,6 +186,8 @@ def main():
     torch.cuda.set_device(dev)
     import paper_1902_01829_gb300 as h2
 
+    if args.workload == "batch256":
+        return batch_main(h2, args, dev, dist, world, rank, hbm, peak_kind)
     A = h2gen.generate(**cfg)
     M = h2.H2Matrix.from_generator(A, storage=args.storage, bases_fp32=args.bases_fp32)
     info = M.info()
@@ -292,6 +298,9 @@ def main():
         # precision form (per-block scaled 16-bit S and D; U, V, E, F in FP32 or 16-bit) at several vector counts
         out["mixed"] = mixed_lines(h2, A, info, dev, stream, y_ref, x_np, args.steps, world, rank)
 
+        # many independent matrices of uneven size in one batched, graph-captured product
+        out["batch"] = batch_line(h2, dev, args.steps, world, rank, hbm)
+
         if rank == 0 and world == 1:
             sec, reps, cores = run_oracle_baseline(A, x_np)
             out["cpu_baseline"] = {"value": round(info["paper_bytes"] / sec / 1e9, 2), "unit": "GB/s",
@@ -347,10 +356,132 @@ def mixed_lines(h2, A, info64, dev, stream, y_ref, x_np, steps, world, rank):
     return lines
 
 
+def batch_line(h2, dev, steps, world, rank, hbm, count=256, storage="fp16", timed_barrier=None):
+    """The batched workload: 256 independent 2D exp(-r/0.1) matrices, n log-uniform in [2^12, 2^17],
+    m=32, k=16, nv_i drawn from {1, 4, 16}, fp16 storage with per-block scales, FP32 arithmetic.
+    One product of every member = one graph replay (one launch per phase for the whole batch).
+    Reported: stored bytes streamed per second, vectors/s, member products/s; the same products
+    as a loop of one h2_matvec per member, for comparison; the error of sampled members."""
+    import oracle
+    import torch
+    from oracle import quant
+
+    t_build = time.perf_counter()
+    spec = h2gen.batch_workload(count=count, seed=40 + rank)
+    ns = [kw["n"] for kw, _ in spec]
+    sample = sorted({int(np.argmin(ns)), int(np.argmax(ns))})
+    Ms, xs, ys, keep = [], [], [], {}
+    for i, (kw, nv) in enumerate(spec):
+        A = h2gen.generate(**kw)
+        Ms.append(h2.H2Matrix.from_generator(A, storage=storage))
+        x = h2gen.vectors(3000 + i, A.n, nv)
+        xs.append(torch.from_numpy(np.ascontiguousarray(x.T)).to(dev).t())
+        ys.append(torch.empty((nv, A.n), dtype=torch.float64, device=dev).t())
+        if i in sample:
+            keep[i] = (A, x)
+        else:
+            A.free()
+    B = h2.H2Batch(Ms)
+    t_build = time.perf_counter() - t_build
+    stored = sum(M.info()["paper_bytes"] for M in Ms)
+    vecs = sum(nv for _, nv in spec)
+    args = B.prepare(xs, ys)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            B.matvec_prepared(args, s)
+    s.synchronize()
+    B.check(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        B.matvec_prepared(args, s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    k = max(5, steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream(dev)
+    if timed_barrier is not None:
+        timed_barrier.barrier()
+    torch.cuda.synchronize()
+    e0.record(cur)
+    for _ in range(k):
+        g.replay()
+    e1.record(cur)
+    if timed_barrier is not None:
+        timed_barrier.barrier()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / k, timed_barrier, dev)
+    B.check(s)
+    # per-phase split (events between the phase launches; outside the timed graph replays)
+    B.profile(True)
+    B.profile_read()
+    for _ in range(3):
+        B.matvec_prepared(args, cur)
+    phase_ms, _ = B.profile_read()
+    B.profile(False)
+    errs = {}
+    for i, (A, x) in keep.items():
+        y = ys[i].cpu().numpy()
+        errs[str(A.n)] = {"vs_fp64_oracle": oracle.rel_l2(y, oracle.matvec(A, x)),
+                          "vs_quantized_oracle": oracle.rel_l2(y, oracle.matvec(A, x, **quant.dequantized_arrays(A, storage)))}
+    # the same products one handle at a time (no graph)
+    loop_k = max(3, k // 4)
+    for M, x, y in zip(Ms, xs, ys):
+        M.matvec(x, y, stream=cur)
+    torch.cuda.synchronize()
+    e0.record(cur)
+    for _ in range(loop_k):
+        for M, x, y in zip(Ms, xs, ys):
+            M.matvec(x, y, stream=cur)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1) / loop_k
+    info = B.info()
+    del g
+    B.close()
+    for M in Ms:
+        M.close()
+    gbs = stored * world / (ms * 1e-3) / 1e9
+    return {"workload": f"{count} 2D exp(-r/0.1) matrices, n log-uniform in [2^12, 2^17] (sum {sum(ns)}), m=32, k=16, "
+                        f"eta=0.9, nv in {{1, 4, 16}} (sum {vecs}), {storage} + per-block f32 scale, f32 arithmetic",
+            "ms_per_step": round(ms, 4), "GBs": round(gbs, 1), "frac_of_hbm": round(gbs / world / hbm, 4),
+            "vectors_per_s": round(vecs * world / (ms * 1e-3), 1),
+            "matvecs_per_s": round(count * world / (ms * 1e-3), 1), "stored_bytes": stored,
+            "l2": "batch (%.1f GB) >> 129 MB L2: no flush needed" % (stored / 1e9),
+            "launches_per_step": info["launches_per_pass"], "tree_jobs": info["tree_jobs"],
+            "dense_items": info["dense_items"], "graph": True,
+            "phase_ms": {key: round(v / 3, 4) for key, v in phase_ms.items()},
+            "one_handle_at_a_time_ms": round(loop_ms, 4), "rel_err_sampled": errs,
+            "build_s": round(t_build, 1)}
+
+
+def batch_main(h2, args, dev, dist, world, rank, hbm, peak_kind):
+    """--workload batch256: the batched product alone, as the main line."""
+    import torch
+
+    with ClockSampler(dev.index) as clk:
+        b = batch_line(h2, dev, args.steps, world, rank, hbm, timed_barrier=dist)
+    out = {"metric": METRIC, "value": b["GBs"], "unit": "GB/s", "n_gpus": world, "steps": max(5, args.steps),
+           "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "fp16 + per-block f32 scale (stored) / f32 (computed)", "data": "synthetic",
+           "config": {"workload": WORKLOADS["batch256"], "l2": b["l2"],
+                      "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+           "vectors_per_s": b["vectors_per_s"], "gpu_launches": b["launches_per_step"] * max(5, args.steps),
+           "batch": b, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def reference_arm(args, cfg, world):
     """The FP64 CPU oracle, timed as it stands on the host cores, same workload and metric."""
     import oracle
 
+    if args.workload == "batch256":
+        return reference_batch(args, world)
     A = h2gen.generate(**dict(h2gen.CONFIGS[args.workload]))
     x = h2gen.vectors(77, A.n, args.nv)
     paper_bytes = 8 * (2 * A.n * A.k + 2 * (A.n_nodes - 1) * A.k * A.k + A.nS * A.k * A.k + int(A.D_valoff[-1]))
@@ -370,6 +501,48 @@ def reference_arm(args, cfg, world):
            "vectors_per_s": round(args.nv / sec, 2),
            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
                             "sample": f"full workload, nv={args.nv}, {steps} products"},
+           "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def fp16_stored_bytes(A) -> int:
+    """Bytes of a matrix in the scaled 16-bit form: 2 per entry of U, V, E, F, S, D plus a 4-byte scale per block."""
+    kk = A.k * A.k
+    entries = 2 * A.n * A.k + 2 * (A.n_nodes - 1) * kk + A.nS * kk + int(A.D_valoff[-1])
+    blocks = 2 * A.leaves + 2 * (A.n_nodes - 1) + A.nS + A.nD
+    return 2 * entries + 4 * blocks
+
+
+def reference_batch(args, world):
+    """The FP64 oracle on a bounded sample of the batched workload (the first members, in order, each
+    with its own vector count), reported in the batched line's unit (stored 16-bit bytes per second)."""
+    import oracle
+
+    spec = h2gen.batch_workload()
+    sample, total = [], 0
+    for kw, nv in spec:  # about 1.5e6 points of work per step
+        A = h2gen.generate(**kw)
+        sample.append((A, h2gen.vectors(3000 + len(sample), A.n, nv), nv))
+        total += A.n * nv
+        if total >= 1_500_000:
+            break
+    stored = sum(fp16_stored_bytes(A) for A, _, _ in sample)
+    vecs = sum(nv for _, _, nv in sample)
+    for A, x, _ in sample[:2]:
+        oracle.matvec(A, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for A, x, _ in sample:
+            oracle.matvec(A, x)
+    sec = (time.perf_counter() - t0) / args.steps
+    val = round(stored / sec / 1e9, 3)
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOADS["batch256"], "sample_members": len(sample), "stored_bytes": stored},
+           "vectors_per_s": round(vecs / sec, 2),
+           "cpu_baseline": {"value": val, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+                            "sample": f"first {len(sample)} of 256 members ({vecs} vectors) per step"},
            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -211,3 +211,17 @@ CONFIGS = {
     # 3D, n=2^20, exp(-r/0.2), m=64, 4x4x4 Chebyshev (k=64), eta=0.9
     "3d_n1M": dict(dim=3, n=1 << 20, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=3),
 }
+
+
+def batch_workload(count: int = 256, lo: float = 12.0, hi: float = 17.0, seed: int = 40, nvs=(1, 4, 16)):
+    """The batched workload: `count` independent 2D exponential-covariance matrices (length 0.1,
+    leaf m=32, 4x4 Chebyshev rank k=16, eta=0.9), n_i = floor(2^u) with u ~ U(lo, hi)
+    (log-uniform sizes) and nv_i drawn uniformly from `nvs`. Returns (generate kwargs, nv) pairs;
+    matrix i uses seed 1000 * seed + i + 1."""
+    u = uniform(seed, (count, 2))
+    out = []
+    for i in range(count):
+        n = int(np.floor(2.0 ** (lo + (hi - lo) * u[i, 0])))
+        nv = int(nvs[min(int(u[i, 1] * len(nvs)), len(nvs) - 1)])
+        out.append((dict(dim=2, n=n, m=32, p=4, eta=0.9, kernel="exp", ell=0.1, seed=1000 * seed + i + 1), nv))
+    return out

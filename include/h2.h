@@ -225,6 +225,76 @@ h2_status h2_matvec_static(const h2_desc* d, int64_t n_dense_blocks, int32_t nv,
 /* Free all device memory of the handle (synchronizes the device first). NULL is a no-op. */
 h2_status h2_destroy(h2_handle h);
 
+/*
+ * Batches: many independent H^2 matrices of uneven size multiplied together,
+ * one launch per phase for the whole batch. The paper runs each phase of one
+ * matrix as batched small operations over the nodes of a level (Sec. 3.1,
+ * Sec. 4.2-4.4); a batch extends the same node-parallel phases across
+ * matrices: the tree phases run over (matrix, subtree) jobs, the coupling
+ * phase over the concatenated node rows of all matrices, and the dense phase
+ * over one work list of every matrix's leaf rows, balanced across the SMs by
+ * bytes.
+ */
+typedef struct h2_batch_s* h2_batch;
+
+/*
+ * Group `count` handles (host array, 1 <= count <= 2^23) into a batch.
+ * The handles must be distinct, use the same scaled storage (H2_FP16_SCALED,
+ * H2_BF16_SCALED or H2_INT16_SCALED, not H2_FP64), the same bases_fp32 choice
+ * and the same rank k; their sizes and trees may differ. The batch refers to
+ * the handles (it copies none of their blocks) and uses their work space:
+ * keep them alive until h2_batch_destroy, and do not run a product of a
+ * member handle, alone or in another batch, concurrently with a product of
+ * this batch (order them on one stream). Errors: H2_ERR_INVALID (NULL,
+ * duplicates, mixed forms or ranks), H2_ERR_UNSUPPORTED (H2_FP64 handles),
+ * H2_ERR_OOM, H2_ERR_CUDA.
+ */
+h2_status h2_batch_create(const h2_handle* hs, int32_t count, h2_batch* out);
+
+/*
+ * y_i = A_i x_i for every member i (host arrays of `count` entries each):
+ *   nv[i]     vectors of matrix i (>= 0; 0 skips the matrix: its x[i] and
+ *             y[i] are not touched and may be NULL)
+ *   x[i]      device FP64, n_i x nv[i] column-major, leading dimension
+ *             ldx[i] >= n_i
+ *   y[i]      device FP64, n_i x nv[i], ldy[i] >= n_i; overwritten; must not
+ *             overlap any x or another y
+ * Works in passes of up to 16 vectors per matrix (as many as the largest
+ * nv[i] needs). A pass launches ceil(count / 256) small kernels that write
+ * the pointers into the batch's device table, then for each vector-count
+ * bucket present among the members (1, 2, 3-4, 5-8, 9-16 vectors) one launch
+ * of each tree and coupling phase (covering every member of the bucket), and
+ * one launch of the dense phase for all members. Every launch goes to
+ * `stream` (cudaStream_t, NULL = the default stream), so the call can be
+ * captured in a CUDA graph (the pointers and counts are baked into the
+ * graph). Asynchronous: bounded-wait failures surface through
+ * h2_batch_check. Errors: H2_ERR_INVALID, H2_ERR_CUDA.
+ */
+h2_status h2_batch_matvec(h2_batch b, const int32_t* nv, const double* const* x, const int64_t* ldx,
+                          double* const* y, const int64_t* ldy, void* stream);
+
+/* Synchronize `stream`, then report H2_ERR_TIMEOUT (and clear it) if a bounded
+ * device wait of a batched product ran out since the last check. */
+h2_status h2_batch_check(h2_batch b, void* stream);
+
+/*
+ * info[0] members, [1] coupling rows (sum of the members' node counts),
+ * [2] tree jobs (subtree CTAs of the tree phases), [3] dense work items,
+ * [4] device bytes the batch itself holds, [5] kernel launches of one pass
+ * whose members all fall in one vector-count bucket (each further bucket
+ * present adds 3).
+ */
+h2_status h2_batch_info(h2_batch b, int64_t info[6]);
+
+/* Per-phase timing of batched products, as h2_profile / h2_profile_read for a
+ * handle: the phases are those of H2_NPHASES; the launch count includes the
+ * pointer-table kernels. */
+h2_status h2_batch_profile(h2_batch b, int32_t enable);
+h2_status h2_batch_profile_read(h2_batch b, double ms[H2_NPHASES], int64_t* launches);
+
+/* Free the batch's own tables (not the member handles). NULL is a no-op. */
+h2_status h2_batch_destroy(h2_batch b);
+
 /* Message of the calling thread's last failed call ("" if none). Valid until the next call. */
 const char* h2_last_error(void);
 

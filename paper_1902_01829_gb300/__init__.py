@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
 
 # every symbol include/h2.h declares
 EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
-           "h2_profile_read", "h2_matvec_static", "h2_destroy", "h2_last_error"]
+           "h2_profile_read", "h2_matvec_static", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
+           "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy", "h2_last_error"]
 PHASES = ["upsweep", "coupling", "downsweep", "dense_expand"]
 
 
@@ -57,9 +58,17 @@ def _load():
     lib.h2_matvec_static.argtypes = [ctypes.POINTER(h2_desc), i64, i32, vp, i64, vp, i64, vp]
     lib.h2_debug_withhold_copy.argtypes = [vp, i32, i64]
     lib.h2_profile_read.argtypes = [vp, vp, vp]
+    lib.h2_batch_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
+    lib.h2_batch_matvec.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.h2_batch_check.argtypes = [vp, vp]
+    lib.h2_batch_info.argtypes = [vp, vp]
+    lib.h2_batch_destroy.argtypes = [vp]
+    lib.h2_batch_profile.argtypes = [vp, i32]
+    lib.h2_batch_profile_read.argtypes = [vp, vp, vp]
     lib.h2_last_error.restype = ctypes.c_char_p
     for name in ("h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
-                 "h2_profile_read", "h2_matvec_static", "h2_destroy"):
+                 "h2_profile_read", "h2_matvec_static", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
+                 "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -179,6 +188,90 @@ class H2Matrix:
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.h2_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class H2Batch:
+    """Independent precision-form matrices multiplied together, one launch per phase
+    (h2_batch_create / h2_batch_matvec). Keeps its member H2Matrix objects alive."""
+
+    def __init__(self, mats):
+        self.mats = list(mats)
+        arr = (ctypes.c_void_p * len(self.mats))(*[m._h.value for m in self.mats])
+        self._b = ctypes.c_void_p()
+        _check(_lib.h2_batch_create(arr, len(self.mats), ctypes.byref(self._b)))
+
+    def prepare(self, xs, ys):
+        """Argument arrays of h2_batch_matvec for lists of (n_i, nv_i) column-major torch tensors
+        (None or nv_i = 0 skips a matrix)."""
+        count = len(self.mats)
+        assert len(xs) == count and len(ys) == count
+        nv = np.zeros(count, dtype=np.int32)
+        ldx = np.zeros(count, dtype=np.int64)
+        ldy = np.zeros(count, dtype=np.int64)
+        xp = (ctypes.c_void_p * count)()
+        yp = (ctypes.c_void_p * count)()
+        for i, (m, x, y) in enumerate(zip(self.mats, xs, ys)):
+            if x is None or (x.dim() == 2 and x.shape[1] == 0):
+                continue
+            X = x.unsqueeze(1) if x.dim() == 1 else x
+            Y = y.unsqueeze(1) if y.dim() == 1 else y
+            assert X.stride(0) == 1 and Y.stride(0) == 1 and X.shape == Y.shape and X.shape[0] == m.n
+            nv[i] = X.shape[1]
+            ldx[i] = X.stride(1) if X.shape[1] > 1 else m.n
+            ldy[i] = Y.stride(1) if Y.shape[1] > 1 else m.n
+            xp[i] = X.data_ptr()
+            yp[i] = Y.data_ptr()
+        return (nv, xp, ldx, yp, ldy)
+
+    def matvec_prepared(self, args, stream=None):
+        nv, xp, ldx, yp, ldy = args
+        _check(_lib.h2_batch_matvec(self._b, _ptr(nv), xp, _ptr(ldx), yp, _ptr(ldy), _stream_ptr(stream)))
+
+    def matvec(self, xs, ys=None, stream=None):
+        """ys[i] = A_i xs[i]; xs: list of float64 CUDA tensors (n_i,) or (n_i, nv_i) column-major."""
+        import torch
+        if ys is None:
+            ys = []
+            for m, x in zip(self.mats, xs):
+                if x is None:
+                    ys.append(None)
+                elif x.dim() == 1:
+                    ys.append(torch.empty(m.n, dtype=torch.float64, device=x.device))
+                else:
+                    ys.append(torch.empty((x.shape[1], m.n), dtype=torch.float64, device=x.device).t())
+        self.matvec_prepared(self.prepare(xs, ys), stream)
+        return ys
+
+    def check(self, stream=None):
+        _check(_lib.h2_batch_check(self._b, _stream_ptr(stream)))
+
+    def profile(self, enable: bool = True):
+        """Record per-phase CUDA events in every batched product while enabled (h2_batch_profile)."""
+        _check(_lib.h2_batch_profile(self._b, 1 if enable else 0))
+
+    def profile_read(self) -> tuple[dict, int]:
+        """Summed milliseconds per phase since the last read, and the kernel launch count."""
+        ms = np.zeros(len(PHASES), dtype=np.float64)
+        n = np.zeros(1, dtype=np.int64)
+        _check(_lib.h2_batch_profile_read(self._b, _ptr(ms), _ptr(n)))
+        return dict(zip(PHASES, ms.tolist())), int(n[0])
+
+    def info(self) -> dict:
+        a = np.zeros(6, dtype=np.int64)
+        _check(_lib.h2_batch_info(self._b, _ptr(a)))
+        keys = ["members", "coupling_rows", "tree_jobs", "dense_items", "device_bytes", "launches_per_pass"]
+        return {key: int(v) for key, v in zip(keys, a)}
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            _lib.h2_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -41,8 +41,7 @@ namespace {
 h2_status (&fail)(h2_status, const char*, ...) = h2_fail;
 
 void free_all(h2_matrix_s* h) {
-  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-  h->events.clear();
+  profile_free(&h->prof);
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->hx) cudaFree(h->hx);
@@ -246,15 +245,37 @@ h2_status upload_items(h2_matrix_s* h, ItemList* L, const std::vector<h2::Stream
 namespace h2i {
 
 // record a phase-boundary event when profiling (events are pooled per handle)
-cudaError_t mark(h2_matrix_s* h, cudaStream_t st) {
-  if (!h->profiling) return cudaSuccess;
-  if (h->ev_used == h->events.size()) {
+cudaError_t mark(Profiler* p, cudaStream_t st) {
+  if (!p->on) return cudaSuccess;
+  if (p->used == p->events.size()) {
     cudaEvent_t e;
     cudaError_t err = cudaEventCreate(&e);
     if (err != cudaSuccess) return err;
-    h->events.push_back(e);
+    p->events.push_back(e);
   }
-  return cudaEventRecord(h->events[h->ev_used++], st);
+  return cudaEventRecord(p->events[p->used++], st);
+}
+
+h2_status profile_read(Profiler* p, double ms[H2_NPHASES], int64_t* launches) {
+  for (int i = 0; i < H2_NPHASES; i++) ms[i] = 0.0;
+  const size_t per = H2_NPHASES + 1;
+  if (p->used) CUDA_TRY(cudaEventSynchronize(p->events[p->used - 1]));
+  for (size_t base = 0; base + per <= p->used; base += per)
+    for (int i = 0; i < H2_NPHASES; i++) {
+      float t = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&t, p->events[base + i], p->events[base + i + 1]));
+      ms[i] += t;
+    }
+  if (launches) *launches = p->launches;
+  p->used = 0;
+  p->launches = 0;
+  return H2_OK;
+}
+
+void profile_free(Profiler* p) {
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  p->events.clear();
+  p->used = 0;
 }
 
 }  // namespace h2i
@@ -302,9 +323,9 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
   T.L = h->tree_L;
   T.nv = nv;
   const unsigned tree_grid = 1u << h->tree_L, tree_threads = kTreeWarps * 32;
-  cudaError_t me = mark(h, st);
+  cudaError_t me = mark(&h->prof, st);
   k_upsweep_tree<RPL_K, NVB><<<tree_grid, tree_threads, 0, st>>>(T);
-  if (me == cudaSuccess) me = mark(h, st);
+  if (me == cudaSuccess) me = mark(&h->prof, st);
   if (h->pair_rows) {
     constexpr int CB = NVB <= 2 ? 4 : (NVB <= 4 ? 2 : 1);
     if (h->s_tiny)
@@ -317,9 +338,9 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
     k_coupling_generic<RPL_K, NVB><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, LR, h->n_nodes,
                                                                      nv, h->xhat, h->yhat);
   }
-  if (me == cudaSuccess) me = mark(h, st);
+  if (me == cudaSuccess) me = mark(&h->prof, st);
   k_downsweep_tree<RPL_K, NVB><<<tree_grid, tree_threads, 0, st>>>(T);
-  if (me == cudaSuccess) me = mark(h, st);
+  if (me == cudaSuccess) me = mark(&h->prof, st);
   StreamParams P{};
   P.items = h->dense_items.items;
   P.cta_begin = h->dense_items.cta_begin;
@@ -337,8 +358,8 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
     h->inject = -1;
     h->budget = kWaitBudget;
   }
-  if (me == cudaSuccess) me = mark(h, st);
-  h->launches += 4;
+  if (me == cudaSuccess) me = mark(&h->prof, st);
+  h->prof.launches += 4;
   if (me != cudaSuccess) return fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(H2_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
@@ -621,27 +642,15 @@ h2_status h2_info(h2_handle h, int64_t info[8]) {
 
 h2_status h2_profile(h2_handle h, int32_t enable) {
   if (!h) return fail(H2_ERR_INVALID, "NULL handle");
-  h->profiling = enable != 0;
-  h->ev_used = 0;
-  h->launches = 0;
+  h->prof.on = enable != 0;
+  h->prof.used = 0;
+  h->prof.launches = 0;
   return H2_OK;
 }
 
 h2_status h2_profile_read(h2_handle h, double ms[H2_NPHASES], int64_t* launches) {
   if (!h || !ms) return fail(H2_ERR_INVALID, "NULL handle or output");
-  for (int p = 0; p < H2_NPHASES; p++) ms[p] = 0.0;
-  const size_t per = H2_NPHASES + 1;
-  if (h->ev_used) CUDA_TRY(cudaEventSynchronize(h->events[h->ev_used - 1]));
-  for (size_t base = 0; base + per <= h->ev_used; base += per)
-    for (int p = 0; p < H2_NPHASES; p++) {
-      float t = 0.f;
-      CUDA_TRY(cudaEventElapsedTime(&t, h->events[base + p], h->events[base + p + 1]));
-      ms[p] += t;
-    }
-  if (launches) *launches = h->launches;
-  h->ev_used = 0;
-  h->launches = 0;
-  return H2_OK;
+  return profile_read(&h->prof, ms, launches);
 }
 
 h2_status h2_destroy(h2_handle h) {

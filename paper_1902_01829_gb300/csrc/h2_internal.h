@@ -19,6 +19,8 @@ void h2_internal_set_error(const char* msg);
     }                                                                                                         \
   } while (0)
 
+struct h2_matrix_s;
+
 namespace h2i {
 
 constexpr int kMaxLeaf = 64;
@@ -33,6 +35,33 @@ struct ItemList {
   h2::StreamItem* items = nullptr;  // device
   int* cta_begin = nullptr;         // device [grid + 1]
   int64_t count = 0;
+};
+
+// per-phase profiling: CUDA events recorded at phase boundaries while enabled
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> events;  // pooled
+  size_t used = 0;
+  int64_t launches = 0;
+};
+
+// what one precision-form product launches over: a table of matrices (one
+// matrix, or a batch), the tree jobs, the coupling row map and the dense items
+struct MixedLaunch {
+  void* mats = nullptr;              // device h2::MatDesc table
+  const int2* jobs = nullptr;        // (matrix, subtree) per tree CTA
+  int64_t njobs = 0;
+  const int4* chunks = nullptr;      // coupling row chunks {matrix, first row, rows, 0}
+  int64_t nchunks = 0;
+  const h2::StreamItem* items = nullptr;
+  const int* cta_begin = nullptr;    // [grid + 1]
+  const void* blk = nullptr;         // h2::MixedBlock records
+  int grid = 0;
+  int* err = nullptr;
+  long long budget = kWaitBudget;
+  int k = 0;
+  bool bases_fp32 = false;
+  Profiler* prof = nullptr;          // profiler whose events mark the phases (or none)
 };
 
 // device copy of the precision form (per-block scaled 16-bit storage, FP32 arithmetic)
@@ -56,7 +85,23 @@ struct MixedData {
   float* yhat = nullptr;
   int kp4 = 0;                // k rounded up to a multiple of 4
   int64_t kk8 = 0;            // k*k rounded up to a multiple of 8
+  int64_t nblk = 0;           // dense-stream blocks (dense blocks + one U per leaf row)
+  // the table-driven kernels' tables for this matrix alone (a batch of one)
+  MixedLaunch launch;
+  std::vector<h2::StreamItem> items_host;  // the dense items (matrix index 0), kept for batches
+  std::vector<int64_t> row_bytes;          // bytes each leaf row streams (load balance)
+  std::vector<int64_t> row_item0;          // first item of each leaf row, [leaves + 1]
+  std::vector<int4> chunks_host;           // coupling row chunks (matrix index 0)
 };
+
+// vector-count buckets of the precision-form kernels: bucket b runs the
+// variant for up to kBucketNV[b] vectors and takes counts kBucketLo[b] ..
+constexpr int kBuckets = 5;
+constexpr int kBucketNV[kBuckets] = {1, 2, 4, 8, 16};
+constexpr int kBucketLo[kBuckets] = {1, 2, 3, 5, 9};
+inline int bucket_of(int nv) { return nv <= 1 ? 0 : nv <= 2 ? 1 : nv <= 4 ? 2 : nv <= 8 ? 3 : 4; }
+inline int bucket_count(unsigned mask) { return __builtin_popcount(mask); }
+
 
 }  // namespace h2i
 
@@ -87,11 +132,7 @@ struct h2_matrix_s {
   float2* yhat = nullptr;
   long long budget = h2i::kWaitBudget;
   int inject = -1;
-  // per-phase profiling: events recorded at phase boundaries while enabled
-  bool profiling = false;
-  std::vector<cudaEvent_t> events;
-  size_t ev_used = 0;
-  int64_t launches = 0;
+  h2i::Profiler prof;
   // host-buffer staging (h2_matvec_host)
   double* hx = nullptr;
   double* hy = nullptr;
@@ -128,9 +169,24 @@ h2_status upload(h2_matrix_s* h, T** p, const T* src, int64_t count) {
 // rows weighed by bytes -> first item of each of `grid` contiguous, about equal ranges
 std::vector<int> balance(const std::vector<int64_t>& row_bytes, const std::vector<int64_t>& row_item0, int grid);
 // record a phase-boundary event when profiling
-cudaError_t mark(h2_matrix_s* h, cudaStream_t st);
+cudaError_t mark(Profiler* p, cudaStream_t st);
+// summed milliseconds per phase since the last read (groups of H2_NPHASES + 1 events), then reset
+h2_status profile_read(Profiler* p, double ms[H2_NPHASES], int64_t* launches);
+void profile_free(Profiler* p);
 // precision form: device layout (h2_create) and one product pass of up to kPassVectors vectors
 h2_status mixed_build(h2_matrix_s* h, const h2_desc* d);
+// one product pass; buckets: bit b set when some matrix has a vector count in bucket b
+h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st);
 h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st);
 
 }  // namespace h2i
+
+// A batch of precision-form matrices multiplied by one launch per phase.
+struct h2_batch_s {
+  std::vector<h2_matrix_s*> hs;  // the member handles (not owned)
+  int storage = 0;
+  h2i::MixedLaunch launch;       // over the concatenated tables
+  h2i::Profiler prof;
+  int64_t n_items = 0, device_bytes = 0;
+  std::vector<void*> allocs;
+};

@@ -19,7 +19,7 @@
 namespace h2i {
 
 template <int F>
-h2_status mixed_pass_form(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st);
+h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st);
 
 }  // namespace h2i
 
@@ -89,6 +89,100 @@ float quantize_transposed(const double* a, int64_t rows, int64_t cols, int form,
   for (int64_t c = 0; c < cols; c++)
     for (int64_t r = 0; r < rows; r++) codes[c + cols * r] = tmp[r + rows * c];
   return s;
+}
+
+// the product's fields (vectors, leading dimensions, vector counts) of up to
+// kCallChunk matrices, passed by value so that a captured graph replays them
+constexpr int kCallChunk = 256;
+struct CallChunk {
+  int first, count;
+  const double* x[kCallChunk];
+  double* y[kCallChunk];
+  long long ldx[kCallChunk];
+  long long ldy[kCallChunk];
+  int nv[kCallChunk];
+};
+static_assert(sizeof(CallChunk) < 32000, "kernel parameter space");
+
+__global__ void k_set_calls(h2::MatDesc* mats, CallChunk c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < c.count) {
+    h2::MatDesc& D = mats[c.first + i];
+    D.x = c.x[i];
+    D.ldx = c.ldx[i];
+    D.y = c.y[i];
+    D.ldy = c.ldy[i];
+    D.nv = c.nv[i];
+  }
+}
+
+// coupling row chunks of one matrix: consecutive rows, at most kChunkRows rows
+// and (unless one row alone has more) about kChunkBlocks coupling blocks each
+constexpr int64_t kChunkBlocks = 64;
+std::vector<int4> coupling_chunks(const int32_t* Srow, int64_t n_nodes) {
+  std::vector<int4> out;
+  for (int64_t r = 0; r < n_nodes;) {
+    const int64_t r0 = r;
+    int64_t blocks = 0;
+    while (r < n_nodes && r - r0 < h2::kChunkRows &&
+           (r == r0 || blocks + (Srow[r + 1] - Srow[r]) <= kChunkBlocks)) {
+      blocks += Srow[r + 1] - Srow[r];
+      r++;
+    }
+    out.push_back(make_int4(0, (int)r0, (int)(r - r0), 0));
+  }
+  return out;
+}
+
+// static fields of a handle's matrix descriptor; row0 = its first row in the coupling row space
+h2::MatDesc fill_desc(const h2_matrix_s* h, int tree_L) {
+  const MixedData& M = h->mx;
+  h2::MatDesc D{};
+  D.dmat = static_cast<const char*>(M.dmat);
+  D.smat = M.smat;
+  D.sscale = M.sscale;
+  D.Srow = h->Srow;
+  D.Scol = h->Scol;
+  D.Vt = M.Vt;
+  D.vscale = M.vscale;
+  D.vt_off = M.vt_off;
+  D.Ft = M.Ft;
+  D.fscale = M.fscale;
+  D.E = M.E;
+  D.escale = M.escale;
+  D.leaf_off = h->leaf_off;
+  D.xp4_off = M.xp4_off;
+  D.x4 = M.x4;
+  D.xhat = M.xhat;
+  D.yhat = M.yhat;
+  D.ticket = h->ticket;
+  D.kk8 = M.kk8;
+  D.n_nodes = h->n_nodes;
+  D.k = h->k;
+  D.kp = M.kp4;
+  D.LR = h->lr;
+  D.q = h->q;
+  D.L = tree_L;
+  return D;
+}
+
+// write the fields of one product pass into a matrix table (entries [0, count))
+h2_status set_calls(h2::MatDesc* mats, int64_t count, const int* nv, const double* const* x, const int64_t* ldx,
+                    double* const* y, const int64_t* ldy, cudaStream_t st) {
+  for (int64_t c0 = 0; c0 < count; c0 += kCallChunk) {
+    CallChunk c{};
+    c.first = (int)c0;
+    c.count = (int)std::min<int64_t>(kCallChunk, count - c0);
+    for (int i = 0; i < c.count; i++) {
+      c.x[i] = x[c0 + i];
+      c.y[i] = y[c0 + i];
+      c.ldx[i] = ldx[c0 + i];
+      c.ldy[i] = ldy[c0 + i];
+      c.nv[i] = nv[c0 + i];
+    }
+    k_set_calls<<<(c.count + 127) / 128, 128, 0, st>>>(mats, c);
+  }
+  return H2_OK;
 }
 
 }  // namespace
@@ -233,7 +327,8 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
     if ((st = upload(h, &dblk, blk.data(), nblk)) != H2_OK) return st;
     M.dblk = dblk;
 
-    // work items: consecutive blocks of one row, at most 4 and 32 KB per item
+    // work items: consecutive blocks of one row, at most kMixedMaxBlocks blocks, 32 KB of
+    // entries and kMixedVecCols vector columns per item
     std::vector<h2::StreamItem> items;
     std::vector<int64_t> row_bytes((size_t)leaves), row_item0((size_t)leaves + 1);
     for (int64_t i = 0; i < leaves; i++) {
@@ -241,9 +336,11 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
       const int64_t g0 = row_blk0[i], g1 = row_blk0[i + 1];
       int64_t bytes = 0;
       for (int64_t g = g0; g < g1;) {
-        int64_t e = g, mb = 0;
-        while (e < g1 && e - g < h2::kMixedMaxBlocks && mb + (boff[e + 1] - boff[e]) <= h2::kStageMat) {
+        int64_t e = g, mb = 0, vc = 0;
+        while (e < g1 && e - g < h2::kMixedMaxBlocks && mb + (boff[e + 1] - boff[e]) <= h2::kStageMat &&
+               vc + blk[e].vs <= h2::kMixedVecCols) {
           mb += boff[e + 1] - boff[e];
+          vc += blk[e].vs;
           e++;
         }
         h2::StreamItem it{};
@@ -254,7 +351,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
         it.row = (int)lo[i];
         it.flags = (e == g1) ? h2::kItemFlagLast : 0;
         items.push_back(it);
-        for (int64_t u = g; u < e; u++) bytes += mb / (e - g) + 4 * blk[u].vs;
+        bytes += mb + 4 * vc + 512;  // entries, one vector's columns, and a fixed cost per item
         g = e;
       }
       row_bytes[i] = bytes;
@@ -269,29 +366,330 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
       const int nb = (int)((it.shape >> 8) & 0xFF);
       bool ok = it.m_off % 16 == 0 && it.m_bytes % 16 == 0 && it.m_bytes > 0 && it.m_bytes <= h2::kStageMat &&
                 it.m_off + it.m_bytes <= total && nb >= 1 && nb <= h2::kMixedMaxBlocks && it.v_off + nb <= nblk;
+      int64_t vc = 0;
       for (int u = 0; ok && u < nb; u++) {
         const h2::MixedBlock& m = blk[it.v_off + u];
-        const int64_t lim = m.src ? nodes * M.kp4 : xp4[leaves];
+        const int64_t lim = (m.src & 1) ? nodes * M.kp4 : xp4[leaves];
         ok = m.vs % 4 == 0 && m.vs >= m.cols && m.vs <= 64 && m.voff % 4 == 0 && m.voff + m.vs <= lim;
+        vc += m.vs;
       }
+      ok = ok && vc <= h2::kMixedVecCols;
       if (!ok) return h2_fail(H2_ERR_INVALID, "internal: precision-form work item %lld fails the layout audit", (long long)t);
     }
     if ((st = upload(h, &M.dense_items.items, items.data(), (int64_t)items.size())) != H2_OK) return st;
     if ((st = upload(h, &M.dense_items.cta_begin, begin.data(), (int64_t)begin.size())) != H2_OK) return st;
     M.dense_items.count = (int64_t)items.size();
+    M.nblk = nblk;
+    M.items_host = std::move(items);
+    M.row_bytes = std::move(row_bytes);
+    M.row_item0 = std::move(row_item0);
   }
   if ((st = dalloc(h, &M.x4, xp4[leaves] * kPassVectors)) != H2_OK) return st;
   if ((st = dalloc(h, &M.xhat, nodes * kPassVectors * M.kp4)) != H2_OK) return st;
   if ((st = dalloc(h, &M.yhat, nodes * kPassVectors * M.kp4)) != H2_OK) return st;
+  // entries k .. kp4 - 1 of every node vector are padding that no kernel writes except with
+  // zeros; the dense stream multiplies them by zero codes, so they must be finite
+  CUDA_TRY(cudaMemset(M.xhat, 0, (size_t)(nodes * kPassVectors * M.kp4) * sizeof(float)));
+  CUDA_TRY(cudaMemset(M.yhat, 0, (size_t)(nodes * kPassVectors * M.kp4) * sizeof(float)));
+
+  // tables of the table-driven kernels: this matrix alone
+  MixedLaunch& L = M.launch;
+  const h2::MatDesc D = fill_desc(h, h->tree_L);
+  h2::MatDesc* md = nullptr;
+  if ((st = upload(h, &md, &D, 1)) != H2_OK) return st;
+  L.mats = md;
+  std::vector<int2> jobs((size_t)1 << h->tree_L);
+  for (size_t t = 0; t < jobs.size(); t++) jobs[t] = make_int2(0, (int)t);
+  int2* dj = nullptr;
+  if ((st = upload(h, &dj, jobs.data(), (int64_t)jobs.size())) != H2_OK) return st;
+  L.jobs = dj;
+  L.njobs = (int64_t)jobs.size();
+  M.chunks_host = coupling_chunks(d->S_rowptr, nodes);
+  int4* dc = nullptr;
+  if ((st = upload(h, &dc, M.chunks_host.data(), (int64_t)M.chunks_host.size())) != H2_OK) return st;
+  L.chunks = dc;
+  L.nchunks = (int64_t)M.chunks_host.size();
+  L.items = M.dense_items.items;
+  L.cta_begin = M.dense_items.cta_begin;
+  L.blk = M.dblk;
+  L.grid = h->grid;
+  L.err = h->err;
+  L.k = k;
+  L.bases_fp32 = M.bases_fp32;
   return H2_OK;
 }
 
-h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
-  switch (form_of(h->storage)) {
-    case h2::kFormFp16: return mixed_pass_form<h2::kFormFp16>(h, nv, x, ldx, y, ldy, st);
-    case h2::kFormBf16: return mixed_pass_form<h2::kFormBf16>(h, nv, x, ldx, y, ldy, st);
-    default: return mixed_pass_form<h2::kFormInt16>(h, nv, x, ldx, y, ldy, st);
+h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st) {
+  switch (form_of(storage)) {
+    case h2::kFormFp16: return mixed_pass_form<h2::kFormFp16>(L, buckets, st);
+    case h2::kFormBf16: return mixed_pass_form<h2::kFormBf16>(L, buckets, st);
+    default: return mixed_pass_form<h2::kFormInt16>(L, buckets, st);
   }
 }
 
+h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
+  MixedLaunch L = h->mx.launch;
+  L.budget = h->budget;
+  L.prof = &h->prof;
+  cudaError_t me = mark(&h->prof, st);
+  if (me != cudaSuccess) return h2_fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
+  h2_status s = set_calls(static_cast<h2::MatDesc*>(L.mats), 1, &nv, &x, &ldx, &y, &ldy, st);
+  if (s != H2_OK) return s;
+  h->prof.launches += 5;
+  return mixed_launch(h->storage, L, 1u << bucket_of(nv), st);
+}
+
 }  // namespace h2i
+
+// ------------------------------------------------------------------ batches
+namespace {
+
+template <class T>
+h2_status balloc(h2_batch_s* b, T** p, int64_t count, const T* src = nullptr) {
+  *p = nullptr;
+  if (count <= 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return h2_fail(e == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA, "cudaMalloc of %lld bytes failed: %s",
+                   (long long)(count * sizeof(T)), cudaGetErrorString(e));
+  }
+  b->allocs.push_back(q);
+  b->device_bytes += count * (int64_t)sizeof(T);
+  *p = (T*)q;
+  if (src) CUDA_TRY(cudaMemcpy(q, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice));
+  return H2_OK;
+}
+
+void batch_free(h2_batch_s* b) {
+  for (void* p : b->allocs) cudaFree(p);
+  b->allocs.clear();
+  profile_free(&b->prof);
+}
+
+h2_status batch_build(h2_batch_s* b) {
+  const int64_t count = (int64_t)b->hs.size();
+  const h2_matrix_s* h0 = b->hs[0];
+  MixedLaunch& L = b->launch;
+  h2_status st;
+  // subtree level per matrix: at most 64 leaves per tree CTA, fewer while the
+  // whole batch has under four CTAs per SM
+  auto jobs_for = [&](int T) {
+    int64_t s = 0;
+    for (const h2_matrix_s* h : b->hs) s += (int64_t)1 << std::max(0, h->q - T);
+    return s;
+  };
+  int T = 6;
+  while (T > 0 && jobs_for(T) < 4 * (int64_t)h0->grid) T--;
+  std::vector<h2::MatDesc> descs((size_t)count);
+  std::vector<int2> jobs;
+  std::vector<int4> chunks;
+  std::vector<h2::StreamItem> items;
+  std::vector<int64_t> row_bytes, row_item0;
+  int64_t blk0 = 0;
+  for (int64_t i = 0; i < count; i++) {
+    const h2_matrix_s* h = b->hs[(size_t)i];
+    const MixedData& M = h->mx;
+    const int Li = std::max(0, h->q - T);
+    descs[(size_t)i] = fill_desc(h, Li);
+    for (int64_t t = 0; t < ((int64_t)1 << Li); t++) jobs.push_back(make_int2((int)i, (int)t));
+    for (int4 c : M.chunks_host) {
+      c.x = (int)i;
+      chunks.push_back(c);
+    }
+    const int64_t item0 = (int64_t)items.size();
+    for (h2::StreamItem it : M.items_host) {
+      it.v_off += blk0;
+      it.flags = (it.flags & 0xFF) | (int)(i << 8);
+      items.push_back(it);
+    }
+    for (size_t r = 0; r + 1 < M.row_item0.size(); r++) {
+      row_item0.push_back(item0 + M.row_item0[r]);
+      row_bytes.push_back(M.row_bytes[r]);
+    }
+    blk0 += M.nblk;
+  }
+  row_item0.push_back((int64_t)items.size());
+  if ((int64_t)items.size() >= INT32_MAX || (int64_t)jobs.size() >= INT32_MAX)
+    return h2_fail(H2_ERR_UNSUPPORTED, "batch too large: %lld dense items, %lld tree jobs", (long long)items.size(),
+                   (long long)jobs.size());
+  const std::vector<int> begin = balance(row_bytes, row_item0, h0->grid);
+  for (size_t c = 0; c + 1 < begin.size(); c++)
+    if (begin[c] > begin[c + 1]) return h2_fail(H2_ERR_INVALID, "internal: item ranges not monotone");
+  for (const h2::StreamItem& it : items)  // the member audits hold; only the block index moved
+    if (it.v_off < 0 || it.v_off + ((it.shape >> 8) & 0xFF) > blk0)
+      return h2_fail(H2_ERR_INVALID, "internal: batched work item outside the block records");
+
+  h2::MatDesc* md = nullptr;
+  if ((st = balloc(b, &md, count, descs.data())) != H2_OK) return st;
+  int2* dj = nullptr;
+  if ((st = balloc(b, &dj, (int64_t)jobs.size(), jobs.data())) != H2_OK) return st;
+  int4* dc = nullptr;
+  if ((st = balloc(b, &dc, (int64_t)chunks.size(), chunks.data())) != H2_OK) return st;
+  h2::StreamItem* di = nullptr;
+  if ((st = balloc(b, &di, (int64_t)items.size(), items.data())) != H2_OK) return st;
+  int* db = nullptr;
+  if ((st = balloc(b, &db, (int64_t)begin.size(), begin.data())) != H2_OK) return st;
+  h2::MixedBlock* blk = nullptr;
+  if ((st = balloc(b, &blk, blk0)) != H2_OK) return st;
+  for (int64_t i = 0, o = 0; i < count; o += b->hs[(size_t)i]->mx.nblk, i++)
+    CUDA_TRY(cudaMemcpy(blk + o, b->hs[(size_t)i]->mx.dblk, (size_t)b->hs[(size_t)i]->mx.nblk * sizeof(h2::MixedBlock),
+                        cudaMemcpyDeviceToDevice));
+  int* err = nullptr;
+  if ((st = balloc(b, &err, 1)) != H2_OK) return st;
+  CUDA_TRY(cudaMemset(err, 0, sizeof(int)));
+  L.mats = md;
+  L.jobs = dj;
+  L.njobs = (int64_t)jobs.size();
+  L.chunks = dc;
+  L.nchunks = (int64_t)chunks.size();
+  L.items = di;
+  L.cta_begin = db;
+  L.blk = blk;
+  L.grid = h0->grid;
+  L.err = err;
+  L.k = h0->k;
+  L.bases_fp32 = h0->mx.bases_fp32;
+  L.prof = nullptr;
+  b->n_items = (int64_t)items.size();
+  return H2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+h2_status h2_batch_create(const h2_handle* hs, int32_t count, h2_batch* out) {
+  h2_internal_set_error("");
+  if (!out) return h2_fail(H2_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!hs) return h2_fail(H2_ERR_INVALID, "handle array is NULL");
+  if (count < 1 || count > (1 << 23)) return h2_fail(H2_ERR_INVALID, "count = %d outside 1 .. 2^23", count);
+  std::vector<h2_matrix_s*> v((size_t)count);
+  for (int32_t i = 0; i < count; i++) {
+    if (!hs[i]) return h2_fail(H2_ERR_INVALID, "handle %d is NULL", i);
+    v[(size_t)i] = hs[i];
+  }
+  if (v[0]->storage == H2_FP64)
+    return h2_fail(H2_ERR_UNSUPPORTED, "batches take the scaled storage forms only (handle 0 is H2_FP64)");
+  for (int32_t i = 1; i < count; i++) {
+    const h2_matrix_s* h = v[(size_t)i];
+    if (h->storage != v[0]->storage || h->mx.bases_fp32 != v[0]->mx.bases_fp32 || h->k != v[0]->k)
+      return h2_fail(H2_ERR_INVALID, "handle %d differs from handle 0 in storage, bases_fp32 or rank", i);
+  }
+  {
+    std::vector<h2_matrix_s*> sorted = v;
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return h2_fail(H2_ERR_INVALID, "a handle appears twice in the batch");
+  }
+  h2_batch_s* b = new (std::nothrow) h2_batch_s();
+  if (!b) return h2_fail(H2_ERR_OOM, "host allocation failed");
+  b->hs = std::move(v);
+  b->storage = b->hs[0]->storage;
+  h2_status st;
+  try {
+    st = batch_build(b);
+  } catch (const std::bad_alloc&) {
+    st = h2_fail(H2_ERR_OOM, "host allocation failed");
+  }
+  if (st != H2_OK) {
+    batch_free(b);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return H2_OK;
+}
+
+h2_status h2_batch_matvec(h2_batch b, const int32_t* nv, const double* const* x, const int64_t* ldx, double* const* y,
+                          const int64_t* ldy, void* stream) {
+  if (!b) return h2_fail(H2_ERR_INVALID, "NULL batch");
+  if (!nv || !x || !ldx || !y || !ldy) return h2_fail(H2_ERR_INVALID, "NULL argument array");
+  const int64_t count = (int64_t)b->hs.size();
+  int nvmax = 0;
+  for (int64_t i = 0; i < count; i++) {
+    if (nv[i] < 0) return h2_fail(H2_ERR_INVALID, "nv[%lld] = %d < 0", (long long)i, nv[i]);
+    if (nv[i] == 0) continue;
+    if (!x[i] || !y[i]) return h2_fail(H2_ERR_INVALID, "x[%lld] or y[%lld] is NULL", (long long)i, (long long)i);
+    if (ldx[i] < b->hs[(size_t)i]->n || ldy[i] < b->hs[(size_t)i]->n)
+      return h2_fail(H2_ERR_INVALID, "leading dimension of matrix %lld below its n", (long long)i);
+    nvmax = std::max(nvmax, nv[i]);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  MixedLaunch L = b->launch;
+  L.prof = &b->prof;
+  std::vector<int> pnv((size_t)count);
+  std::vector<const double*> px((size_t)count);
+  std::vector<double*> py((size_t)count);
+  std::vector<int64_t> pldx(ldx, ldx + count), pldy(ldy, ldy + count);
+  for (int v0 = 0; v0 < nvmax; v0 += kPassVectors) {
+    unsigned buckets = 0;
+    for (int64_t i = 0; i < count; i++) {
+      const int c = std::max(0, std::min(kPassVectors, nv[i] - v0));
+      pnv[(size_t)i] = c;
+      px[(size_t)i] = c ? x[i] + (int64_t)v0 * ldx[i] : nullptr;
+      py[(size_t)i] = c ? y[i] + (int64_t)v0 * ldy[i] : nullptr;
+      if (c) buckets |= 1u << bucket_of(c);
+    }
+    cudaError_t me = mark(&b->prof, st);
+    if (me != cudaSuccess) return h2_fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
+    h2_status s = set_calls(static_cast<h2::MatDesc*>(L.mats), count, pnv.data(), px.data(), pldx.data(), py.data(),
+                            pldy.data(), st);
+    if (s != H2_OK) return s;
+    b->prof.launches += (count + kCallChunk - 1) / kCallChunk + 3 * bucket_count(buckets) + 1;
+    s = mixed_launch(b->storage, L, buckets, st);
+    if (s != H2_OK) return s;
+  }
+  return H2_OK;
+}
+
+h2_status h2_batch_check(h2_batch b, void* stream) {
+  if (!b) return h2_fail(H2_ERR_INVALID, "NULL batch");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  int e = 0;
+  CUDA_TRY(cudaMemcpy(&e, b->launch.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CUDA_TRY(cudaMemset(b->launch.err, 0, sizeof(int)));
+    return h2_fail(H2_ERR_TIMEOUT, "a bounded device wait ran out; batched products since the last check are invalid");
+  }
+  return H2_OK;
+}
+
+h2_status h2_batch_info(h2_batch b, int64_t info[6]) {
+  if (!b || !info) return h2_fail(H2_ERR_INVALID, "NULL batch or info");
+  const int64_t count = (int64_t)b->hs.size();
+  info[0] = count;
+  int64_t rows = 0;
+  for (const h2_matrix_s* h : b->hs) rows += h->n_nodes;
+  info[1] = rows;
+  info[2] = b->launch.njobs;
+  info[3] = b->n_items;
+  info[4] = b->device_bytes;
+  info[5] = (count + kCallChunk - 1) / kCallChunk + 4;
+  return H2_OK;
+}
+
+h2_status h2_batch_profile(h2_batch b, int32_t enable) {
+  if (!b) return h2_fail(H2_ERR_INVALID, "NULL batch");
+  b->prof.on = enable != 0;
+  b->prof.used = 0;
+  b->prof.launches = 0;
+  return H2_OK;
+}
+
+h2_status h2_batch_profile_read(h2_batch b, double ms[H2_NPHASES], int64_t* launches) {
+  if (!b || !ms) return h2_fail(H2_ERR_INVALID, "NULL batch or output");
+  return profile_read(&b->prof, ms, launches);
+}
+
+h2_status h2_batch_destroy(h2_batch b) {
+  if (!b) return H2_OK;
+  cudaDeviceSynchronize();
+  batch_free(b);
+  delete b;
+  return H2_OK;
+}
+
+}  // extern "C"

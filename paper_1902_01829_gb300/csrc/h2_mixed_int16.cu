@@ -2,6 +2,5 @@
 #include "h2_mixed_launch.cuh"
 
 namespace h2i {
-template h2_status mixed_pass_form<h2::kFormInt16>(h2_matrix_s*, int, const double*, int64_t, double*, int64_t,
-                                                 cudaStream_t);
+template h2_status mixed_pass_form<h2::kFormInt16>(const MixedLaunch&, unsigned, cudaStream_t);
 }  // namespace h2i

@@ -1,6 +1,7 @@
 // Launch sequence of one precision-form product pass (up to kPassVectors
-// vectors) for storage format F. Each h2_mixed_<format>.cu instantiates it
-// once, so the three formats compile in parallel.
+// vectors per matrix) for storage format F, over a table of matrices: one
+// handle, or a batch. Each h2_mixed_<format>.cu instantiates it once, so the
+// three formats compile in parallel.
 #pragma once
 #include "h2_internal.h"
 #include "mixed.cuh"
@@ -16,92 +17,99 @@ cudaError_t set_mixed_smem() {
   return done;
 }
 
+// the tree and coupling launches of one vector-count bucket (phase 0: upsweep, 1: coupling, 2: downsweep)
 template <int F, int FB, int RPL, int NVB>
-h2_status mixed_pass_t(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
+void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st) {
   using namespace h2;
-  MixedData& M = h->mx;
+  const MatDesc* mats = static_cast<const MatDesc*>(L.mats);
+  const unsigned tree_threads = kTreeWarpsM * 32;
+  if (phase == 0 && L.njobs > 0) {
+    k_upsweep_tree_m<FB, RPL, NVB><<<(unsigned)L.njobs, tree_threads, 0, st>>>(mats, L.jobs, nvlo, NVB);
+  } else if (phase == 1 && L.nchunks > 0) {
+    const unsigned cgrid = (unsigned)((L.nchunks + 3) / 4);
+    const int k = L.k;
+    if (k == 16 || k == 32 || k == 64) {
+      // up to four vectors per warp; 8 and 16 vectors take two and four warps per chunk
+      constexpr int NVW = NVB < 4 ? NVB : 4, VG = NVB / NVW;
+      const unsigned grid = (unsigned)((L.nchunks * VG + 3) / 4);
+      if (k == 16) {
+        constexpr int CB = NVW <= 2 ? 4 : 2;
+        k_coupling_m<F, 16, NVW, CB, VG><<<grid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
+      } else if (k == 32) {
+        constexpr int CB = NVW <= 1 ? 2 : 1;
+        k_coupling_m<F, 32, NVW, CB, VG><<<grid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
+      } else {
+        constexpr int CB = NVW <= 1 ? 2 : 1;
+        k_coupling_m<F, 64, NVW, CB, VG><<<grid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
+      }
+    } else {
+      k_coupling_m_generic<F, RPL, NVB><<<cgrid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
+    }
+  } else if (phase == 2 && L.njobs > 0) {
+    k_downsweep_tree_m<FB, RPL, NVB><<<(unsigned)L.njobs, tree_threads, 0, st>>>(mats, L.jobs, nvlo, NVB);
+  }
+}
+
+template <int F, int FB, int RPL>
+void bucket_dispatch(const MixedLaunch& L, int phase, int b, cudaStream_t st) {
+  switch (b) {
+    case 0: return bucket_phase<F, FB, RPL, 1>(L, phase, kBucketLo[0], st);
+    case 1: return bucket_phase<F, FB, RPL, 2>(L, phase, kBucketLo[1], st);
+    case 2: return bucket_phase<F, FB, RPL, 4>(L, phase, kBucketLo[2], st);
+    case 3: return bucket_phase<F, FB, RPL, 8>(L, phase, kBucketLo[3], st);
+    default: return bucket_phase<F, FB, RPL, 16>(L, phase, kBucketLo[4], st);
+  }
+}
+
+template <int F, int NVB>
+h2_status dense_launch(const MixedLaunch& L, cudaStream_t st) {
+  using namespace h2;
   cudaError_t e = set_mixed_smem<F, NVB>();
   if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-  TreeParamsM T{};
-  T.Vt = M.Vt;
-  T.vscale = M.vscale;
-  T.vt_off = M.vt_off;
-  T.Ft = M.Ft;
-  T.fscale = M.fscale;
-  T.E = M.E;
-  T.escale = M.escale;
-  T.leaf_off = h->leaf_off;
-  T.xp4_off = M.xp4_off;
-  T.x = x;
-  T.ldx = ldx;
-  T.x4 = M.x4;
-  T.xhat = M.xhat;
-  T.yhat = M.yhat;
-  T.ticket = h->ticket;
-  T.kk8 = M.kk8;
-  T.k = h->k;
-  T.kp = M.kp4;
-  T.LR = h->lr;
-  T.q = h->q;
-  T.L = h->tree_L;
-  T.nv = nv;
-  const unsigned tree_grid = 1u << h->tree_L, tree_threads = kTreeWarpsM * 32;
-  const unsigned cgrid = (unsigned)((h->n_nodes + 3) / 4);
-  const int k = h->k;
-  cudaError_t me = mark(h, st);
-  k_upsweep_tree_m<FB, RPL, NVB><<<tree_grid, tree_threads, 0, st>>>(T);
-  if (me == cudaSuccess) me = mark(h, st);
-  if (k >= 4 && k <= 64 && (k & (k - 1)) == 0) {
-    constexpr int CB = NVB <= 2 ? 8 : (NVB <= 4 ? 4 : 2);
-    k_coupling_m<F, NVB, CB><<<cgrid, 128, 0, st>>>(M.smat, M.sscale, M.kk8, h->Srow, h->Scol, k, M.kp4, h->n_nodes, nv,
-                                                     M.xhat, M.yhat);
-  } else {
-    k_coupling_m_generic<F, RPL, NVB><<<cgrid, 128, 0, st>>>(M.smat, M.sscale, M.kk8, h->Srow, h->Scol, k, M.kp4, h->lr,
-                                                              h->n_nodes, nv, M.xhat, M.yhat);
-  }
-  if (me == cudaSuccess) me = mark(h, st);
-  k_downsweep_tree_m<FB, RPL, NVB><<<tree_grid, tree_threads, 0, st>>>(T);
-  if (me == cudaSuccess) me = mark(h, st);
   MixedStreamParams P{};
-  P.items = M.dense_items.items;
-  P.cta_begin = M.dense_items.cta_begin;
-  P.mat = reinterpret_cast<const char*>(M.dmat);
-  P.blk = reinterpret_cast<const MixedBlock*>(M.dblk);
-  P.vsrc0 = M.x4;
-  P.vsrc1 = M.yhat;
-  P.nv = nv;
-  P.y = y;
-  P.ldy = ldy;
-  P.err = h->err;
-  P.budget = h->budget;
-  k_dense_stream_m<F, NVB, kMixedCW><<<h->grid, (kMixedCW + 1) * 32, mixed_smem_bytes(NVB, kMixedCW), st>>>(P);
-  if (me == cudaSuccess) me = mark(h, st);
-  h->launches += 4;
+  P.items = L.items;
+  P.cta_begin = L.cta_begin;
+  P.blk = static_cast<const MixedBlock*>(L.blk);
+  P.mats = static_cast<const MatDesc*>(L.mats);
+  P.err = L.err;
+  P.budget = L.budget;
+  k_dense_stream_m<F, NVB, kMixedCW><<<L.grid, (kMixedCW + 1) * 32, mixed_smem_bytes(NVB, kMixedCW), st>>>(P);
+  return H2_OK;
+}
+
+// the phase launches; the caller has written the product's fields into the
+// matrix table and recorded the first profiling mark
+template <int F, int FB, int RPL>
+h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st) {
+  cudaError_t me = cudaSuccess;
+  auto mk = [&]() {
+    if (L.prof && me == cudaSuccess) me = mark(L.prof, st);
+  };
+  for (int phase = 0; phase < 3; phase++) {
+    for (int b = 0; b < kBuckets; b++)
+      if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, st);
+    mk();
+  }
+  const int top = 31 - __builtin_clz(buckets | 1u);
+  h2_status s = top == 0   ? dense_launch<F, 1>(L, st)
+                : top == 1 ? dense_launch<F, 2>(L, st)
+                : top == 2 ? dense_launch<F, 4>(L, st)
+                : top == 3 ? dense_launch<F, 8>(L, st)
+                           : dense_launch<F, 16>(L, st);
+  if (s != H2_OK) return s;
+  mk();
   if (me != cudaSuccess) return h2_fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
   return H2_OK;
 }
 
-template <int F, int FB, int RPL>
-h2_status mixed_pass_nv(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
-  if (nv <= 1) return mixed_pass_t<F, FB, RPL, 1>(h, nv, x, ldx, y, ldy, st);
-  if (nv <= 2) return mixed_pass_t<F, FB, RPL, 2>(h, nv, x, ldx, y, ldy, st);
-  if (nv <= 4) return mixed_pass_t<F, FB, RPL, 4>(h, nv, x, ldx, y, ldy, st);
-  if (nv <= 8) return mixed_pass_t<F, FB, RPL, 8>(h, nv, x, ldx, y, ldy, st);
-  return mixed_pass_t<F, FB, RPL, 16>(h, nv, x, ldx, y, ldy, st);
-}
-
 // FB: format of the bases and transfers (the storage format, or FP32 entries)
-template <int F, int FB>
-h2_status mixed_pass_fb(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
-  return h->k > 32 ? mixed_pass_nv<F, FB, 2>(h, nv, x, ldx, y, ldy, st) : mixed_pass_nv<F, FB, 1>(h, nv, x, ldx, y, ldy, st);
-}
-
 template <int F>
-h2_status mixed_pass_form(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
-  return h->mx.bases_fp32 ? mixed_pass_fb<F, h2::kFormF32>(h, nv, x, ldx, y, ldy, st)
-                          : mixed_pass_fb<F, F>(h, nv, x, ldx, y, ldy, st);
+h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st) {
+  if (L.bases_fp32)
+    return L.k > 32 ? mixed_pass_t<F, h2::kFormF32, 2>(L, buckets, st) : mixed_pass_t<F, h2::kFormF32, 1>(L, buckets, st);
+  return L.k > 32 ? mixed_pass_t<F, F, 2>(L, buckets, st) : mixed_pass_t<F, F, 1>(L, buckets, st);
 }
 
 }  // namespace h2i

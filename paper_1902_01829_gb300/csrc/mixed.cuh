@@ -54,6 +54,39 @@ __device__ __forceinline__ float2 codes_to_f2(uint32_t w) {
                      __uint_as_float(0x4B000000u | (w >> 16)) - 8421376.0f);
 }
 
+// ---------------------------------------------------------------- per-matrix descriptor
+// One entry per matrix of a batch (a single product is a batch of one); the
+// kernels of every phase find their matrix through it. The last group of
+// fields changes with every product.
+struct MatDesc {
+  const char* dmat;      // dense stream: per leaf row its blocks then U_i
+  const uint16_t* smat;  // coupling blocks (kk8 codes each)
+  const float* sscale;
+  const int32_t* Srow;
+  const int32_t* Scol;
+  const void* Vt;        // bases and transfers (codes, or FP32 entries)
+  const float* vscale;
+  const int64_t* vt_off;
+  const void* Ft;
+  const float* fscale;
+  const void* E;
+  const float* escale;
+  const int64_t* leaf_off;
+  const int64_t* xp4_off;
+  float* x4;             // workspace: FP32 x, xhat, yhat
+  float* xhat;
+  float* yhat;
+  int* ticket;
+  long long kk8, n_nodes;
+  int k, kp, LR, q, L, pad0;
+  // per product
+  const double* x;
+  long long ldx;
+  double* y;
+  long long ldy;
+  int nv, pad1;
+};
+
 // ---------------------------------------------------------------- generic warp routine
 // rows += scale * (A * x_cols) for a column-major R x C block of codes; lane
 // = g * LR + rl owns rows rl + 32 r, column groups g take columns g, g + G, ...
@@ -142,6 +175,33 @@ struct TreeParamsM {
 
 constexpr int kTreeWarpsM = 8;
 
+__device__ __forceinline__ TreeParamsM tree_params(const MatDesc& D) {
+  TreeParamsM P;
+  P.Vt = D.Vt;
+  P.vscale = D.vscale;
+  P.vt_off = D.vt_off;
+  P.Ft = D.Ft;
+  P.fscale = D.fscale;
+  P.E = D.E;
+  P.escale = D.escale;
+  P.leaf_off = D.leaf_off;
+  P.xp4_off = D.xp4_off;
+  P.x = D.x;
+  P.ldx = D.ldx;
+  P.x4 = D.x4;
+  P.xhat = D.xhat;
+  P.yhat = D.yhat;
+  P.ticket = D.ticket;
+  P.kk8 = D.kk8;
+  P.k = D.k;
+  P.kp = D.kp;
+  P.LR = D.LR;
+  P.q = D.q;
+  P.L = D.L;
+  P.nv = D.nv;
+  return P;
+}
+
 template <int F, int RPL, int NVB>
 __device__ __forceinline__ void project_leaf_m(const TreeParamsM& P, int64_t j, int lane) {
   const int64_t leaf0 = ((int64_t)1 << P.q) - 1;
@@ -150,7 +210,8 @@ __device__ __forceinline__ void project_leaf_m(const TreeParamsM& P, int64_t j, 
   const int spad = (sj + 3) & ~3;
   float* xj = P.x4 + P.xp4_off[j] * P.nv;
   for (int v = 0; v < P.nv; v++)
-    for (int a = lane; a < sj; a += 32) xj[v * spad + a] = __double2float_rn(P.x[v * P.ldx + off + a]);
+    for (int a = lane; a < spad; a += 32)  // padding columns are zero
+      xj[v * spad + a] = a < sj ? __double2float_rn(P.x[v * P.ldx + off + a]) : 0.f;
   __syncwarp();
   float acc[RPL][NVB];
 #pragma unroll
@@ -191,11 +252,17 @@ __device__ __forceinline__ void up_node_m(const TreeParamsM& P, int64_t p, int l
 }
 
 // leaf projection + the whole upsweep in one launch (see k_upsweep_tree)
+// CTA b works on subtree jobs[b].y of matrix jobs[b].x
 template <int F, int RPL, int NVB>
-__global__ void __launch_bounds__(kTreeWarpsM * 32) k_upsweep_tree_m(TreeParamsM P) {
+// (the matrices whose vector count lies outside [nvlo, nvhi] are left to another launch: all their CTAs return)
+__global__ void __launch_bounds__(kTreeWarpsM * 32) k_upsweep_tree_m(const MatDesc* __restrict__ mats,
+                                                                    const int2* __restrict__ jobs, int nvlo, int nvhi) {
+  const int2 job = jobs[blockIdx.x];
+  const TreeParamsM P = tree_params(mats[job.x]);
+  if (P.nv < nvlo || P.nv > nvhi) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int T = P.q - P.L;
-  const int64_t sub = blockIdx.x;
+  const int64_t sub = job.y;
   for (int64_t t = warp; t < ((int64_t)1 << T); t += kTreeWarpsM) project_leaf_m<F, RPL, NVB>(P, (sub << T) + t, lane);
   __syncthreads();
   for (int lvl = P.q - 1; lvl >= P.L; lvl--) {
@@ -227,10 +294,15 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_upsweep_tree_m(TreeParamsM
 
 // the whole downsweep in one launch (see k_downsweep_tree)
 template <int F, int RPL, int NVB>
-__global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(TreeParamsM P) {
+__global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(const MatDesc* __restrict__ mats,
+                                                                      const int2* __restrict__ jobs, int nvlo,
+                                                                      int nvhi) {
   __shared__ float path[2][NVB][64];
+  const int2 job = jobs[blockIdx.x];
+  const TreeParamsM P = tree_params(mats[job.x]);
+  if (P.nv < nvlo || P.nv > nvhi) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t sub = blockIdx.x;
+  const int64_t sub = job.y;
   const int64_t root = ((int64_t)1 << P.L) - 1 + sub;
   if (warp == 0 && P.L > 0) {
     int cur = 0;
@@ -285,122 +357,235 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(TreeParam
 }
 
 // ---------------------------------------------------------------- coupling, all levels
-// One warp per node row. k = 4 * H with H a power of two (k = 4 .. 64): lane
-// = g * H + h owns rows 4h .. 4h + 3, read as one 8-byte load per column;
-// column groups g = 0 .. G-1 (G = 32 / H) take columns g, g + G, ... The
-// row's (block, column) slots are walked CB at a time, two batches in
-// flight; a block's partial sum is scaled once, after its last column.
-// Blocks are padded to kk8 codes.
-template <int F, int NVB, int CB>
-__global__ void __launch_bounds__(128) k_coupling_m(const uint16_t* __restrict__ S, const float* __restrict__ sscale,
-                                                   int64_t kk8, const int32_t* __restrict__ Srow,
-                                                   const int32_t* __restrict__ Scol, int k, int kp, int64_t n_nodes,
-                                                   int nv, const float* __restrict__ xhat, float* __restrict__ yhat) {
+// The coupling rows of all levels (Eq. 3) are cut into chunks of consecutive
+// rows of one matrix: int4 {matrix, first row, rows (1 .. 31), 0}, about the
+// same number of blocks each. One warp per chunk; a launch serves the
+// matrices whose vector count lies in [nvlo, nvhi] (the others' chunks return
+// at once), so a batch with mixed vector counts runs each count's variant.
+constexpr int kChunkRows = 31;
+
+// chunk state shared by both kernels: row pointers of the chunk in lanes 0 .. rows
+struct ChunkRows {
+  int32_t sr;         // Srow[row0 + lane] (lanes 0 .. rows)
+  unsigned nonempty;  // bit j: row row0 + j has coupling blocks
+};
+
+// rows without coupling blocks get yhat = 0 (vectors vbase .. vbase + vcount - 1);
+// returns the chunk's row pointers
+__device__ __forceinline__ ChunkRows chunk_rows(const int32_t* __restrict__ Srow, float* __restrict__ yhat, int row0,
+                                                int rows, int nv, int kp, int lane, int vbase, int vcount) {
+  ChunkRows c;
+  c.sr = (lane <= rows) ? __ldg(Srow + row0 + lane) : 0;
+  const int32_t next = __shfl_down_sync(0xFFFFFFFFu, c.sr, 1);
+  const bool has = lane < rows && next > c.sr;
+  c.nonempty = __ballot_sync(0xFFFFFFFFu, has);
+  for (int j = 0; j < rows; j++)
+    if (!((c.nonempty >> j) & 1u)) {
+      float* dst = yhat + ((int64_t)(row0 + j) * nv + vbase) * kp;
+      for (int t = lane; t < vcount * kp; t += 32) dst[t] = 0.f;
+    }
+  return c;
+}
+
+// k = 16, 32 or 64. Lane l reads 16 bytes, 8 consecutive codes (rows 8m ..
+// 8m + 7, m = l % RG, RG = k / 8) of a column c = l / RG + (32 / RG) t, so a
+// 16 x 16 block is one 512-byte load of the warp; a slot is OPS such octets
+// per lane (a quarter of a 64 x 64 block, a whole block for k <= 32). The
+// block scale multiplies the vector entry (S_ij x_j = Q (sigma x_j)). The warp
+// walks the slots of its chunk's non-empty rows CB at a time with two batches
+// in flight; after a row's last batch its sums are reduced over the lanes of
+// the same row group and stored. VG warps of a CTA share a chunk, warp w taking
+// vectors (w % VG) * NVW .. + NVW - 1 (the later ones read the blocks from L1).
+template <int F, int K, int NVW, int CB, int VG>
+__global__ void __launch_bounds__(128) k_coupling_m(const MatDesc* __restrict__ mats, const int4* __restrict__ chunks,
+                                                   int64_t nchunks, int nvlo, int nvhi) {
+  static_assert(K == 16 || K == 32 || K == 64, "octet layout");
+  static_assert(VG == 1 || VG == 2 || VG == 4, "vector groups per chunk");
+  constexpr int RG = K / 8, CS = 32 / RG;   // row groups per column; column stride between a lane's octets
+  constexpr int OPL = K * K / 256;          // octets per lane per block
+  constexpr int OPS = OPL < 4 ? OPL : 4;    // octets per lane per slot
+  constexpr int SPB = OPL / OPS;            // slots per block
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * 4 + warp;
-  if (i >= n_nodes) return;
-  const int H = k >> 2, G = 32 / H;
-  const int g = lane / H, h = lane - g * H;
-  const int cpl = max(1, k / G);  // columns per lane per block, a power of two (lanes with col >= k idle)
-  const int lcpl = __ffs(cpl) - 1;
-  const int32_t b0 = Srow[i];
-  const int nslot = (Srow[i + 1] - b0) * cpl;
-  float acc[4][NVB], p[4][NVB];
+  const int64_t cidx = (int64_t)blockIdx.x * (4 / VG) + warp / VG;
+  const int vbase = (warp % VG) * NVW;
+  if (cidx >= nchunks) return;
+  const int4 ch = __ldg(chunks + cidx);
+  const MatDesc& D = mats[ch.x];
+  const int nv = D.nv;
+  if (nv < nvlo || nv > nvhi || vbase >= nv) return;
+  const uint16_t* __restrict__ S = D.smat;
+  const float* __restrict__ sscale = D.sscale;
+  const int64_t kk8 = D.kk8;
+  const int32_t* __restrict__ Scol = D.Scol;
+  const int kp = D.kp;
+  const float* __restrict__ xhat = D.xhat;
+  float* __restrict__ yhat = D.yhat;
+  const int row0 = ch.y, rows = min(ch.z, kChunkRows);
+  const ChunkRows cr = chunk_rows(D.Srow, yhat, row0, rows, nv, kp, lane, vbase, min(NVW, nv - vbase));
+  if (!cr.nonempty) return;
+  const int m = lane % RG, cl = lane / RG;
+  float acc[8][NVW];
 #pragma unroll
-  for (int r = 0; r < 4; r++)
+  for (int r = 0; r < 8; r++)
 #pragma unroll
-    for (int v = 0; v < NVB; v++) acc[r][v] = p[r][v] = 0.f;
-  uint2 a0[CB], a1[CB];
-  float x0[CB][NVB], x1[CB][NVB], s0[CB], s1[CB];
-  auto load = [&](int bt, uint2(&a)[CB], float(&xv)[CB][NVB], float(&sc)[CB]) {
+    for (int v = 0; v < NVW; v++) acc[r][v] = 0.f;
+  uint4 a0[CB][OPS], a1[CB][OPS];
+  float x0[CB][OPS][NVW], x1[CB][OPS][NVW], s0[CB], s1[CB];
+  // loads only: nothing here consumes a loaded value, so a batch's loads stay in flight
+  // while the previous batch is computed
+  auto load = [&](int32_t b0, int nslot, int bt, uint4(&a)[CB][OPS], float(&xv)[CB][OPS][NVW], float(&sc)[CB]) {
 #pragma unroll
     for (int u = 0; u < CB; u++) {
       const int slot = bt * CB + u;
-      const int b = slot >> lcpl, c = slot & (cpl - 1);
-      const int col = g + G * c;
-      const bool ok = slot < nslot && col < k;
       sc[u] = 0.f;
-      a[u] = make_uint2(0u, 0u);
 #pragma unroll
-      for (int v = 0; v < NVB; v++) xv[u][v] = 0.f;
-      if (slot < nslot) {
-        sc[u] = __ldg(sscale + b0 + b);
-        if (ok) {
-          a[u] = __ldg(reinterpret_cast<const uint2*>(S + (int64_t)(b0 + b) * kk8 + 4 * h + k * col));
-          const float* X = xhat + (int64_t)__ldg(Scol + b0 + b) * nv * kp;
+      for (int o = 0; o < OPS; o++) {
+        a[u][o] = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-          for (int v = 0; v < NVB; v++) xv[u][v] = (v < nv) ? __ldg(X + v * kp + col) : 0.f;
+        for (int v = 0; v < NVW; v++) xv[u][o][v] = 0.f;
+      }
+      if (slot < nslot) {  // warp-uniform
+        const int32_t gb = b0 + slot / SPB;
+        const int tq = slot % SPB;
+        sc[u] = __ldg(sscale + gb);
+        const float* X = xhat + ((int64_t)__ldg(Scol + gb) * nv + vbase) * kp;
+        const uint16_t* blk = S + (int64_t)gb * kk8 + 8 * m;
+#pragma unroll
+        for (int o = 0; o < OPS; o++) {
+          const int c = cl + CS * (tq * OPS + o);
+          a[u][o] = __ldg(reinterpret_cast<const uint4*>(blk + K * c));
+#pragma unroll
+          for (int v = 0; v < NVW; v++) xv[u][o][v] = (vbase + v < nv) ? __ldg(X + v * kp + c) : 0.f;
         }
       }
     }
   };
-  auto compute = [&](int bt, const uint2(&a)[CB], const float(&xv)[CB][NVB], const float(&sc)[CB]) {
+  auto compute = [&](const uint4(&a)[CB][OPS], const float(&xv)[CB][OPS][NVW], const float(&sc)[CB]) {
 #pragma unroll
-    for (int u = 0; u < CB; u++) {
-      const int slot = bt * CB + u;
-      const float2 lo = codes_to_f2<F>(a[u].x), hi = codes_to_f2<F>(a[u].y);
+    for (int u = 0; u < CB; u++)
 #pragma unroll
-      for (int v = 0; v < NVB; v++) {
-        p[0][v] = fmaf(lo.x, xv[u][v], p[0][v]);
-        p[1][v] = fmaf(lo.y, xv[u][v], p[1][v]);
-        p[2][v] = fmaf(hi.x, xv[u][v], p[2][v]);
-        p[3][v] = fmaf(hi.y, xv[u][v], p[3][v]);
+      for (int o = 0; o < OPS; o++) {
+        const float2 q0 = codes_to_f2<F>(a[u][o].x), q1 = codes_to_f2<F>(a[u][o].y);
+        const float2 q2 = codes_to_f2<F>(a[u][o].z), q3 = codes_to_f2<F>(a[u][o].w);
+#pragma unroll
+        for (int v = 0; v < NVW; v++) {
+          const float xs = sc[u] * xv[u][o][v];
+          acc[0][v] = fmaf(q0.x, xs, acc[0][v]);
+          acc[1][v] = fmaf(q0.y, xs, acc[1][v]);
+          acc[2][v] = fmaf(q1.x, xs, acc[2][v]);
+          acc[3][v] = fmaf(q1.y, xs, acc[3][v]);
+          acc[4][v] = fmaf(q2.x, xs, acc[4][v]);
+          acc[5][v] = fmaf(q2.y, xs, acc[5][v]);
+          acc[6][v] = fmaf(q3.x, xs, acc[6][v]);
+          acc[7][v] = fmaf(q3.y, xs, acc[7][v]);
+        }
       }
-      if (slot < nslot && (slot & (cpl - 1)) == cpl - 1) {  // last column of a block: scale its partial sum
-#pragma unroll
-        for (int r = 0; r < 4; r++)
-#pragma unroll
-          for (int v = 0; v < NVB; v++) {
-            acc[r][v] = fmaf(sc[u], p[r][v], acc[r][v]);
-            p[r][v] = 0.f;
-          }
-      }
-    }
   };
-  const int nbatch = (nslot + CB - 1) / CB;
-  if (nbatch > 0) load(0, a0, x0, s0);
-  for (int bt = 0; bt < nbatch; bt += 2) {
-    if (bt + 1 < nbatch) load(bt + 1, a1, x1, s1);
-    compute(bt, a0, x0, s0);
-    if (bt + 2 < nbatch) load(bt + 2, a0, x0, s0);
-    if (bt + 1 < nbatch) compute(bt + 1, a1, x1, s1);
-  }
-  for (int off = H; off < 32; off <<= 1)
+  auto flush = [&](int r) {  // row row0 + r is complete
 #pragma unroll
-    for (int r = 0; r < 4; r++)
+    for (int off = RG; off < 32; off <<= 1)
 #pragma unroll
-      for (int v = 0; v < NVB; v++) acc[r][v] += __shfl_xor_sync(0xFFFFFFFFu, acc[r][v], off);
-  if (g == 0) {
-    float* dst = yhat + i * nv * kp;
+      for (int rr = 0; rr < 8; rr++)
 #pragma unroll
-    for (int v = 0; v < NVB; v++)
-      if (v < nv)
+        for (int v = 0; v < NVW; v++) acc[rr][v] += __shfl_xor_sync(0xFFFFFFFFu, acc[rr][v], off);
+    if (cl == 0) {
+      float* dst = yhat + ((int64_t)(row0 + r) * nv + vbase) * kp + 8 * m;
 #pragma unroll
-        for (int r = 0; r < 4; r++) dst[v * kp + 4 * h + r] = acc[r][v];
+      for (int v = 0; v < NVW; v++)
+        if (vbase + v < nv) {
+          *reinterpret_cast<float4*>(dst + v * kp) = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+          *reinterpret_cast<float4*>(dst + v * kp + 4) = make_float4(acc[4][v], acc[5][v], acc[6][v], acc[7][v]);
+        }
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; rr++)
+#pragma unroll
+      for (int v = 0; v < NVW; v++) acc[rr][v] = 0.f;
+  };
+  // a cursor over the batches of the chunk's non-empty rows, in order
+  struct Cursor {
+    unsigned mask;  // rows not yet finished; r is its lowest bit
+    int r, bt, nslot;
+    int32_t b0;
+  };
+  auto begin = [&](Cursor& c) {
+    c.mask = cr.nonempty;
+    c.r = __ffs(c.mask) - 1;
+    c.bt = 0;
+    c.b0 = __shfl_sync(0xFFFFFFFFu, cr.sr, c.r);
+    c.nslot = (__shfl_sync(0xFFFFFFFFu, cr.sr, c.r + 1) - c.b0) * SPB;
+  };
+  auto advance = [&](Cursor& c) -> bool {
+    if ((c.bt + 1) * CB < c.nslot) {
+      c.bt++;
+      return true;
+    }
+    c.mask &= c.mask - 1u;
+    if (!c.mask) return false;
+    c.r = __ffs(c.mask) - 1;
+    c.bt = 0;
+    c.b0 = __shfl_sync(0xFFFFFFFFu, cr.sr, c.r);
+    c.nslot = (__shfl_sync(0xFFFFFFFFu, cr.sr, c.r + 1) - c.b0) * SPB;
+    return true;
+  };
+  Cursor lc, cc;
+  begin(lc);
+  begin(cc);
+  load(lc.b0, lc.nslot, lc.bt, a0, x0, s0);
+  bool more = advance(lc);
+  while (true) {
+    if (more) {
+      load(lc.b0, lc.nslot, lc.bt, a1, x1, s1);
+      more = advance(lc);
+    }
+    compute(a0, x0, s0);
+    if ((cc.bt + 1) * CB >= cc.nslot) flush(cc.r);
+    if (!advance(cc)) break;
+    if (more) {
+      load(lc.b0, lc.nslot, lc.bt, a0, x0, s0);
+      more = advance(lc);
+    }
+    compute(a1, x1, s1);
+    if ((cc.bt + 1) * CB >= cc.nslot) flush(cc.r);
+    if (!advance(cc)) break;
   }
 }
 
-// any other k: generic row mapping, one block at a time
+// any other k: the chunk's rows one after another, one block at a time
 template <int F, int RPL, int NVB>
-__global__ void __launch_bounds__(128) k_coupling_m_generic(const uint16_t* __restrict__ S,
-                                                           const float* __restrict__ sscale, int64_t kk8,
-                                                           const int32_t* __restrict__ Srow,
-                                                           const int32_t* __restrict__ Scol, int k, int kp, int LR,
-                                                           int64_t n_nodes, int nv, const float* __restrict__ xhat,
-                                                           float* __restrict__ yhat) {
+__global__ void __launch_bounds__(128) k_coupling_m_generic(const MatDesc* __restrict__ mats,
+                                                           const int4* __restrict__ chunks, int64_t nchunks, int nvlo,
+                                                           int nvhi) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * 4 + warp;
-  if (i >= n_nodes) return;
-  float acc[RPL][NVB];
+  const int64_t cidx = (int64_t)blockIdx.x * 4 + warp;
+  if (cidx >= nchunks) return;
+  const int4 ch = __ldg(chunks + cidx);
+  const MatDesc& D = mats[ch.x];
+  const int nv = D.nv;
+  if (nv < nvlo || nv > nvhi) return;
+  const uint16_t* __restrict__ S = D.smat;
+  const float* __restrict__ sscale = D.sscale;
+  const int64_t kk8 = D.kk8;
+  const int32_t* __restrict__ Scol = D.Scol;
+  const int k = D.k, kp = D.kp, LR = D.LR;
+  const float* __restrict__ xhat = D.xhat;
+  float* __restrict__ yhat = D.yhat;
+  const int row0 = ch.y, rows = min(ch.z, kChunkRows);
+  const ChunkRows cr = chunk_rows(D.Srow, yhat, row0, rows, nv, kp, lane, 0, nv);
+  for (unsigned m = cr.nonempty; m; m &= m - 1u) {
+    const int r = __ffs(m) - 1;
+    const int32_t b0 = __shfl_sync(0xFFFFFFFFu, cr.sr, r), b1 = __shfl_sync(0xFFFFFFFFu, cr.sr, r + 1);
+    float acc[RPL][NVB];
 #pragma unroll
-  for (int r = 0; r < RPL; r++)
+    for (int rr = 0; rr < RPL; rr++)
 #pragma unroll
-    for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
-  for (int32_t b = Srow[i]; b < Srow[i + 1]; b++)
-    warp_mv_m<F, RPL, NVB>(S + (int64_t)b * kk8, sscale[b], k, k, LR, xhat + (int64_t)Scol[b] * nv * kp, kp, nv, acc,
-                           lane);
-  group_reduce_m(acc, LR);
-  store_node_m<RPL, NVB, false>(yhat + i * nv * kp, k, kp, LR, nv, acc, lane);
+      for (int v = 0; v < NVB; v++) acc[rr][v] = 0.f;
+    for (int32_t b = b0; b < b1; b++)
+      warp_mv_m<F, RPL, NVB>(S + (int64_t)b * kk8, sscale[b], k, k, LR, xhat + (int64_t)Scol[b] * nv * kp, kp, nv, acc,
+                             lane);
+    group_reduce_m(acc, LR);
+    store_node_m<RPL, NVB, false>(yhat + (int64_t)(row0 + r) * nv * kp, k, kp, LR, nv, acc, lane);
+  }
 }
 
 // ---------------------------------------------------------------- dense near field + expansion (TMA stream)
@@ -413,14 +598,13 @@ struct __align__(16) MixedBlock {
   unsigned char src;    // bit 0: vector from the second source (yhat); bit 1: FP32 entries (not codes)
 };
 
-constexpr int kMixedMaxBlocks = 4;   // blocks of one row per work item
+constexpr int kMixedMaxBlocks = 8;   // blocks of one row per work item
+constexpr int kMixedVecCols = 256;   // vector columns of one work item (sum of its blocks' vs)
 constexpr int kMixedHeader = 256;
-__host__ __device__ constexpr int mixed_vec_slot(int nvb) { return 64 * nvb * 4; }
-__host__ __device__ constexpr int mixed_stage_bytes(int nvb) {
-  return kMixedHeader + kStageMat + kMixedMaxBlocks * mixed_vec_slot(nvb);
-}
+__host__ __device__ constexpr int mixed_vec_area(int nvb) { return kMixedVecCols * nvb * 4; }
+__host__ __device__ constexpr int mixed_stage_bytes(int nvb) { return kMixedHeader + kStageMat + mixed_vec_area(nvb); }
 __host__ __device__ constexpr int mixed_red_bytes(int nvb, int cw) { return cw * nvb * 64 * 4; }
-constexpr int kMixedBlkBuf = 32 * 4 * 16;  // block records of one producer batch (32 items x 4 blocks)
+constexpr int kMixedBlkBuf = 32 * kMixedMaxBlocks * 16;  // block records of one producer batch (32 items)
 __host__ __device__ constexpr int mixed_stages(int nvb, int cw) {
   return (kSmemLimit - 256 - kMixedBlkBuf - mixed_red_bytes(nvb, cw)) / mixed_stage_bytes(nvb) < 6
              ? (kSmemLimit - 256 - kMixedBlkBuf - mixed_red_bytes(nvb, cw)) / mixed_stage_bytes(nvb)
@@ -431,23 +615,22 @@ __host__ __device__ constexpr int mixed_smem_bytes(int nvb, int cw) {
 }
 constexpr int kMixedCW = 8;
 
+// items: m_off (in the matrix's dmat), m_bytes, shape = R | nb << 8, v_off = first block (batch-wide
+// index into blk), row = y offset, flags = last-of-row | matrix index << 8
 struct MixedStreamParams {
-  const StreamItem* items;  // m_off, m_bytes, shape = R | nb << 8, v_off = first block, row = y offset, flags
+  const StreamItem* items;
   const int* cta_begin;
-  const char* mat;
   const MixedBlock* blk;
-  const float* vsrc0;       // FP32 x (padded leaf layout)
-  const float* vsrc1;       // yhat
-  int nv;
-  double* y;
-  long long ldy;
+  const MatDesc* mats;
   int* err;
   long long budget;
 };
 
-// Stage header: [0] R, [1] nb, [2] row, [3] flags; block t at int index 8 + 4 t:
-// cols | FP32-entries flag << 16, vs, matrix offset in bytes, scale (bits).
-template <int NST, int SB, int VSLOT>
+// Stage header (ints): [0] R, [1] nb, [2] row, [3] flags; block t at 8 + 4 t:
+// cols | FP32-entries flag << 16, vs, matrix offset in bytes, scale (bits);
+// [40 + t] block t's vector offset in bytes; [48] nv; [50..51] y; [52..53] ldy.
+constexpr int kHdVoff = 40, kHdNv = 48, kHdY = 50, kHdLdy = 52;
+template <int NST, int SB, int VAREA>
 __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const StreamShared& S, int ib, int ie,
                                               MixedBlock* blkbuf) {
   const int lane = threadIdx.x & 31;
@@ -475,6 +658,22 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
                             min((int)((lshape >> 8) & 0xFF), kMixedMaxBlocks);
     const int nbatch = (int)min(blast - bfirst, (long long)(32 * kMixedMaxBlocks));
     for (int u = lane; u < nbatch; u += 32) blkbuf[u] = P.blk[bfirst + u];
+    // each lane fetches the matrix fields of its own item
+    const char* l_dmat = nullptr;
+    const float* l_x4 = nullptr;
+    const float* l_yhat = nullptr;
+    double* l_y = nullptr;
+    long long l_ldy = 0;
+    int l_nv = 0;
+    if (base + lane < ie) {
+      const MatDesc& D = P.mats[d1.w >> 8];
+      l_dmat = D.dmat;
+      l_x4 = D.x4;
+      l_yhat = D.yhat;
+      l_y = D.y;
+      l_ldy = D.ldy;
+      l_nv = D.nv;
+    }
     __syncwarp();
     for (int t = 0; t < cnt; t++) {
       const int it = base + t - ib;
@@ -497,6 +696,12 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
       const int flags = __shfl_sync(0xFFFFFFFFu, d1.w, t);
       const int R = (int)(shape & 0xFF), nb = min((int)((shape >> 8) & 0xFF), kMixedMaxBlocks);
       const long long b0 = (long long)(((unsigned long long)b_hi << 32) | b_lo);
+      const char* dmat = reinterpret_cast<const char*>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)l_dmat, t));
+      const float* x4 = reinterpret_cast<const float*>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)l_x4, t));
+      const float* yh = reinterpret_cast<const float*>(__shfl_sync(0xFFFFFFFFu, (unsigned long long)l_yhat, t));
+      const unsigned long long ydst = __shfl_sync(0xFFFFFFFFu, (unsigned long long)l_y, t);
+      const long long ldy = (long long)__shfl_sync(0xFFFFFFFFu, (unsigned long long)l_ldy, t);
+      const int nv = __shfl_sync(0xFFFFFFFFu, l_nv, t);
       unsigned char* stage = S.stage0 + s * SB;
       int* hd = reinterpret_cast<int*>(stage);
       // per-block side information, one lane per block
@@ -512,32 +717,41 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
         if (lane >= d) moff += o;
       }
       moff -= codes;
-      unsigned vbytes = (lane < nb) ? (unsigned)(P.nv * (int)mb.vs * 4) : 0u;
-      unsigned vtot = vbytes;
+      const unsigned vbytes = (lane < nb) ? (unsigned)(nv * (int)mb.vs * 4) : 0u;
+      unsigned voff = vbytes;  // inclusive prefix of the blocks' vector bytes
 #pragma unroll
-      for (int d = 1; d < kMixedMaxBlocks; d <<= 1) vtot += __shfl_xor_sync(0xFFFFFFFFu, vtot, d);
+      for (int d = 1; d < kMixedMaxBlocks; d <<= 1) {
+        const unsigned o = __shfl_up_sync(0xFFFFFFFFu, voff, d);
+        if (lane >= d) voff += o;
+      }
+      const unsigned vtot = __shfl_sync(0xFFFFFFFFu, voff, kMixedMaxBlocks - 1);
+      voff -= vbytes;
       if (lane < nb) {
         hd[8 + 4 * lane] = mb.cols | ((mb.src & 2) << 15);
         hd[9 + 4 * lane] = mb.vs;
         hd[10 + 4 * lane] = moff;
         hd[11 + 4 * lane] = __float_as_int(mb.scale);
+        hd[kHdVoff + lane] = (int)voff;
       }
       if (lane == 0) {
         hd[0] = R;
         hd[1] = nb;
         hd[2] = row;
         hd[3] = flags;
+        hd[kHdNv] = nv;
+        *reinterpret_cast<unsigned long long*>(hd + kHdY) = ydst;
+        *reinterpret_cast<long long*>(hd + kHdLdy) = ldy;
       }
       __syncwarp();
       if (lane == 0) {
         mbar_arrive_expect_tx(S.full + s, (unsigned)m_bytes + vtot);
-        bulk_g2s_stream(stage + kMixedHeader, P.mat + (((unsigned long long)m_hi << 32) | m_lo), (unsigned)m_bytes,
+        bulk_g2s_stream(stage + kMixedHeader, dmat + (((unsigned long long)m_hi << 32) | m_lo), (unsigned)m_bytes,
                         S.full + s, pol);
       }
       __syncwarp();
-      if (lane < nb) {
-        const float* src = mb.src ? P.vsrc1 : P.vsrc0;
-        bulk_g2s(stage + kMixedHeader + kStageMat + lane * VSLOT, src + mb.voff * P.nv, vbytes, S.full + s);
+      if (lane < nb && vbytes > 0) {  // a matrix multiplies no vectors in this product: matrix bytes only
+        const float* src = (mb.src & 1) ? yh : x4;
+        bulk_g2s(stage + kMixedHeader + kStageMat + voff, src + mb.voff * nv, vbytes, S.full + s);
       }
       __syncwarp();
       issued = it + 1;
@@ -554,12 +768,170 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
     }
 }
 
+// One work item of the dense stream for up to NV2 vectors (NV2 <= NVB): every
+// block's products are added, scaled by the block's scale, into acc (lane:
+// rows r0, r0 + 1 of the item's row, summed over the warps at the row end).
+// Rows of more than 32: warp w takes columns C w / CW .. C (w + 1) / CW of each
+// block (full 64 x 64 blocks of codes on a branch-free path). Rows of at most
+// 32: lanes l and l + 16 own rows 2 (l & 15), +1, and the 16 half-warps take
+// the item's 4-column units (block, columns 4u .. 4u + 3) in turn, reading the
+// four vector entries of a unit as one 16-byte load.
+template <int F, int NV2, int NVB, int CW>
+__device__ __forceinline__ void consume_item(const unsigned char* stage, const int* hd, int nb, int R, int warp, int lane,
+                                             float (&acc)[2][NVB]) {
+  constexpr int VAREA = mixed_vec_area(NVB);
+  constexpr int SETS = NV2 == 1 ? 4 : (NV2 == 2 ? 2 : 1);
+  constexpr bool kScaleCodes = NV2 >= 4;  // scale the codes once instead of per-vector partial sums
+  if (R <= 32) {
+    const int r0 = 2 * (lane & 15), hw = warp * 2 + (lane >> 4);
+    const bool even = (R & 1) == 0;
+    int base = 0;
+    for (int t = 0; t < nb; t++) {
+      const int cw = hd[8 + 4 * t];
+      const bool f32 = (cw >> 16) & 1;
+      const int C = min(cw & 0xFFFF, 64), vs = min(hd[9 + 4 * t], 64);
+      const int moff = min(hd[10 + 4 * t], kStageMat - 16) & ~15;
+      const float scale = __int_as_float(hd[11 + 4 * t]);
+      const int voff = min(hd[kHdVoff + t], VAREA - 16) & ~15;
+      const uint16_t* A = reinterpret_cast<const uint16_t*>(stage + kMixedHeader + moff);
+      const float* A32 = reinterpret_cast<const float*>(stage + kMixedHeader + moff);
+      const float* X = reinterpret_cast<const float*>(stage + kMixedHeader + kStageMat + voff);
+      const int G = (C + 3) >> 2;
+      int first = hw - (base & 15);
+      if (first < 0) first += 16;
+      base += G;
+      if (r0 >= R) continue;
+      for (int grp = first; grp < G; grp += 16) {
+        const int c = 4 * grp;
+        float2 a[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const int col = c + j;
+          if (col >= C) {
+            a[j] = make_float2(0.f, 0.f);
+          } else if (f32) {
+            a[j].x = A32[r0 + R * col];
+            a[j].y = (r0 + 1 < R) ? A32[r0 + 1 + R * col] : 0.f;
+          } else if (even) {
+            a[j] = codes_to_f2<F>(*reinterpret_cast<const uint32_t*>(A + r0 + R * col));
+          } else {
+            a[j].x = code_to_f<F>(A[r0 + R * col]);
+            a[j].y = (r0 + 1 < R) ? code_to_f<F>(A[r0 + 1 + R * col]) : 0.f;
+          }
+          if (kScaleCodes) {
+            a[j].x *= scale;
+            a[j].y *= scale;
+          }
+        }
+        float p[2][NV2];
+#pragma unroll
+        for (int v = 0; v < NV2; v++) p[0][v] = p[1][v] = 0.f;
+#pragma unroll
+        for (int v = 0; v < NV2; v++) {
+          const float4 x4 = *reinterpret_cast<const float4*>(X + v * vs + c);
+          float* tgt0 = kScaleCodes ? &acc[0][v] : &p[0][v];
+          float* tgt1 = kScaleCodes ? &acc[1][v] : &p[1][v];
+          *tgt0 = fmaf(a[0].x, x4.x, *tgt0);
+          *tgt1 = fmaf(a[0].y, x4.x, *tgt1);
+          *tgt0 = fmaf(a[1].x, x4.y, *tgt0);
+          *tgt1 = fmaf(a[1].y, x4.y, *tgt1);
+          *tgt0 = fmaf(a[2].x, x4.z, *tgt0);
+          *tgt1 = fmaf(a[2].y, x4.z, *tgt1);
+          *tgt0 = fmaf(a[3].x, x4.w, *tgt0);
+          *tgt1 = fmaf(a[3].y, x4.w, *tgt1);
+        }
+        if (!kScaleCodes)
+#pragma unroll
+          for (int v = 0; v < NV2; v++) {
+            acc[0][v] = fmaf(scale, p[0][v], acc[0][v]);
+            acc[1][v] = fmaf(scale, p[1][v], acc[1][v]);
+          }
+      }
+    }
+    return;
+  }
+  const int r0 = 2 * lane;
+  for (int t = 0; t < nb; t++) {
+    const int cw = hd[8 + 4 * t];
+    const bool f32 = (cw >> 16) & 1;
+    const int C = min(cw & 0xFFFF, 64), vs = min(hd[9 + 4 * t], 64);
+    const int moff = min(hd[10 + 4 * t], kStageMat - 16) & ~15;
+    const float scale = __int_as_float(hd[11 + 4 * t]);
+    const int voff = min(hd[kHdVoff + t], VAREA - 16) & ~15;
+    const uint16_t* A = reinterpret_cast<const uint16_t*>(stage + kMixedHeader + moff);
+    const float* A32 = reinterpret_cast<const float*>(stage + kMixedHeader + moff);
+    const float* X = reinterpret_cast<const float*>(stage + kMixedHeader + kStageMat + voff);
+    const int c0 = (C * warp) / CW, c1 = (C * (warp + 1)) / CW;
+    float p[SETS][2][NV2];
+#pragma unroll
+    for (int u = 0; u < SETS; u++)
+#pragma unroll
+      for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int v = 0; v < NV2; v++) p[u][r][v] = 0.f;
+    if (!f32 && R == 64 && C == 64 && vs == 64) {
+      // full 64 x 64 block of codes: fixed strides, every column loaded up front
+      constexpr int CPW = 64 / CW;
+      const uint32_t* Aw = reinterpret_cast<const uint32_t*>(A + r0 + 64 * c0);
+      uint32_t w[CPW];
+#pragma unroll
+      for (int u = 0; u < CPW; u++) w[u] = Aw[32 * u];
+#pragma unroll
+      for (int v = 0; v < NV2; v++) {
+        float xv[CPW];
+#pragma unroll
+        for (int u = 0; u < CPW; u += 4) {
+          const float4 t4 = *reinterpret_cast<const float4*>(X + v * 64 + c0 + u);
+          xv[u] = t4.x;
+          xv[u + 1] = t4.y;
+          xv[u + 2] = t4.z;
+          xv[u + 3] = t4.w;
+        }
+#pragma unroll
+        for (int u = 0; u < CPW; u++) {
+          const float2 a = codes_to_f2<F>(w[u]);
+          p[u % SETS][0][v] = fmaf(a.x, xv[u], p[u % SETS][0][v]);
+          p[u % SETS][1][v] = fmaf(a.y, xv[u], p[u % SETS][1][v]);
+        }
+      }
+    } else if (r0 < R) {
+      const bool even = (R & 1) == 0;
+      for (int col = c0; col < c1; col++) {
+        float2 a;
+        if (f32) {
+          a.x = A32[r0 + R * col];
+          a.y = (r0 + 1 < R) ? A32[r0 + 1 + R * col] : 0.f;
+        } else if (even) {
+          a = codes_to_f2<F>(*reinterpret_cast<const uint32_t*>(A + r0 + R * col));
+        } else {
+          a.x = code_to_f<F>(A[r0 + R * col]);
+          a.y = (r0 + 1 < R) ? code_to_f<F>(A[r0 + 1 + R * col]) : 0.f;
+        }
+#pragma unroll
+        for (int v = 0; v < NV2; v++) {
+          const float xv = X[v * vs + col];
+          p[0][0][v] = fmaf(a.x, xv, p[0][0][v]);
+          p[0][1][v] = fmaf(a.y, xv, p[0][1][v]);
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV2; v++)
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        float sum = p[0][r][v];
+#pragma unroll
+        for (int u = 1; u < SETS; u++) sum += p[u][r][v];
+        acc[r][v] = fmaf(scale, sum, acc[r][v]);
+      }
+  }
+}
+
 template <int F, int NVB, int CW>
 __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStreamParams P) {
   constexpr int NST = mixed_stages(NVB, CW);
   constexpr int SB = mixed_stage_bytes(NVB);
-  constexpr int VSLOT = mixed_vec_slot(NVB);
-  constexpr int SETS = NVB == 1 ? 4 : (NVB == 2 ? 2 : 1);
+  constexpr int VAREA = mixed_vec_area(NVB);
   static_assert(NST >= 2, "at least two stages");
   extern __shared__ __align__(1024) unsigned char smem[];
   const StreamShared S = stream_shared<NST, SB>(smem);
@@ -569,20 +941,18 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
   if (warp == CW) {
     // producer-private block records: smem after the row reduction buffer
     MixedBlock* blkbuf = reinterpret_cast<MixedBlock*>(smem + NST * SB + 256 + mixed_red_bytes(NVB, CW));
-    mixed_produce<NST, SB, VSLOT>(P, S, ib, ie, blkbuf);
+    mixed_produce<NST, SB, VAREA>(P, S, ib, ie, blkbuf);
     return;
   }
   StreamParams W{};
   W.err = P.err;
   W.budget = P.budget;
   float* red = reinterpret_cast<float*>(S.red);
-  const int nv = P.nv;
   float acc[2][NVB];
 #pragma unroll
   for (int r = 0; r < 2; r++)
 #pragma unroll
     for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
-  const int r0 = 2 * lane;
   int rows_done = 0;
   for (int it = 0; it < ie - ib; it++) {
     const int st = it % NST, use = it / NST;
@@ -590,91 +960,36 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
     const unsigned char* stage = S.stage0 + st * SB;
     const int* hd = reinterpret_cast<const int*>(stage);
     const int R = min(hd[0], 64), nb = min(hd[1], kMixedMaxBlocks), row = hd[2], flags = hd[3];
-    for (int t = 0; t < nb; t++) {
-      const int cw = hd[8 + 4 * t];
-      const bool f32 = (cw >> 16) & 1;
-      const int C = min(cw & 0xFFFF, 64), vs = min(hd[9 + 4 * t], 64);
-      const int moff = min(hd[10 + 4 * t], kStageMat - 16) & ~15;
-      const float scale = __int_as_float(hd[11 + 4 * t]);
-      const uint16_t* A = reinterpret_cast<const uint16_t*>(stage + kMixedHeader + moff);
-      const float* A32 = reinterpret_cast<const float*>(stage + kMixedHeader + moff);
-      const float* X = reinterpret_cast<const float*>(stage + kMixedHeader + kStageMat + t * VSLOT);
-      const int c0 = (C * warp) / CW, c1 = (C * (warp + 1)) / CW;
-      float p[SETS][2][NVB];
-#pragma unroll
-      for (int u = 0; u < SETS; u++)
-#pragma unroll
-        for (int r = 0; r < 2; r++)
-#pragma unroll
-          for (int v = 0; v < NVB; v++) p[u][r][v] = 0.f;
-      if (!f32 && R == 64 && C == 64 && vs == 64) {
-        // full 64 x 64 block of codes: fixed strides, every column loaded up front
-        constexpr int CPW = 64 / CW;
-        const uint32_t* Aw = reinterpret_cast<const uint32_t*>(A + r0 + 64 * c0);
-        uint32_t w[CPW];
-#pragma unroll
-        for (int u = 0; u < CPW; u++) w[u] = Aw[32 * u];
-#pragma unroll
-        for (int v = 0; v < NVB; v++) {
-          if (v >= nv) continue;
-          float xv[CPW];
-#pragma unroll
-          for (int u = 0; u < CPW; u += 4) {
-            const float4 t4 = *reinterpret_cast<const float4*>(X + v * 64 + c0 + u);
-            xv[u] = t4.x;
-            xv[u + 1] = t4.y;
-            xv[u + 2] = t4.z;
-            xv[u + 3] = t4.w;
-          }
-#pragma unroll
-          for (int u = 0; u < CPW; u++) {
-            const float2 a = codes_to_f2<F>(w[u]);
-            p[u % SETS][0][v] = fmaf(a.x, xv[u], p[u % SETS][0][v]);
-            p[u % SETS][1][v] = fmaf(a.y, xv[u], p[u % SETS][1][v]);
-          }
-        }
-      } else if (r0 < R) {
-        const bool even = (R & 1) == 0;
-        for (int col = c0; col < c1; col++) {
-          float2 a;
-          if (f32) {
-            a.x = A32[r0 + R * col];
-            a.y = (r0 + 1 < R) ? A32[r0 + 1 + R * col] : 0.f;
-          } else if (even) {
-            a = codes_to_f2<F>(*reinterpret_cast<const uint32_t*>(A + r0 + R * col));
-          } else {
-            a.x = code_to_f<F>(A[r0 + R * col]);
-            a.y = (r0 + 1 < R) ? code_to_f<F>(A[r0 + 1 + R * col]) : 0.f;
-          }
-#pragma unroll
-          for (int v = 0; v < NVB; v++) {
-            const float xv = (v < nv) ? X[v * vs + col] : 0.f;
-            p[0][0][v] = fmaf(a.x, xv, p[0][0][v]);
-            p[0][1][v] = fmaf(a.y, xv, p[0][1][v]);
-          }
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < 2; r++)
-#pragma unroll
-        for (int v = 0; v < NVB; v++) {
-          float sum = p[0][r][v];
-#pragma unroll
-          for (int u = 1; u < SETS; u++) sum += p[u][r][v];
-          acc[r][v] = fmaf(scale, sum, acc[r][v]);
-        }
-    }
+    const int nv = min(hd[kHdNv], NVB);
+    double* const ydst = reinterpret_cast<double*>(*reinterpret_cast<const unsigned long long*>(hd + kHdY));
+    const long long ldy = *reinterpret_cast<const long long*>(hd + kHdLdy);
+    // the variant for the item's vector count (a matrix of a batch may take fewer than NVB)
+    if (NVB >= 16 && nv > 8) consume_item<F, (NVB >= 16 ? 16 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
+    else if (NVB >= 8 && nv > 4) consume_item<F, (NVB >= 8 ? 8 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
+    else if (NVB >= 4 && nv > 2) consume_item<F, (NVB >= 4 ? 4 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
+    else if (NVB >= 2 && nv > 1) consume_item<F, (NVB >= 2 ? 2 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
+    else consume_item<F, 1, NVB, CW>(stage, hd, nb, R, warp, lane, acc);
     __syncwarp();
     if (lane == 0) mbar_arrive(S.empty + st);
     if (flags & kItemFlagLast) {
+      const bool half = R <= 32;
+      const int r0 = half ? 2 * (lane & 15) : 2 * lane;
+      if (half)  // add the other half-warp's columns
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+          for (int v = 0; v < NVB; v++) acc[r][v] += __shfl_xor_sync(0xFFFFFFFFu, acc[r][v], 16);
       if (rows_done > 0 && !warp_wait(S.rowfree, (rows_done - 1) & 1, W, S.abort_flag)) break;
+      if (!half || lane < 16)
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+          for (int v = 0; v < NVB; v++)
+            if (v < nv) red[(warp * NVB + v) * 64 + r0 + r] = acc[r][v];
 #pragma unroll
       for (int r = 0; r < 2; r++)
 #pragma unroll
-        for (int v = 0; v < NVB; v++) {
-          red[(warp * NVB + v) * 64 + r0 + r] = acc[r][v];
-          acc[r][v] = 0.f;
-        }
+        for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
       __syncwarp();
       if (lane == 0) mbar_arrive(S.rowfull);
       if (!warp_wait(S.rowfull, rows_done & 1, W, S.abort_flag)) break;
@@ -683,7 +998,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
         float sum = 0.f;
 #pragma unroll
         for (int w = 0; w < CW; w++) sum += red[(w * NVB + v) * 64 + r];
-        P.y[v * P.ldy + row + r] = (double)sum;
+        ydst[v * ldy + row + r] = (double)sum;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(S.rowfree);

@@ -124,3 +124,21 @@ def test_rejects_missing_column_basis(h2, small):
     with pytest.raises(h2.H2Error) as ei:
         h2.H2Matrix(V=small.U, F=None, **kw)
     assert ei.value.status == h2.H2_ERR_INVALID
+
+
+def test_batch_entry_points_reject_null_arguments(h2):
+    lib = h2._lib
+    out = ctypes.c_void_p()
+    null1 = (ctypes.c_void_p * 1)(None)
+    assert lib.h2_batch_create(None, 1, ctypes.byref(out)) == h2.H2_ERR_INVALID
+    assert lib.h2_batch_create(null1, 1, ctypes.byref(out)) == h2.H2_ERR_INVALID
+    assert "NULL" in lib.h2_last_error().decode()
+    assert lib.h2_batch_create(null1, 0, ctypes.byref(out)) == h2.H2_ERR_INVALID
+    assert lib.h2_batch_create(null1, 1, None) == h2.H2_ERR_INVALID
+    assert out.value is None
+    assert lib.h2_batch_matvec(None, None, None, None, None, None, None) == h2.H2_ERR_INVALID
+    assert lib.h2_batch_check(None, None) == h2.H2_ERR_INVALID
+    assert lib.h2_batch_info(None, None) == h2.H2_ERR_INVALID
+    assert lib.h2_batch_profile(None, 1) == h2.H2_ERR_INVALID
+    assert lib.h2_batch_profile_read(None, None, None) == h2.H2_ERR_INVALID
+    assert lib.h2_batch_destroy(None) == h2.H2_OK
