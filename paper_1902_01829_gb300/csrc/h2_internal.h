@@ -64,6 +64,27 @@ struct MixedLaunch {
   Profiler* prof = nullptr;          // profiler whose events mark the phases (or none)
 };
 
+// the tensor-core dense phase of one pass (one matrix, panel layout, fp16 / bf16 codes)
+struct TcCall {
+  const h2::StreamItem* items = nullptr;
+  const int* cta_begin = nullptr;
+  const void* blk = nullptr;
+  const void* dmat = nullptr;
+  const float* x4 = nullptr;
+  const float* yhat = nullptr;
+  const int64_t* xp4_off = nullptr;
+  unsigned* vmax = nullptr;   // [16]
+  float* vscale = nullptr;    // [16]
+  int64_t leaves = 0, leaf0 = 0;
+  int k = 0, kp = 0, grid = 0;
+  float dmax = 0.f, umax = 0.f;  // largest block scale of the dense blocks and of the leaf bases
+  double* y = nullptr;
+  int64_t ldy = 0;
+  int nv = 0;
+  int* err = nullptr;
+  long long budget = kWaitBudget;
+};
+
 // device copy of the precision form (per-block scaled 16-bit storage, FP32 arithmetic)
 struct MixedData {
   void* dmat = nullptr;       // per leaf row: its dense blocks then U_i, each padded to 16 bytes
@@ -86,6 +107,10 @@ struct MixedData {
   int kp4 = 0;                // k rounded up to a multiple of 4
   int64_t kk8 = 0;            // k*k rounded up to a multiple of 8
   int64_t nblk = 0;           // dense-stream blocks (dense blocks + one U per leaf row)
+  bool panel = false;         // blocks in the panel layout (every leaf 64 points, fp16/bf16 codes)
+  float dmax = 0.f, umax = 0.f;  // largest scale of the dense blocks and of the U blocks
+  unsigned* tc_vmax = nullptr;   // tensor-core passes: per-vector maxima and scales
+  float* tc_vscale = nullptr;
   // the table-driven kernels' tables for this matrix alone (a batch of one)
   MixedLaunch launch;
   std::vector<h2::StreamItem> items_host;  // the dense items (matrix index 0), kept for batches
@@ -176,7 +201,9 @@ void profile_free(Profiler* p);
 // precision form: device layout (h2_create) and one product pass of up to kPassVectors vectors
 h2_status mixed_build(h2_matrix_s* h, const h2_desc* d);
 // one product pass; buckets: bit b set when some matrix has a vector count in bucket b
-h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st);
+h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc = nullptr);
+// passes of at least this many vectors use the tensor-core dense phase (panel-layout handles)
+constexpr int kTcMinVectors = 8;
 h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st);
 
 }  // namespace h2i

@@ -15,11 +15,12 @@
 
 #include "h2_internal.h"
 #include "mixed.cuh"
+#include "tc_dense.cuh"
 
 namespace h2i {
 
 template <int F>
-h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st);
+h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc);
 
 }  // namespace h2i
 
@@ -277,48 +278,79 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   {  // dense stream: row i holds its dense blocks then U_i, contiguous, each padded to 16 bytes
     const int64_t ubytes = M.bases_fp32 ? 4 : 2;
     std::vector<int64_t> doff((size_t)h->nD + 1, 0);  // FP64 input offsets
+    // panel layout (the tensor-core operand layout) when every leaf has 64 points and the
+    // blocks are 16-bit floating-point codes with a rank that is a multiple of 16
+    bool panel = form != h2::kFormInt16 && !M.bases_fp32 && k % 16 == 0 && k <= 64;
+    for (int64_t i = 0; panel && i < leaves; i++) panel = lo[i + 1] - lo[i] == 64;
+    M.panel = panel;
     std::vector<int64_t> row_blk0((size_t)leaves + 1, 0), boff((size_t)(h->nD + leaves) + 1, 0);
     for (int64_t i = 0, b = 0; i < leaves; i++) {
       row_blk0[i] = b + i;  // global block index of the row's first block (dense blocks + one U per row)
       const int64_t si = lo[i + 1] - lo[i];
       for (; b < d->D_rowptr[i + 1]; b++) {
-        const int64_t sz = si * (lo[d->D_colidx[b] + 1] - lo[d->D_colidx[b]]);
+        const int64_t sj = lo[d->D_colidx[b] + 1] - lo[d->D_colidx[b]], sz = si * sj;
         doff[b + 1] = doff[b] + sz;
-        boff[b + i + 1] = boff[b + i] + round_up(sz * 2, 16);
+        boff[b + i + 1] = boff[b + i] + (panel ? h2::panel_block_bytes((int)sj) : round_up(sz * 2, 16));
       }
-      boff[b + i + 1] = boff[b + i] + round_up(si * k * ubytes, 16);  // U_i
+      boff[b + i + 1] = boff[b + i] + (panel ? h2::panel_block_bytes(k) : round_up(si * k * ubytes, 16));  // U_i
     }
     row_blk0[leaves] = h->nD + leaves;
     const int64_t nblk = h->nD + leaves, total = boff[nblk];  // bytes
     std::vector<unsigned char> bytes_host((size_t)total, 0);
     unsigned char* base = bytes_host.data();
     std::vector<h2::MixedBlock> blk((size_t)nblk);
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t i = 0; i < leaves; i++) {
-      const int64_t si = lo[i + 1] - lo[i];
-      int64_t g = row_blk0[i];
-      for (int32_t b = d->D_rowptr[i]; b < d->D_rowptr[i + 1]; b++, g++) {
-        const int32_t j = d->D_colidx[b];
-        h2::MixedBlock& m = blk[g];
-        m.scale = quantize(d->D_val + doff[b], doff[b + 1] - doff[b], form, reinterpret_cast<uint16_t*>(base + boff[g]));
-        m.voff = xp4[j];
-        m.cols = (unsigned short)(lo[j + 1] - lo[j]);
-        m.vs = (unsigned char)round_up(lo[j + 1] - lo[j], 4);
-        m.src = 0;
+#pragma omp parallel
+    {
+      std::vector<uint16_t> tmp;
+      // codes of a 64-row column-major block into the panel layout at dst
+      auto to_panels = [&](int64_t C, uint16_t* dst) {
+        const int64_t ps = h2::panel_stride((int)C) / 2;
+        for (int64_t c = 0; c < C; c++)
+          for (int64_t r = 0; r < 64; r++) dst[(r >> 3) * ps + c * 8 + (r & 7)] = tmp[r + 64 * c];
+      };
+#pragma omp for schedule(dynamic, 16)
+      for (int64_t i = 0; i < leaves; i++) {
+        const int64_t si = lo[i + 1] - lo[i];
+        int64_t g = row_blk0[i];
+        for (int32_t b = d->D_rowptr[i]; b < d->D_rowptr[i + 1]; b++, g++) {
+          const int32_t j = d->D_colidx[b];
+          const int64_t sj = lo[j + 1] - lo[j];
+          h2::MixedBlock& m = blk[g];
+          if (panel) {
+            tmp.resize((size_t)(si * sj));
+            m.scale = quantize(d->D_val + doff[b], si * sj, form, tmp.data());
+            to_panels(sj, reinterpret_cast<uint16_t*>(base + boff[g]));
+          } else {
+            m.scale = quantize(d->D_val + doff[b], si * sj, form, reinterpret_cast<uint16_t*>(base + boff[g]));
+          }
+          m.voff = xp4[j];
+          m.cols = (unsigned short)sj;
+          m.vs = (unsigned char)round_up(sj, 4);
+          m.src = panel ? 4 : 0;
+        }
+        h2::MixedBlock& m = blk[g];  // U_i, multiplied with yhat of leaf i
+        if (M.bases_fp32) {
+          float* u = reinterpret_cast<float*>(base + boff[g]);
+          for (int64_t e = 0; e < si * k; e++) u[e] = (float)d->U[lo[i] * k + e];
+          m.scale = 1.0f;
+          m.src = 1 | 2;
+        } else if (panel) {
+          tmp.resize((size_t)(si * k));
+          m.scale = quantize(d->U + lo[i] * k, si * k, form, tmp.data());
+          to_panels(k, reinterpret_cast<uint16_t*>(base + boff[g]));
+          m.src = 1 | 4;
+        } else {
+          m.scale = quantize(d->U + lo[i] * k, si * k, form, reinterpret_cast<uint16_t*>(base + boff[g]));
+          m.src = 1;
+        }
+        m.voff = (h->leaf0 + i) * M.kp4;
+        m.cols = (unsigned short)k;
+        m.vs = (unsigned char)M.kp4;
       }
-      h2::MixedBlock& m = blk[g];  // U_i, multiplied with yhat of leaf i
-      if (M.bases_fp32) {
-        float* u = reinterpret_cast<float*>(base + boff[g]);
-        for (int64_t e = 0; e < si * k; e++) u[e] = (float)d->U[lo[i] * k + e];
-        m.scale = 1.0f;
-        m.src = 1 | 2;
-      } else {
-        m.scale = quantize(d->U + lo[i] * k, si * k, form, reinterpret_cast<uint16_t*>(base + boff[g]));
-        m.src = 1;
-      }
-      m.voff = (h->leaf0 + i) * M.kp4;
-      m.cols = (unsigned short)k;
-      m.vs = (unsigned char)M.kp4;
+    }
+    for (int64_t g = 0; g < nblk; g++) {
+      float& mx = (blk[g].src & 1) ? M.umax : M.dmax;
+      mx = std::max(mx, blk[g].scale);
     }
     unsigned char* dm = nullptr;
     if ((st = upload(h, &dm, base, total)) != H2_OK) return st;
@@ -374,6 +406,11 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
         vc += m.vs;
       }
       ok = ok && vc <= h2::kMixedVecCols;
+      if (ok && M.panel) {  // the tensor-core stage: at most kTcMaxBlocks blocks, their B tiles in kTcStageB
+        int64_t tb = 0;
+        for (int u = 0; u < nb; u++) tb += (int64_t)h2::kTcN * h2::panel_cols(blk[it.v_off + u].cols) * 2;
+        ok = nb <= h2::kTcMaxBlocks && tb <= h2::kTcStageB && it.m_bytes == boff[it.v_off + nb] - boff[it.v_off];
+      }
       if (!ok) return h2_fail(H2_ERR_INVALID, "internal: precision-form work item %lld fails the layout audit", (long long)t);
     }
     if ((st = upload(h, &M.dense_items.items, items.data(), (int64_t)items.size())) != H2_OK) return st;
@@ -391,6 +428,11 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   // zeros; the dense stream multiplies them by zero codes, so they must be finite
   CUDA_TRY(cudaMemset(M.xhat, 0, (size_t)(nodes * kPassVectors * M.kp4) * sizeof(float)));
   CUDA_TRY(cudaMemset(M.yhat, 0, (size_t)(nodes * kPassVectors * M.kp4) * sizeof(float)));
+
+  if (M.panel) {
+    if ((st = dalloc(h, &M.tc_vmax, 16)) != H2_OK) return st;
+    if ((st = dalloc(h, &M.tc_vscale, 16)) != H2_OK) return st;
+  }
 
   // tables of the table-driven kernels: this matrix alone
   MixedLaunch& L = M.launch;
@@ -419,11 +461,11 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   return H2_OK;
 }
 
-h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st) {
+h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {
   switch (form_of(storage)) {
-    case h2::kFormFp16: return mixed_pass_form<h2::kFormFp16>(L, buckets, st);
-    case h2::kFormBf16: return mixed_pass_form<h2::kFormBf16>(L, buckets, st);
-    default: return mixed_pass_form<h2::kFormInt16>(L, buckets, st);
+    case h2::kFormFp16: return mixed_pass_form<h2::kFormFp16>(L, buckets, st, tc);
+    case h2::kFormBf16: return mixed_pass_form<h2::kFormBf16>(L, buckets, st, tc);
+    default: return mixed_pass_form<h2::kFormInt16>(L, buckets, st, nullptr);
   }
 }
 
@@ -435,6 +477,33 @@ h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, doubl
   if (me != cudaSuccess) return h2_fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
   h2_status s = set_calls(static_cast<h2::MatDesc*>(L.mats), 1, &nv, &x, &ldx, &y, &ldy, st);
   if (s != H2_OK) return s;
+  const MixedData& M = h->mx;
+  if (M.panel && nv >= kTcMinVectors && h->storage != H2_INT16_SCALED) {  // dense phase on the tensor cores
+    TcCall T;
+    T.items = M.dense_items.items;
+    T.cta_begin = M.dense_items.cta_begin;
+    T.blk = M.dblk;
+    T.dmat = M.dmat;
+    T.x4 = M.x4;
+    T.yhat = M.yhat;
+    T.xp4_off = M.xp4_off;
+    T.vmax = M.tc_vmax;
+    T.vscale = M.tc_vscale;
+    T.leaves = h->leaves;
+    T.leaf0 = h->leaf0;
+    T.k = h->k;
+    T.kp = M.kp4;
+    T.grid = h->grid;
+    T.dmax = M.dmax;
+    T.umax = M.umax;
+    T.y = y;
+    T.ldy = ldy;
+    T.nv = nv;
+    T.err = h->err;
+    T.budget = h->budget;
+    h->prof.launches += h->storage == H2_FP16_SCALED ? 7 : 6;
+    return mixed_launch(h->storage, L, 1u << bucket_of(nv), st, &T);
+  }
   h->prof.launches += 5;
   return mixed_launch(h->storage, L, 1u << bucket_of(nv), st);
 }

@@ -5,6 +5,7 @@
 #pragma once
 #include "h2_internal.h"
 #include "mixed.cuh"
+#include "tc_dense.cuh"
 
 namespace h2i {
 
@@ -77,10 +78,50 @@ h2_status dense_launch(const MixedLaunch& L, cudaStream_t st) {
   return H2_OK;
 }
 
+// dense phase on the tensor cores: per-vector scales, then the persistent tcgen05 kernel
+template <int F>
+h2_status tc_launch(const TcCall& T, cudaStream_t st) {
+  using namespace h2;
+  if constexpr (F == kFormInt16) {
+    return h2_fail(H2_ERR_UNSUPPORTED, "internal: tensor-core path for int16 codes");
+  } else {
+    static cudaError_t attr = cudaErrorNotReady;
+    if (attr == cudaErrorNotReady)
+      attr = cudaFuncSetAttribute(k_dense_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (attr != cudaSuccess) return h2_fail(H2_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(attr));
+    const bool fp16 = F == kFormFp16;
+    if (fp16) {
+      cudaError_t e = cudaMemsetAsync(T.vmax, 0, kTcVec * sizeof(unsigned), st);
+      if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+      const long long warps = T.leaves * T.nv;
+      k_tc_vmax<F><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+          T.x4, T.yhat, reinterpret_cast<const long long*>(T.xp4_off), T.leaves, T.leaf0, T.nv, T.kp, T.k, T.dmax,
+          T.umax, T.vmax);
+    }
+    k_tc_vscale<F><<<1, 32, 0, st>>>(T.vmax, T.vscale, fp16 ? 1 : 0);
+    TcParams P{};
+    P.items = T.items;
+    P.cta_begin = T.cta_begin;
+    P.blk = static_cast<const MixedBlock*>(T.blk);
+    P.dmat = static_cast<const char*>(T.dmat);
+    P.x4 = T.x4;
+    P.yhat = T.yhat;
+    P.vscale = T.vscale;
+    P.y = T.y;
+    P.ldy = T.ldy;
+    P.nv = T.nv;
+    P.kp = T.kp;
+    P.err = T.err;
+    P.budget = T.budget;
+    k_dense_tc<F><<<T.grid, kTcThreads, kTcSmem, st>>>(P);
+    return H2_OK;
+  }
+}
+
 // the phase launches; the caller has written the product's fields into the
 // matrix table and recorded the first profiling mark
 template <int F, int FB, int RPL>
-h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st) {
+h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {
   cudaError_t me = cudaSuccess;
   auto mk = [&]() {
     if (L.prof && me == cudaSuccess) me = mark(L.prof, st);
@@ -91,7 +132,8 @@ h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st) 
     mk();
   }
   const int top = 31 - __builtin_clz(buckets | 1u);
-  h2_status s = top == 0   ? dense_launch<F, 1>(L, st)
+  h2_status s = tc         ? tc_launch<F>(*tc, st)
+                : top == 0 ? dense_launch<F, 1>(L, st)
                 : top == 1 ? dense_launch<F, 2>(L, st)
                 : top == 2 ? dense_launch<F, 4>(L, st)
                 : top == 3 ? dense_launch<F, 8>(L, st)
@@ -106,10 +148,11 @@ h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st) 
 
 // FB: format of the bases and transfers (the storage format, or FP32 entries)
 template <int F>
-h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st) {
+h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {
   if (L.bases_fp32)
-    return L.k > 32 ? mixed_pass_t<F, h2::kFormF32, 2>(L, buckets, st) : mixed_pass_t<F, h2::kFormF32, 1>(L, buckets, st);
-  return L.k > 32 ? mixed_pass_t<F, F, 2>(L, buckets, st) : mixed_pass_t<F, F, 1>(L, buckets, st);
+    return L.k > 32 ? mixed_pass_t<F, h2::kFormF32, 2>(L, buckets, st, tc)
+                    : mixed_pass_t<F, h2::kFormF32, 1>(L, buckets, st, tc);
+  return L.k > 32 ? mixed_pass_t<F, F, 2>(L, buckets, st, tc) : mixed_pass_t<F, F, 1>(L, buckets, st, tc);
 }
 
 }  // namespace h2i

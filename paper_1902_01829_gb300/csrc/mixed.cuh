@@ -595,8 +595,20 @@ struct __align__(16) MixedBlock {
   float scale;
   unsigned short cols;  // C
   unsigned char vs;     // vector stride (>= C, multiple of 4)
-  unsigned char src;    // bit 0: vector from the second source (yhat); bit 1: FP32 entries (not codes)
+  unsigned char src;    // bit 0: vector from the second source (yhat); bit 1: FP32 entries (not codes);
+                        // bit 2: panel layout (below)
 };
+
+// Panel layout of a block of codes (64 rows, C columns): eight panels of 8 rows,
+// panel p holding column c's rows 8p .. 8p + 7 as 16 contiguous bytes at c * 16,
+// the panels kPanelPad bytes apart beyond their 16 * Cp bytes (Cp = C rounded up
+// to 16, padding columns zero). It is the MN-major operand layout of tcgen05.mma
+// (8 x 8 core matrices: K stride 128 bytes, M stride the panel stride), and the
+// pad staggers the panels over the shared-memory banks for the CUDA-core reader.
+constexpr int kPanelPad = 16;
+__host__ __device__ constexpr int panel_cols(int C) { return (C + 15) & ~15; }
+__host__ __device__ constexpr int panel_stride(int C) { return 16 * panel_cols(C) + kPanelPad; }  // bytes
+__host__ __device__ constexpr int panel_block_bytes(int C) { return 8 * panel_stride(C); }
 
 constexpr int kMixedMaxBlocks = 8;   // blocks of one row per work item
 constexpr int kMixedVecCols = 256;   // vector columns of one work item (sum of its blocks' vs)
@@ -709,7 +721,8 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
       const long long bi = b0 - bfirst + lane;
       if (lane < nb && bi >= 0 && bi < nbatch) mb = blkbuf[bi];
       const int esize = (mb.src & 2) ? 4 : 2;
-      const int codes = (R * (int)mb.cols * esize + 15) & ~15;  // padded bytes of this block
+      const int codes = (mb.src & 4) ? panel_block_bytes(mb.cols)                   // padded bytes of this block
+                                     : (R * (int)mb.cols * esize + 15) & ~15;
       int moff = codes;  // inclusive prefix of the blocks' padded byte counts
 #pragma unroll
       for (int d = 1; d < kMixedMaxBlocks; d <<= 1) {
@@ -727,7 +740,7 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
       const unsigned vtot = __shfl_sync(0xFFFFFFFFu, voff, kMixedMaxBlocks - 1);
       voff -= vbytes;
       if (lane < nb) {
-        hd[8 + 4 * lane] = mb.cols | ((mb.src & 2) << 15);
+        hd[8 + 4 * lane] = mb.cols | ((mb.src & 2) << 15) | ((mb.src & 4) << 15);
         hd[9 + 4 * lane] = mb.vs;
         hd[10 + 4 * lane] = moff;
         hd[11 + 4 * lane] = __float_as_int(mb.scale);
@@ -853,8 +866,11 @@ __device__ __forceinline__ void consume_item(const unsigned char* stage, const i
   const int r0 = 2 * lane;
   for (int t = 0; t < nb; t++) {
     const int cw = hd[8 + 4 * t];
-    const bool f32 = (cw >> 16) & 1;
+    const bool f32 = (cw >> 16) & 1, panel = (cw >> 17) & 1;
     const int C = min(cw & 0xFFFF, 64), vs = min(hd[9 + 4 * t], 64);
+    // codes of rows r0, r0 + 1 in column c: lbase + cstr * c (16-bit units)
+    const int lbase = panel ? (r0 >> 3) * (panel_stride(C) / 2) + (r0 & 7) : r0;
+    const int cstr = panel ? 8 : R;
     const int moff = min(hd[10 + 4 * t], kStageMat - 16) & ~15;
     const float scale = __int_as_float(hd[11 + 4 * t]);
     const int voff = min(hd[kHdVoff + t], VAREA - 16) & ~15;
@@ -872,10 +888,10 @@ __device__ __forceinline__ void consume_item(const unsigned char* stage, const i
     if (!f32 && R == 64 && C == 64 && vs == 64) {
       // full 64 x 64 block of codes: fixed strides, every column loaded up front
       constexpr int CPW = 64 / CW;
-      const uint32_t* Aw = reinterpret_cast<const uint32_t*>(A + r0 + 64 * c0);
+      const uint32_t* Aw = reinterpret_cast<const uint32_t*>(A + lbase + cstr * c0);
       uint32_t w[CPW];
 #pragma unroll
-      for (int u = 0; u < CPW; u++) w[u] = Aw[32 * u];
+      for (int u = 0; u < CPW; u++) w[u] = Aw[(cstr >> 1) * u];
 #pragma unroll
       for (int v = 0; v < NV2; v++) {
         float xv[CPW];
@@ -895,14 +911,14 @@ __device__ __forceinline__ void consume_item(const unsigned char* stage, const i
         }
       }
     } else if (r0 < R) {
-      const bool even = (R & 1) == 0;
+      const bool pair = panel || (R & 1) == 0;  // rows r0, r0 + 1 adjacent: one 4-byte load
       for (int col = c0; col < c1; col++) {
         float2 a;
         if (f32) {
           a.x = A32[r0 + R * col];
           a.y = (r0 + 1 < R) ? A32[r0 + 1 + R * col] : 0.f;
-        } else if (even) {
-          a = codes_to_f2<F>(*reinterpret_cast<const uint32_t*>(A + r0 + R * col));
+        } else if (pair) {
+          a = codes_to_f2<F>(*reinterpret_cast<const uint32_t*>(A + lbase + cstr * col));
         } else {
           a.x = code_to_f<F>(A[r0 + R * col]);
           a.y = (r0 + 1 < R) ? code_to_f<F>(A[r0 + 1 + R * col]) : 0.f;

@@ -1,0 +1,371 @@
+// Dense near field and leaf expansion of the precision form on the 5th-generation
+// tensor cores (tcgen05.mma, FP32 accumulators in tensor memory) for a pass of up
+// to 16 vectors:   y(i) = sum_j D_ij x(j) + U_i yhat_i   (Sec. 2.2 dense blocks,
+// Eq. 4 leaf expansion), with every block stored as 16-bit codes q and one FP32
+// scale sigma (a = sigma q).
+//
+// Operands of one block (M = 64 rows, N = 32, K = the block's columns):
+//  A  the block's fp16 / bf16 codes, copied by TMA as stored (the panel layout of
+//     mixed.cuh is the MN-major canonical layout: 8 x 8 core matrices, K stride
+//     128 bytes, M stride the panel stride);
+//  B  built in shared memory per block by four builder warps from the FP32 copy
+//     of the vectors (x(j), or yhat_i for U_i): z = sigma * s_v * x_v in FP32,
+//     split z = hi + lo into two codes of the block type (rows 2v and 2v + 1 of
+//     the K-major tile), so the products keep about FP32 accuracy and sigma enters
+//     exactly; s_v is a power of two per vector keeping fp16 parts in range (1 for
+//     bf16).
+// All blocks of a row accumulate into one 64 x 32 FP32 accumulator (two of them
+// alternate between rows); four epilogue warps read it back (tcgen05.ld), add the
+// two parts of each vector, divide by s_v and write y in FP64.
+//
+// Warp roles (320 threads, one CTA per SM, persistent over the same byte-balanced
+// work items as the CUDA-core path): 0 producer (TMA of the codes), 1 MMA issuer
+// (one thread), 2-5 B-tile builders, 6-9 epilogue (TMEM lane quadrants 2, 3, 0, 1).
+// Every wait is bounded; on a timeout the kernel sets the error word, the other
+// roles stop at their next wait, the MMA thread waits for its issued MMAs, and the
+// tensor memory is freed before the kernel returns.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "mixed.cuh"
+
+namespace h2 {
+
+constexpr int kTcVec = 16;                 // vectors per pass
+constexpr int kTcN = 2 * kTcVec;           // MMA N (high and low part of each vector)
+constexpr int kTcMaxBlocks = 4;            // blocks per work item (64 x 64 panels: at most 3 + U)
+constexpr int kTcStageB = kTcMaxBlocks * kTcN * 64 * 2;  // B tiles of one stage (16 KB)
+constexpr int kTcHeader = 256;
+constexpr int kTcStage = kTcHeader + kStageMat + kTcStageB;
+constexpr int kTcStages = 4;
+constexpr int kTcSmem = kTcStages * kTcStage + 256;
+constexpr int kTcThreads = 320;
+
+struct TcParams {
+  const StreamItem* items;
+  const int* cta_begin;
+  const MixedBlock* blk;
+  const char* dmat;
+  const float* x4;      // FP32 vectors, leaf j at xp4_off[j] * nv (64 entries per vector)
+  const float* yhat;    // [node][v][kp]
+  const float* vscale;  // [16] per-vector power-of-two scale s_v
+  double* y;
+  long long ldy;
+  int nv, kp;
+  int* err;
+  long long budget;
+};
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);  // no swizzle
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, A and B of the code type,
+// A MN-major, B K-major, N = 32, M = 64
+template <int F>
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | ((F == kFormBf16 ? 1u : 0u) << 7) | ((F == kFormBf16 ? 1u : 0u) << 10) | (1u << 15) |
+         ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int F>
+__device__ __forceinline__ uint32_t tc_pack(float a, float b) {  // two codes, a in the low half
+  if (F == kFormBf16) {
+    const __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&t);
+  }
+  const __half2 t = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&t);
+}
+template <int F>
+__device__ __forceinline__ float tc_round(float z) {  // z rounded to the code type
+  if (F == kFormBf16) return __bfloat162float(__float2bfloat16_rn(z));
+  return __half2float(__float2half_rn(z));
+}
+
+// bounded wait of one warp on an mbarrier phase (all lanes poll; false on timeout or abort)
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                        long long budget) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, err, budget);
+  return __all_sync(0xFFFFFFFFu, ok) != 0;
+}
+
+// stage header (ints): [0] blocks, [1] flags; block t at 4 + 4 t: A offset (bytes),
+// K | (B source is yhat) << 16, panel stride (bytes), scale bits; [24 + 2 t] vector offset
+// (long long, in floats per vector slot)
+template <int F>
+__global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* stage0 = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kTcStages * kTcStage);
+  uint64_t* hdr = full + kTcStages;
+  uint64_t* bready = hdr + kTcStages;
+  uint64_t* empty = bready + kTcStages;
+  uint64_t* accfull = empty + kTcStages;
+  uint64_t* accempty = accfull + 2;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(accempty + 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2) + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ib = P.cta_begin[blockIdx.x], ie = P.cta_begin[blockIdx.x + 1];
+  const int n_items = ie - ib;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; s++) {
+      mbar_init(full + s, 1);
+      mbar_init(hdr + s, 1);
+      mbar_init(bready + s, 4);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(accfull + b, 1);
+      mbar_init(accempty + b, 4);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)), "r"(64)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      const uint64_t pol = policy_evict_first();
+      int issued = 0;
+      for (int it = 0; it < n_items; it++) {
+        const int s = it % kTcStages, use = it / kTcStages;
+        if (use > 0 && !mbar_wait(empty + s, (use - 1) & 1, abort_flag, P.err, P.budget)) break;
+        const StreamItem I = P.items[ib + it];
+        unsigned char* st = stage0 + s * kTcStage;
+        int* hd = reinterpret_cast<int*>(st);
+        const int nb = min((int)((I.shape >> 8) & 0xFF), kTcMaxBlocks);
+        int aoff = 0;
+        for (int t = 0; t < nb; t++) {
+          const MixedBlock mb = P.blk[I.v_off + t];
+          const int C = min((int)mb.cols, 64);
+          hd[4 + 4 * t] = aoff;
+          hd[5 + 4 * t] = panel_cols(C) | ((mb.src & 1) << 16);
+          hd[6 + 4 * t] = panel_stride(C);
+          hd[7 + 4 * t] = __float_as_int(mb.scale);
+          *reinterpret_cast<long long*>(hd + 24 + 2 * t) = mb.voff;
+          aoff += panel_block_bytes(C);
+        }
+        hd[0] = nb;
+        hd[1] = I.flags;
+        const unsigned bytes = (unsigned)min(I.m_bytes, kStageMat);
+        mbar_arrive(hdr + s);  // header ready for the builders (release)
+        mbar_arrive_expect_tx(full + s, bytes);
+        bulk_g2s_stream(st + kTcHeader, P.dmat + I.m_off, bytes, full + s, pol);
+        issued = it + 1;
+      }
+      for (int it = max(0, issued - kTcStages); it < issued; it++) {  // copies in flight land before exit
+        const int s = it % kTcStages, use = it / kTcStages;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(full + s, use & 1) && clock64() - t0 < P.budget) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc<F>();
+      int rows = 0, issued_it = -1;
+      bool row_open = false, ok = true;
+      uint32_t acc_col = 0;
+      for (int it = 0; it < n_items && ok; it++) {
+        const int s = it % kTcStages, use = it / kTcStages;
+        if (!mbar_wait(full + s, use & 1, abort_flag, P.err, P.budget) ||
+            !mbar_wait(bready + s, use & 1, abort_flag, P.err, P.budget)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* st = stage0 + s * kTcStage;
+        const int* hd = reinterpret_cast<const int*>(st);
+        const int nb = min(hd[0], kTcMaxBlocks), flags = hd[1];
+        bool first = false;
+        if (!row_open) {  // a new row: its accumulator must have been read out
+          const int b = rows & 1;
+          if (rows >= 2 && !mbar_wait(accempty + b, ((rows >> 1) - 1) & 1, abort_flag, P.err, P.budget)) {
+            ok = false;
+            break;
+          }
+          acc_col = (uint32_t)(b * kTcN);
+          row_open = true;
+          first = true;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_addr(st + kTcHeader), b0 = smem_addr(st + kTcHeader + kStageMat);
+        uint32_t boff = 0;
+        for (int t = 0; t < nb; t++) {
+          const int aoff = min(hd[4 + 4 * t], kStageMat - 1024);
+          const int K = min(hd[5 + 4 * t] & 0xFFFF, 64), ps = hd[6 + 4 * t];
+          for (int ks = 0; ks < K / 16; ks++) {
+            const uint64_t da = tc_desc(a0 + aoff + ks * 256, 128, ps);
+            const uint64_t db = tc_desc(b0 + boff + ks * 256, 128, K * 16);
+            tc_mma(tmem + acc_col, da, db, idesc, first ? 0u : 1u);
+            first = false;
+          }
+          boff += kTcN * K * 2;
+        }
+        tc_commit(empty + s);  // the stage is free once these MMAs complete
+        issued_it = it;
+        if (flags & kItemFlagLast) {
+          tc_commit(accfull + (rows & 1));
+          rows++;
+          row_open = false;
+        }
+      }
+      if (issued_it >= 0) {  // issued MMAs complete before the tensor memory is freed
+        const int s = issued_it % kTcStages, use = issued_it / kTcStages;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(empty + s, use & 1) && clock64() - t0 < P.budget) {
+        }
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------------------------------------------------------- B-tile builders
+    // thread: vector v = tid / 8 (0 .. 15), K group g = tid % 8 (8 entries); it writes the
+    // 16-byte high and low rows of its vector for that K group
+    const int tid = threadIdx.x - 64, v = tid >> 3, g = tid & 7;
+    const float sv = P.vscale[v];
+    for (int it = 0; it < n_items; it++) {
+      const int s = it % kTcStages, use = it / kTcStages;
+      if (!tc_wait(hdr + s, use & 1, abort_flag, P.err, P.budget)) break;
+      unsigned char* st = stage0 + s * kTcStage;
+      const int* hd = reinterpret_cast<const int*>(st);
+      const int nb = min(hd[0], kTcMaxBlocks);
+      unsigned char* bt = st + kTcHeader + kStageMat;
+      int boff = 0;
+      for (int t = 0; t < nb; t++) {
+        const int K = min(hd[5 + 4 * t] & 0xFFFF, 64);
+        const bool from_yhat = (hd[5 + 4 * t] >> 16) & 1;
+        const float sc = __int_as_float(hd[7 + 4 * t]) * sv;
+        const long long voff = *reinterpret_cast<const long long*>(hd + 24 + 2 * t);
+        if (8 * g < K) {
+          float z[8];
+          if (v < P.nv) {
+            const float* src = from_yhat ? P.yhat + voff * P.nv + (long long)v * P.kp + 8 * g
+                                         : P.x4 + voff * P.nv + (long long)v * 64 + 8 * g;
+            const float4 z0 = __ldg(reinterpret_cast<const float4*>(src));
+            const float4 z1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+            z[0] = z0.x * sc, z[1] = z0.y * sc, z[2] = z0.z * sc, z[3] = z0.w * sc;
+            z[4] = z1.x * sc, z[5] = z1.y * sc, z[6] = z1.z * sc, z[7] = z1.w * sc;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; e++) z[e] = 0.f;
+          }
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const float h0 = tc_round<F>(z[2 * e]), h1 = tc_round<F>(z[2 * e + 1]);
+            hi[e] = tc_pack<F>(h0, h1);
+            lo[e] = tc_pack<F>(z[2 * e] - h0, z[2 * e + 1] - h1);
+          }
+          // K-major tile: row n = 2v (+1), core (n / 8, g) at (n / 8) * K * 16 + g * 128, row n % 8 at 16 bytes
+          unsigned char* dst = bt + boff + ((2 * v) >> 3) * K * 16 + g * 128 + ((2 * v) & 7) * 16;
+          *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(dst + 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        boff += kTcN * K * 2;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bready + s);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    // warp w reads TMEM lanes 32 (w % 4) ..; rows 16 (w % 4) + lane (lane < 16) of the row block
+    const int q = warp & 3;
+    float inv[kTcVec];
+#pragma unroll
+    for (int v = 0; v < kTcVec; v++) inv[v] = 1.0f / P.vscale[v];
+    int r = 0;
+    for (int it = 0; it < n_items; it++) {
+      const StreamItem I = P.items[ib + it];
+      if (!(I.flags & kItemFlagLast)) continue;
+      const int b = r & 1;
+      if (!tc_wait(accfull + b, (r >> 1) & 1, abort_flag, P.err, P.budget)) break;
+      tc_fence_after();
+      uint32_t c[kTcN];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcN);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
+            "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15]),
+            "=r"(c[16]), "=r"(c[17]), "=r"(c[18]), "=r"(c[19]), "=r"(c[20]), "=r"(c[21]), "=r"(c[22]), "=r"(c[23]),
+            "=r"(c[24]), "=r"(c[25]), "=r"(c[26]), "=r"(c[27]), "=r"(c[28]), "=r"(c[29]), "=r"(c[30]), "=r"(c[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accempty + b);
+      if (lane < 16) {
+        double* yr = P.y + I.row + 16 * q + lane;
+#pragma unroll
+        for (int v = 0; v < kTcVec; v++)
+          if (v < P.nv) yr[v * P.ldy] = (double)((__uint_as_float(c[2 * v]) + __uint_as_float(c[2 * v + 1])) * inv[v]);
+      }
+      r++;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64) : "memory");
+  }
+}
+
+// Per-vector power-of-two scales of a pass (fp16 codes): s_v = 2^(14 - e) with 2^e above
+// every |sigma x_v| and |sigma_U yhat_v| the builders form, so their parts stay below 2^14.
+// vmax holds float bits of the maxima (zeroed before the pass); one warp per (leaf, vector).
+template <int F>
+__global__ void k_tc_vmax(const float* __restrict__ x4, const float* __restrict__ yhat, const long long* __restrict__ xp4_off,
+                          long long leaves, long long leaf0, int nv, int kp, int k, float dmax, float umax,
+                          unsigned* __restrict__ vmax) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= leaves * nv) return;
+  const long long j = w / nv;
+  const int v = (int)(w - j * nv);
+  const float* xs = x4 + xp4_off[j] * nv + (long long)v * 64;
+  const float* ys = yhat + ((leaf0 + j) * nv + v) * (long long)kp;
+  float m = fmaxf(fabsf(xs[lane]), fabsf(xs[lane + 32])) * dmax;
+  for (int r = lane; r < k; r += 32) m = fmaxf(m, fabsf(ys[r]) * umax);
+  for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
+  if (lane == 0) atomicMax(vmax + v, __float_as_uint(m));  // non-negative floats order as their bits
+}
+
+template <int F>
+__global__ void k_tc_vscale(const unsigned* __restrict__ vmax, float* __restrict__ vscale, int fp16) {
+  const int v = threadIdx.x;
+  if (v >= kTcVec) return;
+  const float m = __uint_as_float(vmax[v]);
+  int e = 0;
+  if (fp16 && m > 0.f && m < 3.0e38f) frexpf(m, &e);  // m < 2^e
+  vscale[v] = fp16 ? ldexpf(1.0f, 14 - e) : 1.0f;
+}
+
+}  // namespace h2

@@ -107,3 +107,52 @@ def test_full_size_2d_n1M(h2, form, nv, bases_fp32, tol_store):
     y = run(h2, A, form, x, bases_fp32)
     assert oracle.rel_l2(y, oracle.matvec(A, x, **quant.dequantized_arrays(A, form, bases_fp32))) <= TOL_ACC
     assert oracle.rel_l2(y, oracle.matvec(A, x)) <= tol_store
+
+
+# Leaves of exactly 64 points with fp16 / bf16 codes (16-bit bases, rank a multiple of 16): the
+# blocks are stored in the panel layout; passes of at least 8 vectors run the dense phase on the
+# tensor cores (tcgen05), smaller ones on the CUDA cores. Both must agree with the quantized
+# oracle to FP32 accuracy.
+@pytest.fixture(scope="module")
+def panel2d():
+    return h2gen.generate(dim=2, n=16384, m=64, p=4, eta=0.9, kernel="exp", ell=0.1, seed=21)
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+@pytest.mark.parametrize("nv", [1, 3, 8, 16, 20])
+def test_panel_layout_and_tensor_cores_2d(h2, panel2d, form, nv):
+    A = panel2d
+    assert all(A.leaf_size(i) == 64 for i in range(A.leaves))
+    x = h2gen.vectors(640 + nv, A.n, nv)
+    M = h2.H2Matrix.from_generator(A, storage=form)
+    M.profile(True)
+    y = M.matvec(to_dev(x))
+    M.check()
+    _, launches = M.profile_read()
+    passes = [min(16, nv - v0) for v0 in range(0, nv, 16)]
+    per_pass = [(7 if form == "fp16" else 6) if p >= 8 else 5 for p in passes]
+    assert launches == sum(per_pass), (launches, per_pass)  # the tensor-core passes launched their kernels
+    out = y.cpu().numpy()
+    M.close()
+    ref = oracle.matvec(A, x, **quant.dequantized_arrays(A, form))
+    assert oracle.rel_l2(out, ref) <= TOL_ACC
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+@pytest.mark.parametrize("nv", [2, 16])
+def test_panel_layout_and_tensor_cores_3d_k64(h2, form, nv):
+    A = h2gen.generate(dim=3, n=8192, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=22)
+    assert A.k == 64 and all(A.leaf_size(i) == 64 for i in range(A.leaves))
+    x = h2gen.vectors(650 + nv, A.n, nv)
+    y = run(h2, A, form, x)
+    assert oracle.rel_l2(y, oracle.matvec(A, x, **quant.dequantized_arrays(A, form))) <= TOL_ACC
+
+
+def test_tensor_core_pass_scales_large_vectors(h2, panel2d):
+    """fp16 parts of the vectors are scaled per vector by a power of two: entries far outside the
+    fp16 range give the same relative accuracy."""
+    A = panel2d
+    x = h2gen.vectors(660, A.n, 16) * np.ldexp(1.0, np.arange(16) * 4 - 30)[None, :]
+    y = run(h2, A, "fp16", x)
+    ref = oracle.matvec(A, x, **quant.dequantized_arrays(A, "fp16"))
+    assert oracle.rel_l2(y, ref) <= TOL_ACC
