@@ -413,6 +413,13 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
       }
       if (!ok) return h2_fail(H2_ERR_INVALID, "internal: precision-form work item %lld fails the layout audit", (long long)t);
     }
+    if (M.panel)  // the tensor-core phase starts a row's four accumulators with its first four K-steps
+      for (int64_t i = 0; i < leaves; i++) {
+        int64_t ksteps = 0;
+        for (int64_t g = row_blk0[i]; g < row_blk0[i + 1]; g++) ksteps += h2::panel_cols(blk[g].cols) / 16;
+        if (ksteps < h2::kTcAccs) return h2_fail(H2_ERR_INVALID, "internal: leaf row %lld has %lld tensor-core K-steps",
+                                                 (long long)i, (long long)ksteps);
+      }
     if ((st = upload(h, &M.dense_items.items, items.data(), (int64_t)items.size())) != H2_OK) return st;
     if ((st = upload(h, &M.dense_items.cta_begin, begin.data(), (int64_t)begin.size())) != H2_OK) return st;
     M.dense_items.count = (int64_t)items.size();

@@ -202,30 +202,62 @@ __device__ __forceinline__ TreeParamsM tree_params(const MatDesc& D) {
   return P;
 }
 
+// copy n floats (n a multiple of 4, both ends 16-byte aligned) into the warp's staging buffer;
+// CG: read through L2 (the data was written by another CTA)
+template <bool CG>
+__device__ __forceinline__ void stage_vectors(float* __restrict__ dst, const float* __restrict__ src, int n, int lane) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int i = lane; i < n / 4; i += 32) d4[i] = CG ? __ldcg(s4 + i) : s4[i];
+  __syncwarp();
+}
+
+// Each warp stages the vector block it multiplies (a leaf's x chunk, a child's xhat, a
+// parent's yhat: nv x up to 64 floats) in its own shared-memory buffer wbuf, so that
+// warp_mv_m's many reads of it are shared-memory reads.
 template <int F, int RPL, int NVB>
-__device__ __forceinline__ void project_leaf_m(const TreeParamsM& P, int64_t j, int lane) {
+__device__ __forceinline__ void project_leaf_m(const TreeParamsM& P, int64_t j, int lane, float* wbuf) {
   const int64_t leaf0 = ((int64_t)1 << P.q) - 1;
   const int64_t off = P.leaf_off[j];
   const int sj = (int)(P.leaf_off[j + 1] - off);
   const int spad = (sj + 3) & ~3;
   float* xj = P.x4 + P.xp4_off[j] * P.nv;
-  for (int v = 0; v < P.nv; v++)
-    for (int a = lane; a < spad; a += 32)  // padding columns are zero
-      xj[v * spad + a] = a < sj ? __double2float_rn(P.x[v * P.ldx + off + a]) : 0.f;
+  const double* __restrict__ xs = P.x + off;
+  // every load of the chunk is issued before any store (the stores could alias x for the compiler)
+  float xr[NVB][2];
+#pragma unroll
+  for (int v = 0; v < NVB; v++)
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int a = lane + 32 * h;
+      xr[v][h] = (v < P.nv && a < sj) ? __double2float_rn(__ldg(xs + v * P.ldx + a)) : 0.f;  // padding is zero
+    }
+#pragma unroll
+  for (int v = 0; v < NVB; v++)
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int a = lane + 32 * h;
+      if (v < P.nv && a < spad) {
+        xj[v * spad + a] = xr[v][h];
+        wbuf[v * spad + a] = xr[v][h];
+      }
+    }
   __syncwarp();
   float acc[RPL][NVB];
 #pragma unroll
   for (int r = 0; r < RPL; r++)
 #pragma unroll
     for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
-  warp_mv_m<F, RPL, NVB>(static_cast<const typename CodeT<F>::T*>(P.Vt) + P.vt_off[j], P.vscale[j], P.k, sj, P.LR, xj,
+  warp_mv_m<F, RPL, NVB>(static_cast<const typename CodeT<F>::T*>(P.Vt) + P.vt_off[j], P.vscale[j], P.k, sj, P.LR, wbuf,
                          spad, P.nv, acc, lane);
+  __syncwarp();
   group_reduce_m(acc, P.LR);
   store_node_m<RPL, NVB, false>(P.xhat + (leaf0 + j) * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, acc, lane);
 }
 
+// parent p of the upsweep for vectors v0 .. v0 + nw - 1 (nw <= NVB)
 template <int F, int RPL, int NVB, bool CG>
-__device__ __forceinline__ void up_node_m(const TreeParamsM& P, int64_t p, int lane) {
+__device__ __forceinline__ void up_node_m(const TreeParamsM& P, int64_t p, int lane, float* wbuf, int v0, int nw) {
   float acc[RPL][NVB];
 #pragma unroll
   for (int r = 0; r < RPL; r++)
@@ -233,23 +265,19 @@ __device__ __forceinline__ void up_node_m(const TreeParamsM& P, int64_t p, int l
     for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
   for (int ci = 1; ci <= 2; ci++) {
     const int64_t ch = 2 * p + ci;
-    const float* xc = P.xhat + ch * P.nv * P.kp;
-    if (CG) {  // the sibling subtree was written by another CTA: read it through L2
-      __shared__ float tmp[kTreeWarpsM][16 * 64];
-      float* t = tmp[threadIdx.x >> 5];
-      for (int i = lane; i < P.nv * P.kp; i += 32) t[i] = __ldcg(xc + i);
-      __syncwarp();
-      warp_mv_m<F, RPL, NVB>(static_cast<const typename CodeT<F>::T*>(P.Ft) + (ch - 1) * P.kk8, P.fscale[ch - 1], P.k,
-                             P.k, P.LR, t, P.kp, P.nv, acc, lane);
-      __syncwarp();
-    } else {
-      warp_mv_m<F, RPL, NVB>(static_cast<const typename CodeT<F>::T*>(P.Ft) + (ch - 1) * P.kk8, P.fscale[ch - 1], P.k,
-                             P.k, P.LR, xc, P.kp, P.nv, acc, lane);
-    }
+    // CG: the sibling subtree was written by another CTA
+    stage_vectors<CG>(wbuf, P.xhat + (ch * P.nv + v0) * P.kp, nw * P.kp, lane);
+    warp_mv_m<F, RPL, NVB>(static_cast<const typename CodeT<F>::T*>(P.Ft) + (ch - 1) * P.kk8, P.fscale[ch - 1], P.k, P.k,
+                           P.LR, wbuf, P.kp, nw, acc, lane);
+    __syncwarp();
   }
   group_reduce_m(acc, P.LR);
-  store_node_m<RPL, NVB, false>(P.xhat + p * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, acc, lane);
+  store_node_m<RPL, NVB, false>(P.xhat + (p * P.nv + v0) * P.kp, P.k, P.kp, P.LR, nw, acc, lane);
 }
+
+// vectors per warp where the warps of a CTA split one node's vectors between them
+template <int NVB>
+__host__ __device__ constexpr int slice_vectors() { return NVB >= kTreeWarpsM ? NVB / kTreeWarpsM : 1; }
 
 // leaf projection + the whole upsweep in one launch (see k_upsweep_tree)
 // CTA b works on subtree jobs[b].y of matrix jobs[b].x
@@ -257,37 +285,43 @@ template <int F, int RPL, int NVB>
 // (the matrices whose vector count lies outside [nvlo, nvhi] are left to another launch: all their CTAs return)
 __global__ void __launch_bounds__(kTreeWarpsM * 32) k_upsweep_tree_m(const MatDesc* __restrict__ mats,
                                                                     const int2* __restrict__ jobs, int nvlo, int nvhi) {
+  __shared__ __align__(16) float wstage[kTreeWarpsM][NVB * 64];
   const int2 job = jobs[blockIdx.x];
   const TreeParamsM P = tree_params(mats[job.x]);
   if (P.nv < nvlo || P.nv > nvhi) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* wbuf = wstage[warp];
   const int T = P.q - P.L;
   const int64_t sub = job.y;
-  for (int64_t t = warp; t < ((int64_t)1 << T); t += kTreeWarpsM) project_leaf_m<F, RPL, NVB>(P, (sub << T) + t, lane);
+  for (int64_t t = warp; t < ((int64_t)1 << T); t += kTreeWarpsM)
+    project_leaf_m<F, RPL, NVB>(P, (sub << T) + t, lane, wbuf);
   __syncthreads();
   for (int lvl = P.q - 1; lvl >= P.L; lvl--) {
     const int64_t node0 = ((int64_t)1 << lvl) - 1 + (sub << (lvl - P.L));
     for (int64_t t = warp; t < ((int64_t)1 << (lvl - P.L)); t += kTreeWarpsM)
-      up_node_m<F, RPL, NVB, false>(P, node0 + t, lane);
+      up_node_m<F, RPL, NVB, false>(P, node0 + t, lane, wbuf, 0, P.nv);
     __syncthreads();
   }
   __threadfence();
   __syncthreads();
-  if (warp != 0) return;
+  // climb while this CTA arrives second at the parent; every warp takes a slice of the vectors
+  __shared__ int second;
+  constexpr int NVW = slice_vectors<NVB>();
+  const int v0 = warp * NVW, nw = min(NVW, P.nv - v0);
   int64_t node = ((int64_t)1 << P.L) - 1 + sub;
   while (node > 0) {
     const int64_t par = (node - 1) / 2;
-    int second = 0;
-    if (lane == 0) {
-      second = atomicAdd(P.ticket + par, 1) == 1;
-      if (second) P.ticket[par] = 0;
+    if (threadIdx.x == 0) {
+      const int s2 = atomicAdd(P.ticket + par, 1) == 1;
+      if (s2) P.ticket[par] = 0;
+      second = s2;
     }
-    second = __shfl_sync(0xFFFFFFFFu, second, 0);
+    __syncthreads();
     if (!second) break;
     __threadfence();
-    up_node_m<F, RPL, NVB, true>(P, par, lane);
+    if (nw > 0) up_node_m<F, RPL, NVW, true>(P, par, lane, wbuf, v0, nw);
     __threadfence();
-    __syncwarp();
+    __syncthreads();
     node = par;
   }
 }
@@ -298,26 +332,32 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(const Mat
                                                                       const int2* __restrict__ jobs, int nvlo,
                                                                       int nvhi) {
   __shared__ float path[2][NVB][64];
+  __shared__ __align__(16) float wstage[kTreeWarpsM][NVB * 64];
   const int2 job = jobs[blockIdx.x];
   const TreeParamsM P = tree_params(mats[job.x]);
   if (P.nv < nvlo || P.nv > nvhi) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* wbuf = wstage[warp];
   const int64_t sub = job.y;
   const int64_t root = ((int64_t)1 << P.L) - 1 + sub;
-  if (warp == 0 && P.L > 0) {
+  // the path from the root to the subtree root, recomputed by every CTA; every warp takes a
+  // slice of the vectors (the slices are independent)
+  constexpr int NVW = slice_vectors<NVB>();
+  const int v0 = warp * NVW, nw = min(NVW, P.nv - v0);
+  if (P.L > 0 && nw > 0) {
     int cur = 0;
-    for (int v = 0; v < P.nv; v++)
+    for (int v = v0; v < v0 + nw; v++)
       for (int r = lane; r < P.k; r += 32) path[cur][v][r] = P.yhat[(int64_t)v * P.kp + r];
     __syncwarp();
     for (int l = 1; l <= P.L; l++) {
       const int64_t a = ((root + 1) >> (P.L - l)) - 1;
-      float acc[RPL][NVB];
+      float acc[RPL][NVW];
 #pragma unroll
       for (int r = 0; r < RPL; r++)
 #pragma unroll
-        for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
-      warp_mv_m<F, RPL, NVB>(static_cast<const typename CodeT<F>::T*>(P.E) + (a - 1) * P.kk8, P.escale[a - 1], P.k, P.k,
-                             P.LR, &path[cur][0][0], 64, P.nv, acc, lane);
+        for (int v = 0; v < NVW; v++) acc[r][v] = 0.f;
+      warp_mv_m<F, RPL, NVW>(static_cast<const typename CodeT<F>::T*>(P.E) + (a - 1) * P.kk8, P.escale[a - 1], P.k, P.k,
+                             P.LR, &path[cur][v0][0], 64, nw, acc, lane);
       group_reduce_m(acc, P.LR);
       if (lane < P.LR) {
 #pragma unroll
@@ -325,11 +365,12 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(const Mat
           const int row = lane + 32 * rr;
           if (row >= P.k) continue;
 #pragma unroll
-          for (int v = 0; v < NVB; v++) {
-            if (v >= P.nv) continue;
-            const float val = acc[rr][v] + P.yhat[(a * P.nv + v) * P.kp + row];
-            if (l == P.L) P.yhat[(a * P.nv + v) * P.kp + row] = val;
-            else path[cur ^ 1][v][row] = val;
+          for (int v = 0; v < NVW; v++) {
+            if (v >= nw) continue;
+            const int64_t at = (a * P.nv + v0 + v) * P.kp + row;
+            const float val = acc[rr][v] + P.yhat[at];
+            if (l == P.L) P.yhat[at] = val;
+            else path[cur ^ 1][v0 + v][row] = val;
           }
         }
       }
@@ -347,8 +388,10 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(const Mat
       for (int r = 0; r < RPL; r++)
 #pragma unroll
         for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
+      stage_vectors<false>(wbuf, P.yhat + ((ch - 1) / 2) * P.nv * P.kp, P.nv * P.kp, lane);
       warp_mv_m<F, RPL, NVB>(static_cast<const typename CodeT<F>::T*>(P.E) + (ch - 1) * P.kk8, P.escale[ch - 1], P.k,
-                             P.k, P.LR, P.yhat + ((ch - 1) / 2) * P.nv * P.kp, P.kp, P.nv, acc, lane);
+                             P.k, P.LR, wbuf, P.kp, P.nv, acc, lane);
+      __syncwarp();
       group_reduce_m(acc, P.LR);
       store_node_m<RPL, NVB, true>(P.yhat + ch * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, acc, lane);
     }

@@ -14,9 +14,10 @@
 //     the K-major tile), so the products keep about FP32 accuracy and sigma enters
 //     exactly; s_v is a power of two per vector keeping fp16 parts in range (1 for
 //     bf16).
-// All blocks of a row accumulate into one 64 x 32 FP32 accumulator (two of them
-// alternate between rows); four epilogue warps read it back (tcgen05.ld), add the
-// two parts of each vector, divide by s_v and write y in FP64.
+// The K-steps of a row's blocks go round-robin into four 64 x 32 FP32 accumulators
+// (independent MMA chains; two such sets alternate between rows); four epilogue warps
+// read them back (tcgen05.ld), add them and the two parts of each vector, divide by
+// s_v and write y in FP64.
 //
 // Warp roles (320 threads, one CTA per SM, persistent over the same byte-balanced
 // work items as the CUDA-core path): 0 producer (TMA of the codes), 1 MMA issuer
@@ -39,8 +40,11 @@ constexpr int kTcStageB = kTcMaxBlocks * kTcN * 64 * 2;  // B tiles of one stage
 constexpr int kTcHeader = 256;
 constexpr int kTcStage = kTcHeader + kStageMat + kTcStageB;
 constexpr int kTcStages = 4;
-constexpr int kTcSmem = kTcStages * kTcStage + 256;
+constexpr int kTcBlkBuf = 32 * kTcMaxBlocks * 16;  // block records of 32 items (producer)
+constexpr int kTcSmem = kTcStages * kTcStage + 256 + kTcBlkBuf;
 constexpr int kTcThreads = 320;
+constexpr int kTcAccs = 4;                  // accumulators per row: K-step s goes to s % 4 (independent MMA chains)
+constexpr int kTcCols = 2 * kTcAccs * kTcN;  // tensor-memory columns: two rows in flight
 
 struct TcParams {
   const StreamItem* items;
@@ -139,7 +143,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
     fence_mbar_init();
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)), "r"(64)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(kTcCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -150,47 +155,84 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
-    if (lane == 0) {
-      const uint64_t pol = policy_evict_first();
-      int issued = 0;
-      for (int it = 0; it < n_items; it++) {
+    // 32 items at a time: lane l loads item base + l, the items' block records (a contiguous
+    // range) go to shared memory, then the warp walks the items; lane 0 issues the copies
+    MixedBlock* blkbuf = reinterpret_cast<MixedBlock*>(smem + kTcStages * kTcStage + 256);
+    const uint64_t pol = policy_evict_first();
+    int issued = 0;
+    bool ok = true;
+    for (int base = 0; base < n_items && ok; base += 32) {
+      const int cnt = min(32, n_items - base);
+      StreamItem mine{};
+      if (lane < cnt) mine = P.items[ib + base + lane];
+      const long long bfirst = __shfl_sync(0xFFFFFFFFu, mine.v_off, 0);
+      const long long blast = __shfl_sync(0xFFFFFFFFu, mine.v_off, cnt - 1) +
+                              min((int)((__shfl_sync(0xFFFFFFFFu, mine.shape, cnt - 1) >> 8) & 0xFF), kTcMaxBlocks);
+      const int nrec = (int)min(max(blast - bfirst, 0ll), (long long)(32 * kTcMaxBlocks));
+      __syncwarp();
+      for (int u = lane; u < nrec; u += 32) blkbuf[u] = P.blk[bfirst + u];
+      __syncwarp();
+      for (int t = 0; t < cnt; t++) {
+        const int it = base + t;
         const int s = it % kTcStages, use = it / kTcStages;
-        if (use > 0 && !mbar_wait(empty + s, (use - 1) & 1, abort_flag, P.err, P.budget)) break;
-        const StreamItem I = P.items[ib + it];
+        if (use > 0 && !tc_wait(empty + s, (use - 1) & 1, abort_flag, P.err, P.budget)) {
+          ok = false;
+          break;
+        }
+        const long long m_off = __shfl_sync(0xFFFFFFFFu, mine.m_off, t);
+        const int m_bytes = __shfl_sync(0xFFFFFFFFu, mine.m_bytes, t);
+        const unsigned shape = __shfl_sync(0xFFFFFFFFu, mine.shape, t);
+        const long long v_off = __shfl_sync(0xFFFFFFFFu, mine.v_off, t);
+        const int flags = __shfl_sync(0xFFFFFFFFu, mine.flags, t);
+        const int nb = min((int)((shape >> 8) & 0xFF), kTcMaxBlocks);
         unsigned char* st = stage0 + s * kTcStage;
         int* hd = reinterpret_cast<int*>(st);
-        const int nb = min((int)((I.shape >> 8) & 0xFF), kTcMaxBlocks);
-        int aoff = 0;
-        for (int t = 0; t < nb; t++) {
-          const MixedBlock mb = P.blk[I.v_off + t];
-          const int C = min((int)mb.cols, 64);
-          hd[4 + 4 * t] = aoff;
-          hd[5 + 4 * t] = panel_cols(C) | ((mb.src & 1) << 16);
-          hd[6 + 4 * t] = panel_stride(C);
-          hd[7 + 4 * t] = __float_as_int(mb.scale);
-          *reinterpret_cast<long long*>(hd + 24 + 2 * t) = mb.voff;
-          aoff += panel_block_bytes(C);
+        MixedBlock mb{};
+        const long long bi = v_off - bfirst + lane;
+        if (lane < nb && bi >= 0 && bi < nrec) mb = blkbuf[bi];
+        const int C = min((int)mb.cols, 64);
+        const int bytes_t = lane < nb ? panel_block_bytes(C) : 0;
+        int aoff = bytes_t;  // inclusive prefix over the item's blocks
+#pragma unroll
+        for (int d = 1; d < kTcMaxBlocks; d <<= 1) {
+          const int o = __shfl_up_sync(0xFFFFFFFFu, aoff, d);
+          if (lane >= d) aoff += o;
         }
-        hd[0] = nb;
-        hd[1] = I.flags;
-        const unsigned bytes = (unsigned)min(I.m_bytes, kStageMat);
-        mbar_arrive(hdr + s);  // header ready for the builders (release)
-        mbar_arrive_expect_tx(full + s, bytes);
-        bulk_g2s_stream(st + kTcHeader, P.dmat + I.m_off, bytes, full + s, pol);
+        aoff -= bytes_t;
+        if (lane < nb) {
+          hd[4 + 4 * lane] = aoff;
+          hd[5 + 4 * lane] = panel_cols(C) | ((mb.src & 1) << 16);
+          hd[6 + 4 * lane] = panel_stride(C);
+          hd[7 + 4 * lane] = __float_as_int(mb.scale);
+          *reinterpret_cast<long long*>(hd + 24 + 2 * lane) = mb.voff;
+        }
+        if (lane == 0) {
+          hd[0] = nb;
+          hd[1] = flags;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          const unsigned bytes = (unsigned)min(m_bytes, kStageMat);
+          mbar_arrive(hdr + s);  // header ready for the builders (release)
+          mbar_arrive_expect_tx(full + s, bytes);
+          bulk_g2s_stream(st + kTcHeader, P.dmat + m_off, bytes, full + s, pol);
+        }
+        __syncwarp();
         issued = it + 1;
       }
+    }
+    if (lane == 0)
       for (int it = max(0, issued - kTcStages); it < issued; it++) {  // copies in flight land before exit
         const int s = it % kTcStages, use = it / kTcStages;
         const long long t0 = clock64();
         while (!mbar_try_wait(full + s, use & 1) && clock64() - t0 < P.budget) {
         }
       }
-    }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = tc_idesc<F>();
-      int rows = 0, issued_it = -1;
+      int rows = 0, issued_it = -1, kstep = 0;
       bool row_open = false, ok = true;
       uint32_t acc_col = 0;
       for (int it = 0; it < n_items && ok; it++) {
@@ -203,16 +245,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
         const unsigned char* st = stage0 + s * kTcStage;
         const int* hd = reinterpret_cast<const int*>(st);
         const int nb = min(hd[0], kTcMaxBlocks), flags = hd[1];
-        bool first = false;
         if (!row_open) {  // a new row: its accumulator must have been read out
           const int b = rows & 1;
           if (rows >= 2 && !mbar_wait(accempty + b, ((rows >> 1) - 1) & 1, abort_flag, P.err, P.budget)) {
             ok = false;
             break;
           }
-          acc_col = (uint32_t)(b * kTcN);
+          acc_col = (uint32_t)(b * kTcAccs * kTcN);
           row_open = true;
-          first = true;
+          kstep = 0;
         }
         tc_fence_after();
         const uint32_t a0 = smem_addr(st + kTcHeader), b0 = smem_addr(st + kTcHeader + kStageMat);
@@ -223,8 +264,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
           for (int ks = 0; ks < K / 16; ks++) {
             const uint64_t da = tc_desc(a0 + aoff + ks * 256, 128, ps);
             const uint64_t db = tc_desc(b0 + boff + ks * 256, 128, K * 16);
-            tc_mma(tmem + acc_col, da, db, idesc, first ? 0u : 1u);
-            first = false;
+            // the first four K-steps of a row start the four accumulators (every row has its
+            // 64 x 64 diagonal block, four K-steps)
+            tc_mma(tmem + acc_col + (uint32_t)((kstep % kTcAccs) * kTcN), da, db, idesc, kstep >= kTcAccs ? 1u : 0u);
+            kstep++;
           }
           boff += kTcN * K * 2;
         }
@@ -246,35 +289,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
   } else if (warp < 6) {
     // ---------------------------------------------------------------- B-tile builders
     // thread: vector v = tid / 8 (0 .. 15), K group g = tid % 8 (8 entries); it writes the
-    // 16-byte high and low rows of its vector for that K group
+    // 16-byte high and low rows of its vector for that K group. The loads of item it + 1
+    // are issued before item it is converted and stored (one item of look-ahead).
     const int tid = threadIdx.x - 64, v = tid >> 3, g = tid & 7;
     const float sv = P.vscale[v];
-    for (int it = 0; it < n_items; it++) {
+    float4 za[2][kTcMaxBlocks], zb[2][kTcMaxBlocks];
+    auto fetch = [&](int it, float4(&ra)[kTcMaxBlocks], float4(&rb)[kTcMaxBlocks]) -> bool {
       const int s = it % kTcStages, use = it / kTcStages;
-      if (!tc_wait(hdr + s, use & 1, abort_flag, P.err, P.budget)) break;
+      if (!tc_wait(hdr + s, use & 1, abort_flag, P.err, P.budget)) return false;
+      const int* hd = reinterpret_cast<const int*>(stage0 + s * kTcStage);
+      const int nb = min(hd[0], kTcMaxBlocks);
+#pragma unroll
+      for (int t = 0; t < kTcMaxBlocks; t++) {
+        ra[t] = rb[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < nb) {
+          const int K = min(hd[5 + 4 * t] & 0xFFFF, 64);
+          const bool from_yhat = (hd[5 + 4 * t] >> 16) & 1;
+          const long long voff = *reinterpret_cast<const long long*>(hd + 24 + 2 * t);
+          if (8 * g < K && v < P.nv) {
+            const float* src = from_yhat ? P.yhat + voff * P.nv + (long long)v * P.kp + 8 * g
+                                         : P.x4 + voff * P.nv + (long long)v * 64 + 8 * g;
+            ra[t] = __ldg(reinterpret_cast<const float4*>(src));
+            rb[t] = __ldg(reinterpret_cast<const float4*>(src + 4));
+          }
+        }
+      }
+      return true;
+    };
+    auto build = [&](int it, const float4(&ra)[kTcMaxBlocks], const float4(&rb)[kTcMaxBlocks]) {
+      const int s = it % kTcStages;
       unsigned char* st = stage0 + s * kTcStage;
       const int* hd = reinterpret_cast<const int*>(st);
       const int nb = min(hd[0], kTcMaxBlocks);
       unsigned char* bt = st + kTcHeader + kStageMat;
       int boff = 0;
-      for (int t = 0; t < nb; t++) {
-        const int K = min(hd[5 + 4 * t] & 0xFFFF, 64);
-        const bool from_yhat = (hd[5 + 4 * t] >> 16) & 1;
-        const float sc = __int_as_float(hd[7 + 4 * t]) * sv;
-        const long long voff = *reinterpret_cast<const long long*>(hd + 24 + 2 * t);
-        if (8 * g < K) {
-          float z[8];
-          if (v < P.nv) {
-            const float* src = from_yhat ? P.yhat + voff * P.nv + (long long)v * P.kp + 8 * g
-                                         : P.x4 + voff * P.nv + (long long)v * 64 + 8 * g;
-            const float4 z0 = __ldg(reinterpret_cast<const float4*>(src));
-            const float4 z1 = __ldg(reinterpret_cast<const float4*>(src + 4));
-            z[0] = z0.x * sc, z[1] = z0.y * sc, z[2] = z0.z * sc, z[3] = z0.w * sc;
-            z[4] = z1.x * sc, z[5] = z1.y * sc, z[6] = z1.z * sc, z[7] = z1.w * sc;
-          } else {
 #pragma unroll
-            for (int e = 0; e < 8; e++) z[e] = 0.f;
-          }
+      for (int t = 0; t < kTcMaxBlocks; t++) {
+        if (t >= nb) break;
+        const int K = min(hd[5 + 4 * t] & 0xFFFF, 64);
+        const float sc = __int_as_float(hd[7 + 4 * t]) * sv;
+        if (8 * g < K) {
+          const float z[8] = {ra[t].x * sc, ra[t].y * sc, ra[t].z * sc, ra[t].w * sc,
+                              rb[t].x * sc, rb[t].y * sc, rb[t].z * sc, rb[t].w * sc};
           uint32_t hi[4], lo[4];
 #pragma unroll
           for (int e = 0; e < 4; e++) {
@@ -292,6 +348,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
       __syncwarp();
       if (lane == 0) mbar_arrive(bready + s);
+    };
+    if (n_items > 0 && fetch(0, za[0], zb[0])) {
+      for (int it = 0; it < n_items; it++) {
+        // the next item's header is written only after its stage was freed, which needs the
+        // MMAs of this stage's previous use, not this item: waiting for it here cannot deadlock
+        // as long as it + 1 < it + kTcStages
+        const bool more = it + 1 < n_items;
+        bool ok = true;
+        if (more) ok = (it & 1) ? fetch(it + 1, za[0], zb[0]) : fetch(it + 1, za[1], zb[1]);
+        if (it & 1) build(it, za[1], zb[1]);
+        else build(it, za[0], zb[0]);
+        if (!ok) break;
+      }
     }
   } else {
     // ---------------------------------------------------------------- epilogue
@@ -301,40 +370,62 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
 #pragma unroll
     for (int v = 0; v < kTcVec; v++) inv[v] = 1.0f / P.vscale[v];
     int r = 0;
-    for (int it = 0; it < n_items; it++) {
-      const StreamItem I = P.items[ib + it];
-      if (!(I.flags & kItemFlagLast)) continue;
-      const int b = r & 1;
-      if (!tc_wait(accfull + b, (r >> 1) & 1, abort_flag, P.err, P.budget)) break;
-      tc_fence_after();
-      uint32_t c[kTcN];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcN);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
-            "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15]),
-            "=r"(c[16]), "=r"(c[17]), "=r"(c[18]), "=r"(c[19]), "=r"(c[20]), "=r"(c[21]), "=r"(c[22]), "=r"(c[23]),
-            "=r"(c[24]), "=r"(c[25]), "=r"(c[26]), "=r"(c[27]), "=r"(c[28]), "=r"(c[29]), "=r"(c[30]), "=r"(c[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(accempty + b);
-      if (lane < 16) {
-        double* yr = P.y + I.row + 16 * q + lane;
-#pragma unroll
-        for (int v = 0; v < kTcVec; v++)
-          if (v < P.nv) yr[v * P.ldy] = (double)((__uint_as_float(c[2 * v]) + __uint_as_float(c[2 * v + 1])) * inv[v]);
+    bool ok = true;
+    for (int base = 0; base < n_items && ok; base += 32) {
+      // 32 items at a time: the rows that end in them, in order
+      int my_flags = 0, my_row = 0;
+      if (base + lane < n_items) {
+        const StreamItem& I = P.items[ib + base + lane];
+        my_flags = I.flags;
+        my_row = I.row;
       }
-      r++;
+      unsigned ends = __ballot_sync(0xFFFFFFFFu, (my_flags & kItemFlagLast) != 0);
+      for (; ends; ends &= ends - 1u) {
+        const int row_off = __shfl_sync(0xFFFFFFFFu, my_row, __ffs(ends) - 1);
+        const int b = r & 1;
+        if (!tc_wait(accfull + b, (r >> 1) & 1, abort_flag, P.err, P.budget)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        float sum[kTcN];
+#pragma unroll
+        for (int i = 0; i < kTcN; i++) sum[i] = 0.f;
+#pragma unroll
+        for (int a = 0; a < kTcAccs; a++) {
+          uint32_t c[kTcN];
+          const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((b * kTcAccs + a) * kTcN);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
+                "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15]),
+                "=r"(c[16]), "=r"(c[17]), "=r"(c[18]), "=r"(c[19]), "=r"(c[20]), "=r"(c[21]), "=r"(c[22]),
+                "=r"(c[23]), "=r"(c[24]), "=r"(c[25]), "=r"(c[26]), "=r"(c[27]), "=r"(c[28]), "=r"(c[29]),
+                "=r"(c[30]), "=r"(c[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int i = 0; i < kTcN; i++) sum[i] += __uint_as_float(c[i]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(accempty + b);
+        if (lane < 16) {
+          double* yr = P.y + row_off + 16 * q + lane;
+#pragma unroll
+          for (int v = 0; v < kTcVec; v++)
+            if (v < P.nv) yr[v * P.ldy] = (double)((sum[2 * v] + sum[2 * v + 1]) * inv[v]);
+        }
+        r++;
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
   }
 }
 
