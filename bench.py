@@ -35,6 +35,8 @@ WORKLOADS = {
     "2d_n1M": "2D exp(-r/0.1) covariance H^2 matvec, n=2^20 uniform points, m=64, k=16 (4x4 Chebyshev), eta=0.9, FP64",
     "2d_n4096": "2D exp(-r/0.1) covariance H^2 matvec, n=4096 uniform points, m=32, k=16, eta=0.9, FP64",
     "2d_n256k": "2D exp(-r/0.1) covariance H^2 matvec, n=2^18 uniform points, m=64, k=16, eta=0.9, FP64",
+    "3d_n512k": "3D exp(-r/0.2) covariance H^2 matvec, n=2^19 uniform points in the unit cube, m=64, k=64 (4x4x4 Chebyshev), "
+                "eta=0.9, FP64",
     "batch256": "256 independent 2D exp(-r/0.1) covariance H^2 matvecs, n log-uniform in [2^12, 2^17], m=32, k=16, "
                 "eta=0.9, nv in {1, 4, 16}, fp16 storage + f32 arithmetic, one graph-captured batched product",
 }
@@ -161,6 +163,7 @@ def main():
     ap.add_argument("--storage", default="fp64", choices=["fp64", "fp16", "bf16", "int16"],
                     help="storage form of the timed product (the extras always use fp64 and list the scaled forms)")
     ap.add_argument("--bases-fp32", action="store_true", help="scaled forms: keep U, V, E, F in FP32")
+    ap.add_argument("--no-batch", action="store_true", help="extras without the batched-workload line")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -299,7 +302,8 @@ def main():
         out["mixed"] = mixed_lines(h2, A, info, dev, stream, y_ref, x_np, args.steps, world, rank)
 
         # many independent matrices of uneven size in one batched, graph-captured product
-        out["batch"] = batch_line(h2, dev, args.steps, world, rank, hbm)
+        if not args.no_batch:
+            out["batch"] = batch_line(h2, dev, args.steps, world, rank, hbm)
 
         if rank == 0 and world == 1:
             sec, reps, cores = run_oracle_baseline(A, x_np)
@@ -315,7 +319,9 @@ def main():
         dist.destroy_process_group()
 
 
-MIXED_FORMS = [("int16", True), ("fp16", True), ("bf16", False)]
+# (storage, bases_fp32): int16 with FP32 bases meets 1e-4; fp16 / bf16 with 16-bit bases run the dense
+# phase on the tensor cores for passes of 8 or more vectors (64-point leaves)
+MIXED_FORMS = [("int16", True), ("fp16", True), ("fp16", False), ("bf16", False)]
 MIXED_NV = [1, 8, 32, 64]
 
 

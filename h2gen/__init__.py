@@ -210,6 +210,8 @@ CONFIGS = {
     "2d_n256k": dict(dim=2, n=1 << 18, m=64, p=4, eta=0.9, kernel="exp", ell=0.1, seed=4),
     # 3D, n=2^20, exp(-r/0.2), m=64, 4x4x4 Chebyshev (k=64), eta=0.9
     "3d_n1M": dict(dim=3, n=1 << 20, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=3),
+    # the same 3D workload at n=2^19 (its FP64 arrays, about 91 GB, fit the host memory of one GPU node)
+    "3d_n512k": dict(dim=3, n=1 << 19, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=3),
 }
 
 
