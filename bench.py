@@ -125,6 +125,12 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# DRAM bytes (read + write) of one dense-stream launch over its algorithmic bytes, from ncu captures of
+# the 2D n=2^18 workload (profiles/k_dense_stream_2d_n256k_fp64.md, profiles/k_dense_stream_m_2d_n256k_int16.md);
+# the traffic grows with the leaf count, so the ratio carries over to the n=2^20 launch
+TRAFFIC_RATIO = {("fp64", False): 3184277648 / 3178496000, ("int16", True): 809942016 / 805640544}
+
+
 def dense_kernel_bytes(info: dict, A, nv: int, storage: str = "fp64", bases_fp32: bool = False) -> int:
     """Algorithmic bytes of one dense + expansion launch: D and U once (plus one 4-byte scale per block
     in the scaled forms), x read once, y written once (8 bytes), the leaf yhat read once."""
@@ -239,9 +245,12 @@ def main():
     dense_ms = phase_ms["dense_expand"] / args.steps
     dbytes = dense_kernel_bytes(info, A, nv, args.storage, args.bases_fp32)
     achieved = dbytes / (dense_ms * 1e-3) / 1e9
-    roofline = {"kernel": "k_dense_expand", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+    kname = "k_dense_stream" if args.storage == "fp64" else "k_dense_stream_m"
+    roofline = {"kernel": kname + " (dense blocks + leaf expansion)", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": None, "bytes_per_launch": dbytes,
+                "traffic": (round(TRAFFIC_RATIO[(args.storage, args.bases_fp32)] * dbytes)
+                            if (args.storage, args.bases_fp32) in TRAFFIC_RATIO and nv == 1 else None),
+                "bytes_per_launch": dbytes,
                 "phase_share": {k: round(v / max(sum(phase_ms.values()), 1e-9), 4) for k, v in phase_ms.items()}}
 
     out = {"metric": METRIC, "value": round(gbs, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
