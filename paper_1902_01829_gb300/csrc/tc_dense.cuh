@@ -288,10 +288,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
     }
   } else if (warp < 6) {
     // ---------------------------------------------------------------- B-tile builders
-    // thread: vector v = tid / 8 (0 .. 15), K group g = tid % 8 (8 entries); it writes the
-    // 16-byte high and low rows of its vector for that K group. The loads of item it + 1
-    // are issued before item it is converted and stored (one item of look-ahead).
-    const int tid = threadIdx.x - 64, v = tid >> 3, g = tid & 7;
+    // thread: vector v (0 .. 15) and K group g (8 entries); it writes the 16-byte high and
+    // low rows of its vector for that K group. Lane l of builder warp w takes v = 4 w + (l & 3),
+    // g = l >> 2, and threads with odd g store the low row first: each quarter-warp's two
+    // stores then cover all eight 16-byte bank groups (rows 0 .. 7 of a core matrix), free of
+    // bank conflicts. The loads of item it + 1 are issued before item it is converted and
+    // stored (one item of look-ahead).
+    const int tid = threadIdx.x - 64, v = 4 * (tid >> 5) + (tid & 3), g = (tid >> 2) & 7;
     const float sv = P.vscale[v];
     float4 za[2][kTcMaxBlocks], zb[2][kTcMaxBlocks];
     auto fetch = [&](int it, float4(&ra)[kTcMaxBlocks], float4(&rb)[kTcMaxBlocks]) -> bool {
@@ -340,8 +343,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
           }
           // K-major tile: row n = 2v (+1), core (n / 8, g) at (n / 8) * K * 16 + g * 128, row n % 8 at 16 bytes
           unsigned char* dst = bt + boff + ((2 * v) >> 3) * K * 16 + g * 128 + ((2 * v) & 7) * 16;
-          *reinterpret_cast<uint4*>(dst) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(dst + 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          const uint4 wh = make_uint4(hi[0], hi[1], hi[2], hi[3]), wl = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          const bool low_first = g & 1;
+          *reinterpret_cast<uint4*>(dst + (low_first ? 16 : 0)) = low_first ? wl : wh;
+          *reinterpret_cast<uint4*>(dst + (low_first ? 0 : 16)) = low_first ? wh : wl;
         }
         boff += kTcN * K * 2;
       }
