@@ -61,6 +61,7 @@ struct MixedLaunch {
   long long budget = kWaitBudget;
   int k = 0;
   bool bases_fp32 = false;
+  bool small_rows = false;           // every leaf row has at most 32 points
   Profiler* prof = nullptr;          // profiler whose events mark the phases (or none)
 };
 

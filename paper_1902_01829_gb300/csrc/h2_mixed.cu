@@ -465,6 +465,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   L.err = h->err;
   L.k = k;
   L.bases_fp32 = M.bases_fp32;
+  L.small_rows = h->m_max <= 32;
   return H2_OK;
 }
 
@@ -627,6 +628,8 @@ h2_status batch_build(h2_batch_s* b) {
   L.err = err;
   L.k = h0->k;
   L.bases_fp32 = h0->mx.bases_fp32;
+  L.small_rows = true;
+  for (const h2_matrix_s* h : b->hs) L.small_rows = L.small_rows && h->m_max <= 32;
   L.prof = nullptr;
   b->n_items = (int64_t)items.size();
   return H2_OK;

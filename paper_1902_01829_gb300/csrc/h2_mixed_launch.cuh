@@ -9,12 +9,12 @@
 
 namespace h2i {
 
-template <int F, int NVB>
+template <int F, int NVB, int CW>
 cudaError_t set_mixed_smem() {
   static cudaError_t done = cudaErrorNotReady;
   if (done == cudaErrorNotReady)
-    done = cudaFuncSetAttribute(h2::k_dense_stream_m<F, NVB, h2::kMixedCW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                h2::mixed_smem_bytes(NVB, h2::kMixedCW));
+    done = cudaFuncSetAttribute(h2::k_dense_stream_m<F, NVB, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                h2::mixed_smem_bytes(NVB, CW));
   return done;
 }
 
@@ -62,10 +62,10 @@ void bucket_dispatch(const MixedLaunch& L, int phase, int b, cudaStream_t st) {
   }
 }
 
-template <int F, int NVB>
-h2_status dense_launch(const MixedLaunch& L, cudaStream_t st) {
+template <int F, int NVB, int CW>
+h2_status dense_launch_cw(const MixedLaunch& L, cudaStream_t st) {
   using namespace h2;
-  cudaError_t e = set_mixed_smem<F, NVB>();
+  cudaError_t e = set_mixed_smem<F, NVB, CW>();
   if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
   MixedStreamParams P{};
   P.items = L.items;
@@ -74,8 +74,19 @@ h2_status dense_launch(const MixedLaunch& L, cudaStream_t st) {
   P.mats = static_cast<const MatDesc*>(L.mats);
   P.err = L.err;
   P.budget = L.budget;
-  k_dense_stream_m<F, NVB, kMixedCW><<<L.grid, (kMixedCW + 1) * 32, mixed_smem_bytes(NVB, kMixedCW), st>>>(P);
+  k_dense_stream_m<F, NVB, CW><<<L.grid, (CW + 1) * 32, mixed_smem_bytes(NVB, CW), st>>>(P);
   return H2_OK;
+}
+
+// consumer warps of the dense stream: rows of at most 32 points give each warp little
+// arithmetic per item, and twice the warps hide more latency (measured: 163 -> 134 us on a
+// 2^17-point matrix with 32-point leaves); 64-point rows run faster with 8
+template <int F, int NVB>
+h2_status dense_launch(const MixedLaunch& L, cudaStream_t st) {
+  if constexpr (NVB <= 8) {
+    if (L.small_rows) return dense_launch_cw<F, NVB, 2 * h2::kMixedCW>(L, st);
+  }
+  return dense_launch_cw<F, NVB, h2::kMixedCW>(L, st);
 }
 
 // dense phase on the tensor cores: per-vector scales, then the persistent tcgen05 kernel

@@ -839,6 +839,7 @@ __device__ __forceinline__ void consume_item(const unsigned char* stage, const i
   constexpr int SETS = NV2 == 1 ? 4 : (NV2 == 2 ? 2 : 1);
   constexpr bool kScaleCodes = NV2 >= 4;  // scale the codes once instead of per-vector partial sums
   if (R <= 32) {
+    constexpr int HW = 2 * CW;  // half-warps
     const int r0 = 2 * (lane & 15), hw = warp * 2 + (lane >> 4);
     const bool even = (R & 1) == 0;
     int base = 0;
@@ -853,11 +854,11 @@ __device__ __forceinline__ void consume_item(const unsigned char* stage, const i
       const float* A32 = reinterpret_cast<const float*>(stage + kMixedHeader + moff);
       const float* X = reinterpret_cast<const float*>(stage + kMixedHeader + kStageMat + voff);
       const int G = (C + 3) >> 2;
-      int first = hw - (base & 15);
-      if (first < 0) first += 16;
+      int first = hw - (base % HW);
+      if (first < 0) first += HW;
       base += G;
       if (r0 >= R) continue;
-      for (int grp = first; grp < G; grp += 16) {
+      for (int grp = first; grp < G; grp += HW) {
         const int c = 4 * grp;
         float2 a[4];
 #pragma unroll
