@@ -349,6 +349,7 @@ def mixed_lines(h2, A, info64, dev, stream, y_ref, x_np, steps, world, rank):
         for nv in MIXED_NV:
             X = xw[:, :nv]
             Y = torch.empty((nv, A.n), dtype=torch.float64, device=dev).t()
+            tuned = M.tune(X, Y, stream=stream)  # launch parameters chosen by timing (h2_tune)
             for _ in range(3):
                 M.matvec(X, Y, stream=stream)
             M.check(stream)
@@ -363,7 +364,7 @@ def mixed_lines(h2, A, info64, dev, stream, y_ref, x_np, steps, world, rank):
             ms = e0.elapsed_time(e1) / k
             yy = Y[:, :min(nv, 2)].cpu().numpy()
             err = oracle.rel_l2(yy, ref2[:, :yy.shape[1]])
-            lines.append({"storage": form, "bases_fp32": bases, "nv": nv, "ms_per_step": round(ms, 4),
+            lines.append({"storage": form, "bases_fp32": bases, "nv": nv, "tuned": tuned, "ms_per_step": round(ms, 4),
                           "GBs": round(mb * world / (ms * 1e-3) / 1e9, 1),
                           "vectors_per_s": round(nv * world / (ms * 1e-3), 1),
                           "stored_bytes": mb, "rel_err_vs_fp64_oracle": err})
@@ -400,6 +401,9 @@ def batch_line(h2, dev, steps, world, rank, hbm, count=256, storage="fp16", time
     t_build = time.perf_counter() - t_build
     stored = sum(M.info()["paper_bytes"] for M in Ms)
     vecs = sum(nv for _, nv in spec)
+    t_tune = time.perf_counter()
+    tuned = B.tune(xs, ys)  # launch parameters chosen by timing (h2_batch_tune)
+    t_tune = time.perf_counter() - t_tune
     args = B.prepare(xs, ys)
     s = torch.cuda.Stream(dev)
     with torch.cuda.stream(s):
@@ -465,7 +469,7 @@ def batch_line(h2, dev, steps, world, rank, hbm, count=256, storage="fp16", time
             "matvecs_per_s": round(count * world / (ms * 1e-3), 1), "stored_bytes": stored,
             "l2": "batch (%.1f GB) >> 129 MB L2: no flush needed" % (stored / 1e9),
             "launches_per_step": info["launches_per_pass"], "tree_jobs": info["tree_jobs"],
-            "dense_items": info["dense_items"], "graph": True,
+            "dense_items": info["dense_items"], "graph": True, "tuned": tuned, "tune_s": round(t_tune, 2),
             "phase_ms": {key: round(v / 3, 4) for key, v in phase_ms.items()},
             "one_handle_at_a_time_ms": round(loop_ms, 4), "rel_err_sampled": errs,
             "build_s": round(t_build, 1)}

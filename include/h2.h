@@ -222,6 +222,22 @@ h2_status h2_profile_read(h2_handle h, double ms[H2_NPHASES], int64_t* launches)
 h2_status h2_matvec_static(const h2_desc* d, int64_t n_dense_blocks, int32_t nv, const double* x, int64_t ldx, double* y,
                            int64_t ldy, void* stream);
 
+/*
+ * Autotuning of the launch parameters of the scaled storage forms. Runs the
+ * product y = A^H x with each candidate configuration (one warm-up and three
+ * timed products, CUDA events on `stream`) and keeps the fastest for later
+ * calls on this handle:
+ *   dense consumer warps:   8 or 16 (16 only for passes of at most 8 vectors)
+ *   coupling row chunks:    about 64, 128 or 256 coupling blocks per warp
+ * x, y, ldx, ldy, nv as for h2_matvec; y holds the product on return. The call
+ * synchronizes `stream` (do not capture it in a graph). chosen[0] receives the
+ * consumer warps, chosen[1] the chunk size, chosen[2] 0. H2_FP64 handles have
+ * no options: chosen is all zero and nothing runs. Errors: H2_ERR_INVALID,
+ * H2_ERR_CUDA.
+ */
+h2_status h2_tune(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream,
+                  int32_t chosen[3]);
+
 /* Free all device memory of the handle (synchronizes the device first). NULL is a no-op. */
 h2_status h2_destroy(h2_handle h);
 
@@ -272,6 +288,18 @@ h2_status h2_batch_create(const h2_handle* hs, int32_t count, h2_batch* out);
  */
 h2_status h2_batch_matvec(h2_batch b, const int32_t* nv, const double* const* x, const int64_t* ldx,
                           double* const* y, const int64_t* ldy, void* stream);
+
+/*
+ * Autotuning of a batch: as h2_tune, over the candidates
+ *   dense consumer warps:   8 or 16 (16 only when no member takes more than 8 vectors)
+ *   coupling row chunks:    about 64, 128 or 256 coupling blocks per warp
+ *   tree jobs:              subtrees of 16, 32 or 64 leaves per CTA
+ * (one warm-up and two timed batched products each, arguments as for
+ * h2_batch_matvec). chosen[0] consumer warps, chosen[1] chunk size, chosen[2]
+ * leaves per tree CTA. Synchronizes `stream`.
+ */
+h2_status h2_batch_tune(h2_batch b, const int32_t* nv, const double* const* x, const int64_t* ldx,
+                        double* const* y, const int64_t* ldy, void* stream, int32_t chosen[3]);
 
 /* Synchronize `stream`, then report H2_ERR_TIMEOUT (and clear it) if a bounded
  * device wait of a batched product ran out since the last check. */

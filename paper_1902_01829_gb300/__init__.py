@@ -22,8 +22,9 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
 
 # every symbol include/h2.h declares
 EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
-           "h2_profile_read", "h2_matvec_static", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
-           "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy", "h2_last_error"]
+           "h2_profile_read", "h2_matvec_static", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
+           "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_tune", "h2_batch_destroy",
+           "h2_last_error"]
 PHASES = ["upsweep", "coupling", "downsweep", "dense_expand"]
 
 
@@ -65,10 +66,13 @@ def _load():
     lib.h2_batch_destroy.argtypes = [vp]
     lib.h2_batch_profile.argtypes = [vp, i32]
     lib.h2_batch_profile_read.argtypes = [vp, vp, vp]
+    lib.h2_tune.argtypes = [vp, i32, vp, i64, vp, i64, vp, vp]
+    lib.h2_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.h2_last_error.restype = ctypes.c_char_p
     for name in ("h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
                  "h2_profile_read", "h2_matvec_static", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
-                 "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy"):
+                 "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy",
+                 "h2_tune", "h2_batch_tune"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -158,6 +162,18 @@ class H2Matrix:
         Y = np.empty((self.n, nv), order="F") if y is None else y
         _check(_lib.h2_matvec_host(self._h, nv, _ptr(X), self.n, _ptr(Y), self.n, _stream_ptr(stream)))
         return Y[:, 0] if (vec and y is None) else Y
+
+    def tune(self, x, y, stream=None) -> dict:
+        """Choose the launch parameters by timing products with x, y (h2_tune); y holds A^H x on return."""
+        import torch
+        X = x.unsqueeze(1) if x.dim() == 1 else x
+        Y = y.unsqueeze(1) if y.dim() == 1 else y
+        assert X.stride(0) == 1 and Y.stride(0) == 1 and X.dtype == torch.float64 and Y.dtype == torch.float64
+        nv = X.shape[1]
+        ch = np.zeros(3, dtype=np.int32)
+        _check(_lib.h2_tune(self._h, nv, _ptr(X), X.stride(1) if nv > 1 else self.n, _ptr(Y),
+                            Y.stride(1) if nv > 1 else self.n, _stream_ptr(stream), _ptr(ch)))
+        return {"consumer_warps": int(ch[0]), "chunk_blocks": int(ch[1])}
 
     def info(self) -> dict:
         a = np.zeros(8, dtype=np.int64)
@@ -250,6 +266,13 @@ class H2Batch:
 
     def check(self, stream=None):
         _check(_lib.h2_batch_check(self._b, _stream_ptr(stream)))
+
+    def tune(self, xs, ys, stream=None) -> dict:
+        """Choose the batch's launch parameters by timing batched products (h2_batch_tune)."""
+        nv, xp, ldx, yp, ldy = self.prepare(xs, ys)
+        ch = np.zeros(3, dtype=np.int32)
+        _check(_lib.h2_batch_tune(self._b, _ptr(nv), xp, _ptr(ldx), yp, _ptr(ldy), _stream_ptr(stream), _ptr(ch)))
+        return {"consumer_warps": int(ch[0]), "chunk_blocks": int(ch[1]), "tree_leaves": int(ch[2])}
 
     def profile(self, enable: bool = True):
         """Record per-phase CUDA events in every batched product while enabled (h2_batch_profile)."""

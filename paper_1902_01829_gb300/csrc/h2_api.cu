@@ -608,6 +608,52 @@ h2_status h2_matvec_host(h2_handle h, int32_t nv, const double* x, int64_t ldx, 
   return H2_OK;
 }
 
+h2_status h2_tune(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream,
+                  int32_t chosen[3]) {
+  if (!h || !x || !y || !chosen) return fail(H2_ERR_INVALID, "NULL handle, vector or output");
+  if (nv < 1) return fail(H2_ERR_INVALID, "nv = %d < 1", nv);
+  if (ldx < h->n || ldy < h->n) return fail(H2_ERR_INVALID, "leading dimension below n");
+  chosen[0] = chosen[1] = chosen[2] = 0;
+  if (h->storage == H2_FP64) return H2_OK;  // the plain form has no launch options
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  // 16 dense consumer warps exist for passes of at most 8 vectors
+  const int ncw = std::min(nv, kPassVectors) <= 8 ? 2 : 1;
+  float best = 3.4e38f;
+  int best_opt = kDefaultChunkOpt, best_cw = h->mx.launch.cw;
+  h2_status s = H2_OK;
+  for (int c = 0; c < ncw && s == H2_OK; c++)
+    for (int opt = 0; opt < 3 && s == H2_OK; opt++) {
+      const int cw = c ? 2 * kDenseCW : kDenseCW;
+      if ((s = mixed_configure(h, opt, cw)) != H2_OK) break;
+      if ((s = matvec_device(h, nv, x, ldx, y, ldy, st)) != H2_OK) break;  // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3 && s == H2_OK; r++) s = matvec_device(h, nv, x, ldx, y, ldy, st);
+      cudaEventRecord(e1, st);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess) {
+        s = fail(H2_ERR_CUDA, "timing a launch configuration: %s", cudaGetErrorString(ce));
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        best_opt = opt;
+        best_cw = cw;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != H2_OK) return s;
+  if ((s = mixed_configure(h, best_opt, best_cw)) != H2_OK) return s;
+  chosen[0] = best_cw;
+  chosen[1] = kChunkOpts[best_opt];
+  return H2_OK;
+}
+
 h2_status h2_check(h2_handle h, void* stream) {
   if (!h) return fail(H2_ERR_INVALID, "NULL handle");
   CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));

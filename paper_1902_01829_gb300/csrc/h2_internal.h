@@ -61,7 +61,7 @@ struct MixedLaunch {
   long long budget = kWaitBudget;
   int k = 0;
   bool bases_fp32 = false;
-  bool small_rows = false;           // every leaf row has at most 32 points
+  int cw = 8;                        // consumer warps of the dense stream (8, or 16 for passes of <= 8 vectors)
   Profiler* prof = nullptr;          // profiler whose events mark the phases (or none)
 };
 
@@ -117,8 +117,18 @@ struct MixedData {
   std::vector<h2::StreamItem> items_host;  // the dense items (matrix index 0), kept for batches
   std::vector<int64_t> row_bytes;          // bytes each leaf row streams (load balance)
   std::vector<int64_t> row_item0;          // first item of each leaf row, [leaves + 1]
-  std::vector<int4> chunks_host;           // coupling row chunks (matrix index 0)
+  std::vector<int4> chunks_host;           // coupling row chunks (matrix index 0), current target
+  std::vector<int32_t> srow_host;          // S_rowptr (to cut chunks for another target)
+  int4* chunk_dev[3] = {nullptr, nullptr, nullptr};  // device chunk lists per target option
+  int64_t chunk_n[3] = {0, 0, 0};
 };
+
+// launch parameters the tuner chooses between (h2_tune, h2_batch_tune)
+constexpr int kChunkOpts[3] = {64, 128, 256};  // coupling blocks per warp chunk (target)
+constexpr int kTreeOpts[3] = {4, 5, 6};       // log2 of the leaves per tree CTA (batches)
+constexpr int kDefaultChunkOpt = 1, kDefaultTreeOpt = 2;
+constexpr int kDenseCW = 8;                   // dense-stream consumer warps (or twice as many)
+std::vector<int4> coupling_chunks(const int32_t* Srow, int64_t n_nodes, int64_t target);
 
 // vector-count buckets of the precision-form kernels: bucket b runs the
 // variant for up to kBucketNV[b] vectors and takes counts kBucketLo[b] ..
@@ -203,6 +213,8 @@ void profile_free(Profiler* p);
 h2_status mixed_build(h2_matrix_s* h, const h2_desc* d);
 // one product pass; buckets: bit b set when some matrix has a vector count in bucket b
 h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc = nullptr);
+// precision form: use coupling chunk target option `opt` and `cw` dense consumer warps
+h2_status mixed_configure(h2_matrix_s* h, int chunk_opt, int cw);
 // passes of at least this many vectors use the tensor-core dense phase (panel-layout handles)
 constexpr int kTcMinVectors = 8;
 h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st);
@@ -214,6 +226,11 @@ struct h2_batch_s {
   std::vector<h2_matrix_s*> hs;  // the member handles (not owned)
   int storage = 0;
   h2i::MixedLaunch launch;       // over the concatenated tables
+  int chunk_opt = h2i::kDefaultChunkOpt, tree_opt = h2i::kDefaultTreeOpt;
+  int4* chunk_dev[3] = {nullptr, nullptr, nullptr};
+  int64_t chunk_n[3] = {0, 0, 0};
+  int2* jobs_dev[3] = {nullptr, nullptr, nullptr};
+  int64_t jobs_n[3] = {0, 0, 0};
   h2i::Profiler prof;
   int64_t n_items = 0, device_bytes = 0;
   std::vector<void*> allocs;

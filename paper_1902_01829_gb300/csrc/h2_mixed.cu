@@ -117,24 +117,6 @@ __global__ void k_set_calls(h2::MatDesc* mats, CallChunk c) {
   }
 }
 
-// coupling row chunks of one matrix: consecutive rows, at most kChunkRows rows
-// and (unless one row alone has more) about kChunkBlocks coupling blocks each
-constexpr int64_t kChunkBlocks = 64;
-std::vector<int4> coupling_chunks(const int32_t* Srow, int64_t n_nodes) {
-  std::vector<int4> out;
-  for (int64_t r = 0; r < n_nodes;) {
-    const int64_t r0 = r;
-    int64_t blocks = 0;
-    while (r < n_nodes && r - r0 < h2::kChunkRows &&
-           (r == r0 || blocks + (Srow[r + 1] - Srow[r]) <= kChunkBlocks)) {
-      blocks += Srow[r + 1] - Srow[r];
-      r++;
-    }
-    out.push_back(make_int4(0, (int)r0, (int)(r - r0), 0));
-  }
-  return out;
-}
-
 // static fields of a handle's matrix descriptor; row0 = its first row in the coupling row space
 h2::MatDesc fill_desc(const h2_matrix_s* h, int tree_L) {
   const MixedData& M = h->mx;
@@ -188,7 +170,42 @@ h2_status set_calls(h2::MatDesc* mats, int64_t count, const int* nv, const doubl
 
 }  // namespace
 
+static_assert(h2i::kDenseCW == h2::kMixedCW, "dense-stream consumer warps");
+
 namespace h2i {
+
+// coupling row chunks of one matrix: consecutive rows, at most kChunkRows rows
+// and (unless one row alone has more) about `target` coupling blocks each
+std::vector<int4> coupling_chunks(const int32_t* Srow, int64_t n_nodes, int64_t target) {
+  std::vector<int4> out;
+  for (int64_t r = 0; r < n_nodes;) {
+    const int64_t r0 = r;
+    int64_t blocks = 0;
+    while (r < n_nodes && r - r0 < h2::kChunkRows && (r == r0 || blocks + (Srow[r + 1] - Srow[r]) <= target)) {
+      blocks += Srow[r + 1] - Srow[r];
+      r++;
+    }
+    out.push_back(make_int4(0, (int)r0, (int)(r - r0), 0));
+  }
+  return out;
+}
+
+h2_status mixed_configure(h2_matrix_s* h, int chunk_opt, int cw) {
+  MixedData& M = h->mx;
+  if (chunk_opt < 0 || chunk_opt > 2 || (cw != h2::kMixedCW && cw != 2 * h2::kMixedCW))
+    return h2_fail(H2_ERR_INVALID, "internal: launch configuration out of range");
+  if (!M.chunk_dev[chunk_opt]) {
+    const std::vector<int4> c = coupling_chunks(M.srow_host.data(), h->n_nodes, kChunkOpts[chunk_opt]);
+    h2_status st = upload(h, &M.chunk_dev[chunk_opt], c.data(), (int64_t)c.size());
+    if (st != H2_OK) return st;
+    M.chunk_n[chunk_opt] = (int64_t)c.size();
+  }
+  M.chunks_host = coupling_chunks(M.srow_host.data(), h->n_nodes, kChunkOpts[chunk_opt]);
+  M.launch.chunks = M.chunk_dev[chunk_opt];
+  M.launch.nchunks = M.chunk_n[chunk_opt];
+  M.launch.cw = cw;
+  return H2_OK;
+}
 
 h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   MixedData& M = h->mx;
@@ -453,11 +470,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   if ((st = upload(h, &dj, jobs.data(), (int64_t)jobs.size())) != H2_OK) return st;
   L.jobs = dj;
   L.njobs = (int64_t)jobs.size();
-  M.chunks_host = coupling_chunks(d->S_rowptr, nodes);
-  int4* dc = nullptr;
-  if ((st = upload(h, &dc, M.chunks_host.data(), (int64_t)M.chunks_host.size())) != H2_OK) return st;
-  L.chunks = dc;
-  L.nchunks = (int64_t)M.chunks_host.size();
+  M.srow_host.assign(d->S_rowptr, d->S_rowptr + nodes + 1);
   L.items = M.dense_items.items;
   L.cta_begin = M.dense_items.cta_begin;
   L.blk = M.dblk;
@@ -465,8 +478,9 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   L.err = h->err;
   L.k = k;
   L.bases_fp32 = M.bases_fp32;
-  L.small_rows = h->m_max <= 32;
-  return H2_OK;
+  // defaults (h2_tune may choose others): 16 dense consumer warps for leaves of at most 32 points
+  // (little arithmetic per item, more warps hide more latency), 128 coupling blocks per chunk
+  return mixed_configure(h, kDefaultChunkOpt, h->m_max <= 32 ? 2 * h2::kMixedCW : h2::kMixedCW);
 }
 
 h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {
@@ -545,36 +559,70 @@ void batch_free(h2_batch_s* b) {
   profile_free(&b->prof);
 }
 
+// the batch's coupling chunks, tree jobs and member descriptors for launch options
+// (chunk target kChunkOpts[chunk_opt], 2^kTreeOpts[tree_opt] leaves per tree CTA)
+h2_status batch_configure(h2_batch_s* b, int chunk_opt, int tree_opt, int cw) {
+  const int64_t count = (int64_t)b->hs.size();
+  MixedLaunch& L = b->launch;
+  h2_status st;
+  if (chunk_opt < 0 || chunk_opt > 2 || tree_opt < 0 || tree_opt > 2 ||
+      (cw != h2::kMixedCW && cw != 2 * h2::kMixedCW))
+    return h2_fail(H2_ERR_INVALID, "internal: launch configuration out of range");
+  if (!b->chunk_dev[chunk_opt]) {
+    std::vector<int4> chunks;
+    for (int64_t i = 0; i < count; i++) {
+      const h2_matrix_s* h = b->hs[(size_t)i];
+      for (int4 c : coupling_chunks(h->mx.srow_host.data(), h->n_nodes, kChunkOpts[chunk_opt])) {
+        c.x = (int)i;
+        chunks.push_back(c);
+      }
+    }
+    if ((st = balloc(b, &b->chunk_dev[chunk_opt], (int64_t)chunks.size(), chunks.data())) != H2_OK) return st;
+    b->chunk_n[chunk_opt] = (int64_t)chunks.size();
+  }
+  const int T = kTreeOpts[tree_opt];
+  if (!b->jobs_dev[tree_opt]) {
+    std::vector<int2> jobs;
+    for (int64_t i = 0; i < count; i++) {
+      const int Li = std::max(0, b->hs[(size_t)i]->q - T);
+      for (int64_t t = 0; t < ((int64_t)1 << Li); t++) jobs.push_back(make_int2((int)i, (int)t));
+    }
+    if ((int64_t)jobs.size() >= INT32_MAX) return h2_fail(H2_ERR_UNSUPPORTED, "batch too large: %lld tree jobs", (long long)jobs.size());
+    if ((st = balloc(b, &b->jobs_dev[tree_opt], (int64_t)jobs.size(), jobs.data())) != H2_OK) return st;
+    b->jobs_n[tree_opt] = (int64_t)jobs.size();
+  }
+  if (!L.mats || tree_opt != b->tree_opt) {  // the descriptors carry each member's subtree level
+    std::vector<h2::MatDesc> descs((size_t)count);
+    for (int64_t i = 0; i < count; i++) descs[(size_t)i] = fill_desc(b->hs[(size_t)i], std::max(0, b->hs[(size_t)i]->q - T));
+    if (!L.mats) {
+      h2::MatDesc* md = nullptr;
+      if ((st = balloc(b, &md, count, descs.data())) != H2_OK) return st;
+      L.mats = md;
+    } else {
+      CUDA_TRY(cudaMemcpy(L.mats, descs.data(), (size_t)count * sizeof(h2::MatDesc), cudaMemcpyHostToDevice));
+    }
+  }
+  L.chunks = b->chunk_dev[chunk_opt];
+  L.nchunks = b->chunk_n[chunk_opt];
+  L.jobs = b->jobs_dev[tree_opt];
+  L.njobs = b->jobs_n[tree_opt];
+  L.cw = cw;
+  b->chunk_opt = chunk_opt;
+  b->tree_opt = tree_opt;
+  return H2_OK;
+}
+
 h2_status batch_build(h2_batch_s* b) {
   const int64_t count = (int64_t)b->hs.size();
   const h2_matrix_s* h0 = b->hs[0];
   MixedLaunch& L = b->launch;
   h2_status st;
-  // subtree level per matrix: at most 64 leaves per tree CTA, fewer while the
-  // whole batch has under four CTAs per SM
-  auto jobs_for = [&](int T) {
-    int64_t s = 0;
-    for (const h2_matrix_s* h : b->hs) s += (int64_t)1 << std::max(0, h->q - T);
-    return s;
-  };
-  int T = 6;
-  while (T > 0 && jobs_for(T) < 4 * (int64_t)h0->grid) T--;
-  std::vector<h2::MatDesc> descs((size_t)count);
-  std::vector<int2> jobs;
-  std::vector<int4> chunks;
   std::vector<h2::StreamItem> items;
   std::vector<int64_t> row_bytes, row_item0;
   int64_t blk0 = 0;
   for (int64_t i = 0; i < count; i++) {
     const h2_matrix_s* h = b->hs[(size_t)i];
     const MixedData& M = h->mx;
-    const int Li = std::max(0, h->q - T);
-    descs[(size_t)i] = fill_desc(h, Li);
-    for (int64_t t = 0; t < ((int64_t)1 << Li); t++) jobs.push_back(make_int2((int)i, (int)t));
-    for (int4 c : M.chunks_host) {
-      c.x = (int)i;
-      chunks.push_back(c);
-    }
     const int64_t item0 = (int64_t)items.size();
     for (h2::StreamItem it : M.items_host) {
       it.v_off += blk0;
@@ -588,9 +636,8 @@ h2_status batch_build(h2_batch_s* b) {
     blk0 += M.nblk;
   }
   row_item0.push_back((int64_t)items.size());
-  if ((int64_t)items.size() >= INT32_MAX || (int64_t)jobs.size() >= INT32_MAX)
-    return h2_fail(H2_ERR_UNSUPPORTED, "batch too large: %lld dense items, %lld tree jobs", (long long)items.size(),
-                   (long long)jobs.size());
+  if ((int64_t)items.size() >= INT32_MAX)
+    return h2_fail(H2_ERR_UNSUPPORTED, "batch too large: %lld dense items", (long long)items.size());
   const std::vector<int> begin = balance(row_bytes, row_item0, h0->grid);
   for (size_t c = 0; c + 1 < begin.size(); c++)
     if (begin[c] > begin[c + 1]) return h2_fail(H2_ERR_INVALID, "internal: item ranges not monotone");
@@ -598,12 +645,6 @@ h2_status batch_build(h2_batch_s* b) {
     if (it.v_off < 0 || it.v_off + ((it.shape >> 8) & 0xFF) > blk0)
       return h2_fail(H2_ERR_INVALID, "internal: batched work item outside the block records");
 
-  h2::MatDesc* md = nullptr;
-  if ((st = balloc(b, &md, count, descs.data())) != H2_OK) return st;
-  int2* dj = nullptr;
-  if ((st = balloc(b, &dj, (int64_t)jobs.size(), jobs.data())) != H2_OK) return st;
-  int4* dc = nullptr;
-  if ((st = balloc(b, &dc, (int64_t)chunks.size(), chunks.data())) != H2_OK) return st;
   h2::StreamItem* di = nullptr;
   if ((st = balloc(b, &di, (int64_t)items.size(), items.data())) != H2_OK) return st;
   int* db = nullptr;
@@ -616,11 +657,6 @@ h2_status batch_build(h2_batch_s* b) {
   int* err = nullptr;
   if ((st = balloc(b, &err, 1)) != H2_OK) return st;
   CUDA_TRY(cudaMemset(err, 0, sizeof(int)));
-  L.mats = md;
-  L.jobs = dj;
-  L.njobs = (int64_t)jobs.size();
-  L.chunks = dc;
-  L.nchunks = (int64_t)chunks.size();
   L.items = di;
   L.cta_begin = db;
   L.blk = blk;
@@ -628,11 +664,22 @@ h2_status batch_build(h2_batch_s* b) {
   L.err = err;
   L.k = h0->k;
   L.bases_fp32 = h0->mx.bases_fp32;
-  L.small_rows = true;
-  for (const h2_matrix_s* h : b->hs) L.small_rows = L.small_rows && h->m_max <= 32;
   L.prof = nullptr;
   b->n_items = (int64_t)items.size();
-  return H2_OK;
+  // defaults (h2_batch_tune may choose others): at most 64 leaves per tree CTA, fewer while the
+  // batch has under four tree CTAs per SM; 128 coupling blocks per chunk; 16 dense consumer warps
+  // when every member's leaves hold at most 32 points
+  int tree_opt = kDefaultTreeOpt;
+  auto jobs_for = [&](int T) {
+    int64_t n = 0;
+    for (const h2_matrix_s* h : b->hs) n += (int64_t)1 << std::max(0, h->q - T);
+    return n;
+  };
+  while (tree_opt > 0 && jobs_for(kTreeOpts[tree_opt]) < 4 * (int64_t)h0->grid) tree_opt--;
+  bool small = true;
+  for (const h2_matrix_s* h : b->hs) small = small && h->m_max <= 32;
+  b->tree_opt = -1;
+  return batch_configure(b, kDefaultChunkOpt, tree_opt, small ? 2 * h2::kMixedCW : h2::kMixedCW);
 }
 
 }  // namespace
@@ -721,6 +768,54 @@ h2_status h2_batch_matvec(h2_batch b, const int32_t* nv, const double* const* x,
     s = mixed_launch(b->storage, L, buckets, st);
     if (s != H2_OK) return s;
   }
+  return H2_OK;
+}
+
+h2_status h2_batch_tune(h2_batch b, const int32_t* nv, const double* const* x, const int64_t* ldx, double* const* y,
+                        const int64_t* ldy, void* stream, int32_t chosen[3]) {
+  if (!b || !chosen) return h2_fail(H2_ERR_INVALID, "NULL batch or output");
+  chosen[0] = chosen[1] = chosen[2] = 0;
+  const int64_t count = (int64_t)b->hs.size();
+  int nvmax = 0;
+  for (int64_t i = 0; nv && i < count; i++) nvmax = std::max(nvmax, nv[i]);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  const int ncw = std::min(nvmax, kPassVectors) <= 8 ? 2 : 1;  // 16 dense consumer warps: passes of <= 8 vectors
+  float best = 3.4e38f;
+  int best_c = b->chunk_opt, best_t = b->tree_opt, best_cw = b->launch.cw;
+  h2_status s = H2_OK;
+  for (int c = 0; c < ncw && s == H2_OK; c++)
+    for (int co = 0; co < 3 && s == H2_OK; co++)
+      for (int to = 0; to < 3 && s == H2_OK; to++) {
+        const int cw = c ? 2 * h2::kMixedCW : h2::kMixedCW;
+        if ((s = batch_configure(b, co, to, cw)) != H2_OK) break;
+        if ((s = h2_batch_matvec(b, nv, x, ldx, y, ldy, stream)) != H2_OK) break;  // warm-up (validates)
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 2 && s == H2_OK; r++) s = h2_batch_matvec(b, nv, x, ldx, y, ldy, stream);
+        cudaEventRecord(e1, st);
+        cudaError_t ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) {
+          s = h2_fail(H2_ERR_CUDA, "timing a launch configuration: %s", cudaGetErrorString(ce));
+          break;
+        }
+        if (ms < best) {
+          best = ms;
+          best_c = co;
+          best_t = to;
+          best_cw = cw;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != H2_OK) return s;
+  if ((s = batch_configure(b, best_c, best_t, best_cw)) != H2_OK) return s;
+  chosen[0] = best_cw;
+  chosen[1] = kChunkOpts[best_c];
+  chosen[2] = 1 << kTreeOpts[best_t];
   return H2_OK;
 }
 

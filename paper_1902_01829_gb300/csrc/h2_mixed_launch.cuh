@@ -84,7 +84,7 @@ h2_status dense_launch_cw(const MixedLaunch& L, cudaStream_t st) {
 template <int F, int NVB>
 h2_status dense_launch(const MixedLaunch& L, cudaStream_t st) {
   if constexpr (NVB <= 8) {
-    if (L.small_rows) return dense_launch_cw<F, NVB, 2 * h2::kMixedCW>(L, st);
+    if (L.cw == 2 * h2::kMixedCW) return dense_launch_cw<F, NVB, 2 * h2::kMixedCW>(L, st);
   }
   return dense_launch_cw<F, NVB, h2::kMixedCW>(L, st);
 }

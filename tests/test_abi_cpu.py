@@ -142,3 +142,5 @@ def test_batch_entry_points_reject_null_arguments(h2):
     assert lib.h2_batch_profile(None, 1) == h2.H2_ERR_INVALID
     assert lib.h2_batch_profile_read(None, None, None) == h2.H2_ERR_INVALID
     assert lib.h2_batch_destroy(None) == h2.H2_OK
+    assert lib.h2_batch_tune(None, None, None, None, None, None, None, None) == h2.H2_ERR_INVALID
+    assert lib.h2_tune(None, 1, None, 1, None, 1, None, None) == h2.H2_ERR_INVALID

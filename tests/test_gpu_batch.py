@@ -200,3 +200,19 @@ def test_full_batch_sampled_members(h2):
     B.close()
     for M in Ms:
         M.close()
+
+
+def test_batch_tune_chooses_a_candidate_and_keeps_the_products(h2, members):
+    Ms = [h2.H2Matrix.from_generator(A, storage="fp16") for A, _ in members]
+    B = h2.H2Batch(Ms)
+    xs_np = [h2gen.vectors(990 + i, A.n, max(nv, 1)) for i, (A, nv) in enumerate(members)]
+    xs = [to_dev(x) if nv else None for x, (_, nv) in zip(xs_np, members)]
+    ys = [nan_like(A.n, max(nv, 1)) for A, nv in members]
+    chosen = B.tune(xs, ys)
+    assert chosen["consumer_warps"] in (8, 16) and chosen["chunk_blocks"] in (64, 128, 256)
+    assert chosen["tree_leaves"] in (16, 32, 64)
+    ys = [nan_like(A.n, max(nv, 1)) for A, nv in members]
+    B.matvec(xs, ys)
+    B.check()
+    _check_members(members, xs_np, ys, "fp16", False)
+    B.close()

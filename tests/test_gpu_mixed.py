@@ -156,3 +156,21 @@ def test_tensor_core_pass_scales_large_vectors(h2, panel2d):
     y = run(h2, A, "fp16", x)
     ref = oracle.matvec(A, x, **quant.dequantized_arrays(A, "fp16"))
     assert oracle.rel_l2(y, ref) <= TOL_ACC
+
+
+def test_tune_chooses_a_candidate_and_keeps_the_product(h2, c1):
+    x = h2gen.vectors(670, c1.n, 2)
+    M = h2.H2Matrix.from_generator(c1, storage="fp16")
+    X = to_dev(x)
+    Y = torch.empty_like(X)
+    chosen = M.tune(X, Y)
+    assert chosen["consumer_warps"] in (8, 16) and chosen["chunk_blocks"] in (64, 128, 256)
+    ref = oracle.matvec(c1, x, **quant.dequantized_arrays(c1, "fp16"))
+    assert oracle.rel_l2(Y.cpu().numpy(), ref) <= TOL_ACC  # the tuning products themselves
+    y = M.matvec(X)
+    M.check()
+    assert oracle.rel_l2(y.cpu().numpy(), ref) <= TOL_ACC  # with the chosen configuration
+    M.close()
+    F = h2.H2Matrix.from_generator(c1, storage="fp64")
+    assert F.tune(X, Y) == {"consumer_warps": 0, "chunk_blocks": 0}  # no options in the plain form
+    F.close()
