@@ -85,14 +85,16 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
+            import tempfile
+
+            fd, self.path = tempfile.mkstemp(prefix="h2_clocks_", suffix=".csv")
+            self.f = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -116,6 +118,10 @@ class ClockSampler:
                 parts = [p.strip() for p in ln.split(",")]
                 if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
                     rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         sm = [float(r[1]) for r in rows]
@@ -125,9 +131,9 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-# DRAM bytes (read + write) of one dense-stream launch over its algorithmic bytes, from ncu captures of
-# the 2D n=2^18 workload (profiles/k_dense_stream_2d_n256k_fp64.md, profiles/k_dense_stream_m_2d_n256k_int16.md);
-# the traffic grows with the leaf count, so the ratio carries over to the n=2^20 launch
+# DRAM bytes (read + write) of one dense-stream launch over its algorithmic bytes, from full ncu captures
+# of the 2D n=2^18 workload (FP64, and int16 codes with FP32 bases); the traffic grows with the leaf
+# count, so the ratio carries over to the n=2^20 launch
 TRAFFIC_RATIO = {("fp64", False): 3184277648 / 3178496000, ("int16", True): 809942016 / 805640544}
 
 
@@ -160,7 +166,7 @@ def run_oracle_baseline(A, x, budget_s: float = 12.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="h2", choices=["h2", "reference"])
     ap.add_argument("--workload", default="2d_n1M", choices=sorted(WORKLOADS))

@@ -23,7 +23,7 @@
  *   D        block-sparse rows over the leaves: D_rowptr[2^q+1], D_colidx =
  *            leaf index, D_val + D_valoff[b]: size_i x size_j, D[a,b] = K(x_a,x_b).
  *
- * Readings of points the paper leaves open (each listed in the design doc):
+ * Readings of points the paper leaves open:
  *   split    longest side of the tight bounding box; left child gets
  *            ceil(s/2) points ordered by (coordinate, original index), so all
  *            leaves sit on level q = ceil(log2(n/m)) with size <= m.
