@@ -599,7 +599,9 @@ template <int F, int RPL, int NVB>
 __global__ void __launch_bounds__(128) k_coupling_m_generic(const MatDesc* __restrict__ mats,
                                                            const int4* __restrict__ chunks, int64_t nchunks, int nvlo,
                                                            int nvhi) {
+  __shared__ __align__(16) float wstage[4][NVB * 64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* wbuf = wstage[warp];
   const int64_t cidx = (int64_t)blockIdx.x * 4 + warp;
   if (cidx >= nchunks) return;
   const int4 ch = __ldg(chunks + cidx);
@@ -623,9 +625,11 @@ __global__ void __launch_bounds__(128) k_coupling_m_generic(const MatDesc* __res
     for (int rr = 0; rr < RPL; rr++)
 #pragma unroll
       for (int v = 0; v < NVB; v++) acc[rr][v] = 0.f;
-    for (int32_t b = b0; b < b1; b++)
-      warp_mv_m<F, RPL, NVB>(S + (int64_t)b * kk8, sscale[b], k, k, LR, xhat + (int64_t)Scol[b] * nv * kp, kp, nv, acc,
-                             lane);
+    for (int32_t b = b0; b < b1; b++) {  // the column node's vectors staged in shared memory
+      stage_vectors<false>(wbuf, xhat + (int64_t)Scol[b] * nv * kp, nv * kp, lane);
+      warp_mv_m<F, RPL, NVB>(S + (int64_t)b * kk8, sscale[b], k, k, LR, wbuf, kp, nv, acc, lane);
+      __syncwarp();
+    }
     group_reduce_m(acc, LR);
     store_node_m<RPL, NVB, false>(yhat + (int64_t)(row0 + r) * nv * kp, k, kp, LR, nv, acc, lane);
   }
