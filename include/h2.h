@@ -229,11 +229,13 @@ h2_status h2_matvec_static(const h2_desc* d, int64_t n_dense_blocks, int32_t nv,
  * calls on this handle:
  *   dense consumer warps:   8 or 16 (16 only for passes of at most 8 vectors)
  *   coupling row chunks:    about 64, 128 or 256 coupling blocks per warp
+ *   tree jobs:              subtrees at the default level (2^L >= twice the SMs)
+ *                           or one or two levels higher (fewer, larger subtrees)
  * x, y, ldx, ldy, nv as for h2_matvec; y holds the product on return. The call
  * synchronizes `stream` (do not capture it in a graph). chosen[0] receives the
- * consumer warps, chosen[1] the chunk size, chosen[2] 0. H2_FP64 handles have
- * no options: chosen is all zero and nothing runs. Errors: H2_ERR_INVALID,
- * H2_ERR_CUDA.
+ * consumer warps, chosen[1] the chunk size, chosen[2] the leaves per tree CTA.
+ * H2_FP64 handles have no options: chosen is all zero and nothing runs.
+ * Errors: H2_ERR_INVALID, H2_ERR_CUDA.
  */
 h2_status h2_tune(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream,
                   int32_t chosen[3]);

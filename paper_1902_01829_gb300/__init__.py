@@ -173,7 +173,7 @@ class H2Matrix:
         ch = np.zeros(3, dtype=np.int32)
         _check(_lib.h2_tune(self._h, nv, _ptr(X), X.stride(1) if nv > 1 else self.n, _ptr(Y),
                             Y.stride(1) if nv > 1 else self.n, _stream_ptr(stream), _ptr(ch)))
-        return {"consumer_warps": int(ch[0]), "chunk_blocks": int(ch[1])}
+        return {"consumer_warps": int(ch[0]), "chunk_blocks": int(ch[1]), "tree_leaves": int(ch[2])}
 
     def info(self) -> dict:
         a = np.zeros(8, dtype=np.int64)

@@ -622,12 +622,14 @@ h2_status h2_tune(h2_handle h, int32_t nv, const double* x, int64_t ldx, double*
   // 16 dense consumer warps exist for passes of at most 8 vectors
   const int ncw = std::min(nv, kPassVectors) <= 8 ? 2 : 1;
   float best = 3.4e38f;
-  int best_opt = kDefaultChunkOpt, best_cw = h->mx.launch.cw;
+  int best_opt = kDefaultChunkOpt, best_cw = h->mx.launch.cw, best_tree = 0;
   h2_status s = H2_OK;
+  const int ntree = std::min(3, h->tree_L + 1);  // subtree level: default, one or two levels higher
   for (int c = 0; c < ncw && s == H2_OK; c++)
-    for (int opt = 0; opt < 3 && s == H2_OK; opt++) {
+    for (int opt = 0; opt < 3 && s == H2_OK; opt++)
+      for (int tr = 0; tr < ntree && s == H2_OK; tr++) {
       const int cw = c ? 2 * kDenseCW : kDenseCW;
-      if ((s = mixed_configure(h, opt, cw)) != H2_OK) break;
+      if ((s = mixed_configure(h, opt, cw, tr)) != H2_OK) break;
       if ((s = matvec_device(h, nv, x, ldx, y, ldy, st)) != H2_OK) break;  // warm-up
       cudaEventRecord(e0, st);
       for (int r = 0; r < 3 && s == H2_OK; r++) s = matvec_device(h, nv, x, ldx, y, ldy, st);
@@ -643,14 +645,16 @@ h2_status h2_tune(h2_handle h, int32_t nv, const double* x, int64_t ldx, double*
         best = ms;
         best_opt = opt;
         best_cw = cw;
+        best_tree = tr;
       }
-    }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != H2_OK) return s;
-  if ((s = mixed_configure(h, best_opt, best_cw)) != H2_OK) return s;
+  if ((s = mixed_configure(h, best_opt, best_cw, best_tree)) != H2_OK) return s;
   chosen[0] = best_cw;
   chosen[1] = kChunkOpts[best_opt];
+  chosen[2] = 1 << (h->q - std::max(0, h->tree_L - best_tree));  // leaves per tree CTA
   return H2_OK;
 }
 

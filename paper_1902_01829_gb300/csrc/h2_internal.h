@@ -121,6 +121,8 @@ struct MixedData {
   std::vector<int32_t> srow_host;          // S_rowptr (to cut chunks for another target)
   int4* chunk_dev[3] = {nullptr, nullptr, nullptr};  // device chunk lists per target option
   int64_t chunk_n[3] = {0, 0, 0};
+  int2* jobs_dev[3] = {nullptr, nullptr, nullptr};    // tree jobs per subtree-level option
+  int tree_opt = -1;                                  // subtree level L = default - tree_opt
 };
 
 // launch parameters the tuner chooses between (h2_tune, h2_batch_tune)
@@ -213,8 +215,9 @@ void profile_free(Profiler* p);
 h2_status mixed_build(h2_matrix_s* h, const h2_desc* d);
 // one product pass; buckets: bit b set when some matrix has a vector count in bucket b
 h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc = nullptr);
-// precision form: use coupling chunk target option `opt` and `cw` dense consumer warps
-h2_status mixed_configure(h2_matrix_s* h, int chunk_opt, int cw);
+// precision form: use coupling chunk target option `chunk_opt`, `cw` dense consumer warps and
+// tree subtrees at level (default level - tree_opt)
+h2_status mixed_configure(h2_matrix_s* h, int chunk_opt, int cw, int tree_opt);
 // passes of at least this many vectors use the tensor-core dense phase (panel-layout handles)
 constexpr int kTcMinVectors = 8;
 h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st);

@@ -190,10 +190,32 @@ std::vector<int4> coupling_chunks(const int32_t* Srow, int64_t n_nodes, int64_t 
   return out;
 }
 
-h2_status mixed_configure(h2_matrix_s* h, int chunk_opt, int cw) {
+h2_status mixed_configure(h2_matrix_s* h, int chunk_opt, int cw, int tree_opt) {
   MixedData& M = h->mx;
-  if (chunk_opt < 0 || chunk_opt > 2 || (cw != h2::kMixedCW && cw != 2 * h2::kMixedCW))
+  if (chunk_opt < 0 || chunk_opt > 2 || tree_opt < 0 || tree_opt > 2 ||
+      (cw != h2::kMixedCW && cw != 2 * h2::kMixedCW))
     return h2_fail(H2_ERR_INVALID, "internal: launch configuration out of range");
+  if (tree_opt != M.tree_opt) {  // subtree level of the tree jobs (in the descriptor and the job list)
+    const int L = std::max(0, h->tree_L - tree_opt);
+    if (!M.jobs_dev[tree_opt]) {
+      std::vector<int2> jobs((size_t)1 << L);
+      for (size_t t = 0; t < jobs.size(); t++) jobs[t] = make_int2(0, (int)t);
+      h2_status st = upload(h, &M.jobs_dev[tree_opt], jobs.data(), (int64_t)jobs.size());
+      if (st != H2_OK) return st;
+    }
+    const h2::MatDesc D = fill_desc(h, L);
+    if (!M.launch.mats) {
+      h2::MatDesc* md = nullptr;
+      h2_status st = upload(h, &md, &D, 1);
+      if (st != H2_OK) return st;
+      M.launch.mats = md;
+    } else {
+      CUDA_TRY(cudaMemcpy(M.launch.mats, &D, sizeof(D), cudaMemcpyHostToDevice));
+    }
+    M.launch.jobs = M.jobs_dev[tree_opt];
+    M.launch.njobs = (int64_t)1 << L;
+    M.tree_opt = tree_opt;
+  }
   if (!M.chunk_dev[chunk_opt]) {
     const std::vector<int4> c = coupling_chunks(M.srow_host.data(), h->n_nodes, kChunkOpts[chunk_opt]);
     h2_status st = upload(h, &M.chunk_dev[chunk_opt], c.data(), (int64_t)c.size());
@@ -460,16 +482,6 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
 
   // tables of the table-driven kernels: this matrix alone
   MixedLaunch& L = M.launch;
-  const h2::MatDesc D = fill_desc(h, h->tree_L);
-  h2::MatDesc* md = nullptr;
-  if ((st = upload(h, &md, &D, 1)) != H2_OK) return st;
-  L.mats = md;
-  std::vector<int2> jobs((size_t)1 << h->tree_L);
-  for (size_t t = 0; t < jobs.size(); t++) jobs[t] = make_int2(0, (int)t);
-  int2* dj = nullptr;
-  if ((st = upload(h, &dj, jobs.data(), (int64_t)jobs.size())) != H2_OK) return st;
-  L.jobs = dj;
-  L.njobs = (int64_t)jobs.size();
   M.srow_host.assign(d->S_rowptr, d->S_rowptr + nodes + 1);
   L.items = M.dense_items.items;
   L.cta_begin = M.dense_items.cta_begin;
@@ -480,7 +492,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   L.bases_fp32 = M.bases_fp32;
   // defaults (h2_tune may choose others): 16 dense consumer warps for leaves of at most 32 points
   // (little arithmetic per item, more warps hide more latency), 128 coupling blocks per chunk
-  return mixed_configure(h, kDefaultChunkOpt, h->m_max <= 32 ? 2 * h2::kMixedCW : h2::kMixedCW);
+  return mixed_configure(h, kDefaultChunkOpt, h->m_max <= 32 ? 2 * h2::kMixedCW : h2::kMixedCW, 0);
 }
 
 h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {

@@ -50,8 +50,9 @@ __device__ __forceinline__ float2 codes_to_f2(uint32_t w) {
     return __half22float2(h);
   }
   if (F == kFormBf16) return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
-  return make_float2(__uint_as_float(0x4B000000u | (w & 0xFFFFu)) - 8421376.0f,
-                     __uint_as_float(0x4B000000u | (w >> 16)) - 8421376.0f);
+  // offset-binary int16 c: the float with bits 0x4B00 : c is 2^23 + c; one byte permute each
+  return make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7410)) - 8421376.0f,
+                     __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7432)) - 8421376.0f);
 }
 
 // ---------------------------------------------------------------- per-matrix descriptor

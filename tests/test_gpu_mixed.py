@@ -172,5 +172,5 @@ def test_tune_chooses_a_candidate_and_keeps_the_product(h2, c1):
     assert oracle.rel_l2(y.cpu().numpy(), ref) <= TOL_ACC  # with the chosen configuration
     M.close()
     F = h2.H2Matrix.from_generator(c1, storage="fp64")
-    assert F.tune(X, Y) == {"consumer_warps": 0, "chunk_blocks": 0}  # no options in the plain form
+    assert F.tune(X, Y) == {"consumer_warps": 0, "chunk_blocks": 0, "tree_leaves": 0}  # no options in the plain form
     F.close()
