@@ -112,6 +112,7 @@ struct MixedData {
   float dmax = 0.f, umax = 0.f;  // largest scale of the dense blocks and of the U blocks
   unsigned* tc_vmax = nullptr;   // tensor-core passes: per-vector maxima and scales
   float* tc_vscale = nullptr;
+  ItemList tc_items;             // tensor-core passes: their own work items (panel layout only)
   // the table-driven kernels' tables for this matrix alone (a batch of one)
   MixedLaunch launch;
   std::vector<h2::StreamItem> items_host;  // the dense items (matrix index 0), kept for batches

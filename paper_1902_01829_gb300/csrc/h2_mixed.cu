@@ -445,20 +445,68 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
         vc += m.vs;
       }
       ok = ok && vc <= h2::kMixedVecCols;
-      if (ok && M.panel) {  // the tensor-core stage: at most kTcMaxBlocks blocks, their B tiles in kTcStageB
-        int64_t tb = 0;
-        for (int u = 0; u < nb; u++) tb += (int64_t)h2::kTcN * h2::panel_cols(blk[it.v_off + u].cols) * 2;
-        ok = nb <= h2::kTcMaxBlocks && tb <= h2::kTcStageB && it.m_bytes == boff[it.v_off + nb] - boff[it.v_off];
-      }
       if (!ok) return h2_fail(H2_ERR_INVALID, "internal: precision-form work item %lld fails the layout audit", (long long)t);
     }
-    if (M.panel)  // the tensor-core phase starts a row's four accumulators with its first four K-steps
+    if (M.panel) {
+      // the tensor-core phase's own items: consecutive blocks of one row, at most kTcMaxBlocks
+      // blocks, kTcStageMat bytes of codes and kTcStageB bytes of B tiles (tc_layout); weighed
+      // by bytes and by MMAs (one per unit and K-step), the phase's two limits
+      std::vector<h2::StreamItem> titems;
+      std::vector<int64_t> trow_bytes((size_t)leaves), trow_item0((size_t)leaves + 1);
+      int kp[h2::kTcMaxBlocks], bo[h2::kTcMaxBlocks], pm = 0, sm = 0;
       for (int64_t i = 0; i < leaves; i++) {
-        int64_t ksteps = 0;
-        for (int64_t g = row_blk0[i]; g < row_blk0[i + 1]; g++) ksteps += h2::panel_cols(blk[g].cols) / 16;
-        if (ksteps < h2::kTcAccs) return h2_fail(H2_ERR_INVALID, "internal: leaf row %lld has %lld tensor-core K-steps",
-                                                 (long long)i, (long long)ksteps);
+        trow_item0[i] = (int64_t)titems.size();
+        const int64_t g0 = row_blk0[i], g1 = row_blk0[i + 1];
+        int64_t bytes = 0;
+        for (int64_t g = g0; g < g1;) {
+          int64_t e = g, mb = 0;
+          while (e < g1 && e - g < h2::kTcMaxBlocks && mb + (boff[e + 1] - boff[e]) <= h2::kTcStageMat) {
+            kp[e - g] = h2::panel_cols(blk[e].cols);
+            if (h2::tc_layout((int)(e - g + 1), kp, bo, &pm, &sm) > h2::kTcStageB) break;
+            mb += boff[e + 1] - boff[e];
+            e++;
+          }
+          if (e == g) return h2_fail(H2_ERR_INVALID, "internal: block %lld exceeds a tensor-core stage", (long long)g);
+          h2::StreamItem it{};
+          it.m_off = boff[g];
+          it.m_bytes = (int)mb;
+          it.shape = (unsigned)(lo[i + 1] - lo[i]) | ((unsigned)(e - g) << 8);
+          it.v_off = g;
+          it.row = (int)lo[i];
+          it.flags = (e == g1) ? h2::kItemFlagLast : 0;
+          titems.push_back(it);
+          h2::tc_layout((int)(e - g), kp, bo, &pm, &sm);
+          int64_t mmas = 0;
+          for (int u = 0; u < (int)(e - g); u++)
+            if (((pm | sm) >> u) & 1) mmas += kp[u] / 16;
+          bytes += mb + 4096 * mmas + 512;
+          g = e;
+        }
+        trow_bytes[i] = bytes;
       }
+      trow_item0[leaves] = (int64_t)titems.size();
+      const std::vector<int> tbegin = balance(trow_bytes, trow_item0, h->grid);
+      for (size_t t = 0; t < titems.size(); t++) {  // audit, as the kernel reads the items
+        const h2::StreamItem& it = titems[t];
+        const int nb = (int)((it.shape >> 8) & 0xFF);
+        bool ok = (it.shape & 0xFF) == 64 && nb >= 1 && nb <= h2::kTcMaxBlocks && it.v_off + nb <= nblk &&
+                  it.m_off % 16 == 0 && it.m_bytes % 16 == 0 && it.m_bytes <= h2::kTcStageMat &&
+                  it.m_off + it.m_bytes <= total && it.m_bytes == boff[it.v_off + nb] - boff[it.v_off];
+        for (int u = 0; ok && u < nb; u++) {
+          const h2::MixedBlock& m = blk[it.v_off + u];
+          kp[u] = h2::panel_cols(m.cols);
+          ok = (m.src & 4) && m.cols >= 1 && m.cols <= 64 &&
+               boff[it.v_off + u + 1] - boff[it.v_off + u] == h2::panel_block_bytes(m.cols);
+        }
+        ok = ok && h2::tc_layout(nb, kp, bo, &pm, &sm) <= h2::kTcStageB;
+        if (!ok) return h2_fail(H2_ERR_INVALID, "internal: tensor-core work item %lld fails the layout audit", (long long)t);
+      }
+      for (size_t c = 0; c + 1 < tbegin.size(); c++)
+        if (tbegin[c] > tbegin[c + 1]) return h2_fail(H2_ERR_INVALID, "internal: item ranges not monotone");
+      if ((st = upload(h, &M.tc_items.items, titems.data(), (int64_t)titems.size())) != H2_OK) return st;
+      if ((st = upload(h, &M.tc_items.cta_begin, tbegin.data(), (int64_t)tbegin.size())) != H2_OK) return st;
+      M.tc_items.count = (int64_t)titems.size();
+    }
     if ((st = upload(h, &M.dense_items.items, items.data(), (int64_t)items.size())) != H2_OK) return st;
     if ((st = upload(h, &M.dense_items.cta_begin, begin.data(), (int64_t)begin.size())) != H2_OK) return st;
     M.dense_items.count = (int64_t)items.size();
@@ -514,8 +562,8 @@ h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, doubl
   const MixedData& M = h->mx;
   if (M.panel && nv >= kTcMinVectors && h->storage != H2_INT16_SCALED) {  // dense phase on the tensor cores
     TcCall T;
-    T.items = M.dense_items.items;
-    T.cta_begin = M.dense_items.cta_begin;
+    T.items = M.tc_items.items;
+    T.cta_begin = M.tc_items.cta_begin;
     T.blk = M.dblk;
     T.dmat = M.dmat;
     T.x4 = M.x4;

@@ -4,8 +4,11 @@
 // Eq. 4 leaf expansion), with every block stored as 16-bit codes q and one FP32
 // scale sigma (a = sigma q).
 //
-// Operands of one block (M = 64 rows, N = 32, K = the block's columns):
-//  A  the block's fp16 / bf16 codes, copied by TMA as stored (the panel layout of
+// One tcgen05.mma costs about the same time for every shape up to M = 128, N = 256
+// (K = 16), so the kernel issues as few as it can: two consecutive blocks of a row
+// with the same width form one M = 128 operand (the second block's panels follow the
+// first's at the same stride), and their B tiles sit side by side in N:
+//  A  the two blocks' fp16 / bf16 codes, copied by TMA as stored (the panel layout of
 //     mixed.cuh is the MN-major canonical layout: 8 x 8 core matrices, K stride
 //     128 bytes, M stride the panel stride);
 //  B  built in shared memory per block by four builder warps from the FP32 copy
@@ -13,16 +16,19 @@
 //     split z = hi + lo into two codes of the block type (rows 2v and 2v + 1 of
 //     the K-major tile), so the products keep about FP32 accuracy and sigma enters
 //     exactly; s_v is a power of two per vector keeping fp16 parts in range (1 for
-//     bf16).
-// The K-steps of a row's blocks go round-robin into four 64 x 32 FP32 accumulators
-// (independent MMA chains; two such sets alternate between rows); four epilogue warps
-// read them back (tcgen05.ld), add them and the two parts of each vector, divide by
-// s_v and write y in FP64.
+//     bf16). The second block's rows are N rows 32 .. 63.
+// The 128 x 64 product holds the first block's result in rows 0 .. 63, columns
+// 0 .. 31 and the second's in rows 64 .. 127, columns 32 .. 63; the rest is unused.
+// A block without a partner is issued the same way with zero B rows 32 .. 63, so
+// whatever finite codes follow it in shared memory add exact zeros (the stages are
+// zeroed at start). Each row accumulates into one 128 x 64 accumulator (two
+// alternate between rows); four epilogue warps read them back (tcgen05.ld), add the
+// two halves and the two parts of each vector, divide by s_v and write y in FP64.
 //
-// Warp roles (320 threads, one CTA per SM, persistent over the same byte-balanced
-// work items as the CUDA-core path): 0 producer (TMA of the codes), 1 MMA issuer
-// (one thread), 2-5 B-tile builders, 6-9 epilogue (TMEM lane quadrants 2, 3, 0, 1).
-// Every wait is bounded; on a timeout the kernel sets the error word, the other
+// Warp roles (320 threads, one CTA per SM, persistent over byte-balanced work items
+// of their own, up to four 64 x 64 blocks and U): 0 producer (TMA of the codes), 1 MMA
+// issuer (one thread), 2-5 B-tile builders, 6-9 epilogue (TMEM lane quadrants 2, 3,
+// 0, 1). Every wait is bounded; on a timeout the kernel sets the error word, the other
 // roles stop at their next wait, the MMA thread waits for its issued MMAs, and the
 // tensor memory is freed before the kernel returns.
 #pragma once
@@ -34,17 +40,45 @@
 namespace h2 {
 
 constexpr int kTcVec = 16;                 // vectors per pass
-constexpr int kTcN = 2 * kTcVec;           // MMA N (high and low part of each vector)
-constexpr int kTcMaxBlocks = 4;            // blocks per work item (64 x 64 panels: at most 3 + U)
-constexpr int kTcStageB = kTcMaxBlocks * kTcN * 64 * 2;  // B tiles of one stage (16 KB)
+constexpr int kTcN = 2 * kTcVec;           // B rows of one block (high and low part of each vector)
+constexpr int kTcMaxBlocks = 5;            // blocks per work item (64 x 64 panels: at most 4 + U)
+constexpr int kTcStageMat = 35840;         // codes of one stage: four 64 x 64 panel blocks and a 64 x 16 one
+constexpr int kTcStageB = 18432;           // B tiles of one stage (tc_layout)
 constexpr int kTcHeader = 256;
-constexpr int kTcStage = kTcHeader + kStageMat + kTcStageB;
+constexpr int kTcStage = kTcHeader + kTcStageMat + kTcStageB;
 constexpr int kTcStages = 4;
-constexpr int kTcBlkBuf = 32 * kTcMaxBlocks * 16;  // block records of 32 items (producer)
-constexpr int kTcSmem = kTcStages * kTcStage + 256 + kTcBlkBuf;
+constexpr int kTcBlkBuf = 32 * kTcMaxBlocks * 16;    // block records of 32 items (producer)
+constexpr int kTcXBuf = 2 * 64 * (kTcVec + 1) * 4;   // epilogue exchange of the second halves, two rows
+constexpr int kTcSmem = kTcStages * kTcStage + 256 + kTcBlkBuf + kTcXBuf;
 constexpr int kTcThreads = 320;
-constexpr int kTcAccs = 4;                  // accumulators per row: K-step s goes to s % 4 (independent MMA chains)
-constexpr int kTcCols = 2 * kTcAccs * kTcN;  // tensor-memory columns: two rows in flight
+constexpr int kTcCols = 2 * 2 * kTcN;      // tensor-memory columns: a 128 x 64 accumulator per row, two rows
+static_assert(kTcSmem <= 232448, "tensor-core stages exceed the shared memory of a CTA");
+static_assert(kTcStageMat % 16 == 0 && kTcStageB % 16 == 0 && kTcStage % 16 == 0, "stage alignment");
+
+// B tiles of a stage. The item's blocks (padded widths kp[0 .. nb-1]) form MMA units:
+// two consecutive blocks of equal width a pair, any other block a single. A unit's tile
+// holds 2 kTcN K-major rows: the first block's kTcN rows, then the second block's (a
+// pair) or zeros (a single). boff[t] is block t's first row; bit t of *pairs marks a
+// pair starting at block t, bit t of *singles a single. Returns the stage's B bytes.
+__host__ __device__ inline int tc_layout(int nb, const int* kp, int* boff, int* pairs, int* singles) {
+  int cur = 0, pm = 0, sm = 0;
+  for (int t = 0; t < nb;) {
+    const int w = kTcN * kp[t] * 2;  // bytes of one block's rows
+    boff[t] = cur;
+    if (t + 1 < nb && kp[t + 1] == kp[t]) {
+      boff[t + 1] = cur + w;
+      pm |= 1 << t;
+      t += 2;
+    } else {
+      sm |= 1 << t;
+      t += 1;
+    }
+    cur += 2 * w;
+  }
+  *pairs = pm;
+  *singles = sm;
+  return cur;
+}
 
 struct TcParams {
   const StreamItem* items;
@@ -67,11 +101,11 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 }
 
 // kind::f16 instruction descriptor: FP32 accumulator, A and B of the code type,
-// A MN-major, B K-major, N = 32, M = 64
+// A MN-major, B K-major, N = 2 kTcN, M = 128
 template <int F>
 __host__ __device__ constexpr uint32_t tc_idesc() {
   return (1u << 4) | ((F == kFormBf16 ? 1u : 0u) << 7) | ((F == kFormBf16 ? 1u : 0u) << 10) | (1u << 15) |
-         ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
+         ((uint32_t)((2 * kTcN) >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accum) {
@@ -110,9 +144,10 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
   return __all_sync(0xFFFFFFFFu, ok) != 0;
 }
 
-// stage header (ints): [0] blocks, [1] flags; block t at 4 + 4 t: A offset (bytes),
-// K | (B source is yhat) << 16, panel stride (bytes), scale bits; [24 + 2 t] vector offset
-// (long long, in floats per vector slot)
+// stage header (ints): [0] blocks, [1] flags, [2] pair starts, [3] singles (tc_layout);
+// block t at 4 + 4 t: A offset (bytes), K | (B source is yhat) << 16, panel stride (bytes),
+// scale bits; [24 + 2 t] vector offset (long long, in floats per vector slot); [34 + t]
+// B offset (bytes)
 template <int F>
 __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -123,8 +158,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
   uint64_t* empty = bready + kTcStages;
   uint64_t* accfull = empty + kTcStages;
   uint64_t* accempty = accfull + 2;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(accempty + 2);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(accempty + 2) + 1;
+  uint64_t* xfull = accempty + 2;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(xfull + 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(xfull + 2) + 1;
+  float* xbuf = reinterpret_cast<float*>(smem + kTcStages * kTcStage + 256 + kTcBlkBuf);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ib = P.cta_begin[blockIdx.x], ie = P.cta_begin[blockIdx.x + 1];
   const int n_items = ie - ib;
@@ -138,6 +175,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
     for (int b = 0; b < 2; b++) {
       mbar_init(accfull + b, 1);
       mbar_init(accempty + b, 4);
+      mbar_init(xfull + b, 2);
     }
     *abort_flag = 0;
     fence_mbar_init();
@@ -148,6 +186,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // zeroed stages: the operand rows a single block leaves unused read finite codes
+  for (int i = threadIdx.x; i < kTcStages * kTcStage / 16; i += kTcThreads)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -206,13 +248,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
           hd[7 + 4 * lane] = __float_as_int(mb.scale);
           *reinterpret_cast<long long*>(hd + 24 + 2 * lane) = mb.voff;
         }
-        if (lane == 0) {
-          hd[0] = nb;
-          hd[1] = flags;
-        }
         __syncwarp();
         if (lane == 0) {
-          const unsigned bytes = (unsigned)min(m_bytes, kStageMat);
+          int kp[kTcMaxBlocks], bo[kTcMaxBlocks], pm = 0, sm = 0;
+          for (int t = 0; t < nb; t++) kp[t] = hd[5 + 4 * t] & 0xFFFF;
+          tc_layout(nb, kp, bo, &pm, &sm);
+          for (int t = 0; t < nb; t++) hd[34 + t] = bo[t];
+          hd[0] = nb;
+          hd[1] = flags;
+          hd[2] = pm;
+          hd[3] = sm;
+          const unsigned bytes = (unsigned)min(m_bytes, kTcStageMat);
           mbar_arrive(hdr + s);  // header ready for the builders (release)
           mbar_arrive_expect_tx(full + s, bytes);
           bulk_g2s_stream(st + kTcHeader, P.dmat + m_off, bytes, full + s, pol);
@@ -232,8 +278,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = tc_idesc<F>();
-      int rows = 0, issued_it = -1, kstep = 0;
-      bool row_open = false, ok = true;
+      int rows = 0, issued_it = -1;
+      bool row_open = false, first = false, ok = true;
       uint32_t acc_col = 0;
       for (int it = 0; it < n_items && ok; it++) {
         const int s = it % kTcStages, use = it / kTcStages;
@@ -244,32 +290,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
         }
         const unsigned char* st = stage0 + s * kTcStage;
         const int* hd = reinterpret_cast<const int*>(st);
-        const int nb = min(hd[0], kTcMaxBlocks), flags = hd[1];
+        const int nb = min(hd[0], kTcMaxBlocks), flags = hd[1], pm = hd[2];
         if (!row_open) {  // a new row: its accumulator must have been read out
           const int b = rows & 1;
           if (rows >= 2 && !mbar_wait(accempty + b, ((rows >> 1) - 1) & 1, abort_flag, P.err, P.budget)) {
             ok = false;
             break;
           }
-          acc_col = (uint32_t)(b * kTcAccs * kTcN);
+          acc_col = (uint32_t)(b * 2 * kTcN);
           row_open = true;
-          kstep = 0;
+          first = true;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_addr(st + kTcHeader), b0 = smem_addr(st + kTcHeader + kStageMat);
-        uint32_t boff = 0;
-        for (int t = 0; t < nb; t++) {
-          const int aoff = min(hd[4 + 4 * t], kStageMat - 1024);
-          const int K = min(hd[5 + 4 * t] & 0xFFFF, 64), ps = hd[6 + 4 * t];
-          for (int ks = 0; ks < K / 16; ks++) {
-            const uint64_t da = tc_desc(a0 + aoff + ks * 256, 128, ps);
-            const uint64_t db = tc_desc(b0 + boff + ks * 256, 128, K * 16);
-            // the first four K-steps of a row start the four accumulators (every row has its
-            // 64 x 64 diagonal block, four K-steps)
-            tc_mma(tmem + acc_col + (uint32_t)((kstep % kTcAccs) * kTcN), da, db, idesc, kstep >= kTcAccs ? 1u : 0u);
-            kstep++;
+        const uint32_t a0 = smem_addr(st + kTcHeader), b0 = smem_addr(st + kTcHeader + kTcStageMat);
+        for (int t = 0; t < nb;) {  // one MMA unit (a pair, or a single) per pass
+          const int K = max(min(hd[5 + 4 * t] & 0xFFFF, 64), 16), ps = min(hd[6 + 4 * t], panel_stride(64));
+          // the 16 panels read stay inside the stage (A and B regions), the unit's B rows inside B
+          const int aoff = max(min(hd[4 + 4 * t], kTcStageMat - 8 * ps), 0);
+          const int boff = max(min(hd[34 + t], kTcStageB - 4 * kTcN * K), 0);
+          // a K-step advances both start addresses by 256 bytes: 16 in the descriptors' address field
+          // (the addresses stay below 256 KB, so the field does not carry)
+          uint64_t da = tc_desc(a0 + aoff, 128, ps), db = tc_desc(b0 + boff, 128, K * 16);
+          for (int ks = 0; ks < K / 16; ks++, da += 16, db += 16) {
+            tc_mma(tmem + acc_col, da, db, idesc, first ? 0u : 1u);  // a row's first MMA starts its sum
+            first = false;
           }
-          boff += kTcN * K * 2;
+          t += ((pm >> t) & 1) ? 2 : 1;
         }
         tc_commit(empty + s);  // the stage is free once these MMAs complete
         issued_it = it;
@@ -323,13 +369,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
       const int s = it % kTcStages;
       unsigned char* st = stage0 + s * kTcStage;
       const int* hd = reinterpret_cast<const int*>(st);
-      const int nb = min(hd[0], kTcMaxBlocks);
-      unsigned char* bt = st + kTcHeader + kStageMat;
-      int boff = 0;
+      const int nb = min(hd[0], kTcMaxBlocks), singles = hd[3];
+      unsigned char* bt = st + kTcHeader + kTcStageMat;
 #pragma unroll
       for (int t = 0; t < kTcMaxBlocks; t++) {
         if (t >= nb) break;
         const int K = min(hd[5 + 4 * t] & 0xFFFF, 64);
+        const bool single = (singles >> t) & 1;  // its partner's rows (the next 2 K kTcN bytes) are zeros
+        const int boff = max(min(hd[34 + t], kTcStageB - (single ? 4 : 2) * kTcN * K), 0);
         const float sc = __int_as_float(hd[7 + 4 * t]) * sv;
         if (8 * g < K) {
           const float z[8] = {ra[t].x * sc, ra[t].y * sc, ra[t].z * sc, ra[t].w * sc,
@@ -347,8 +394,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
           const bool low_first = g & 1;
           *reinterpret_cast<uint4*>(dst + (low_first ? 16 : 0)) = low_first ? wl : wh;
           *reinterpret_cast<uint4*>(dst + (low_first ? 0 : 16)) = low_first ? wh : wl;
+          if (single) {
+            const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(dst + 2 * kTcN * K) = zero;
+            *reinterpret_cast<uint4*>(dst + 2 * kTcN * K + 16) = zero;
+          }
         }
-        boff += kTcN * K * 2;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
       __syncwarp();
@@ -369,8 +420,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    // warp w reads TMEM lanes 32 (w % 4) ..; rows 16 (w % 4) + lane (lane < 16) of the row block
+    // warp w reads TMEM lanes 32 (w % 4) ..: row 32 (w % 2) + lane of the row block, from the
+    // first blocks of the units (w % 4 < 2, columns 0 .. kTcN - 1) or the second (w % 4 >= 2,
+    // columns kTcN .. 2 kTcN - 1). The second-half warps pass their sums through shared memory
+    // (a buffer per accumulator; xfull marks it written); the first-half warps add them and
+    // write the rows. A buffer is rewritten only after its accumulator was released again,
+    // which the first-half warps do after reading it.
     const int q = warp & 3;
+    const bool second = q >= 2;
     float inv[kTcVec];
 #pragma unroll
     for (int v = 0; v < kTcVec; v++) inv[v] = 1.0f / P.vscale[v];
@@ -393,34 +450,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
           break;
         }
         tc_fence_after();
-        float sum[kTcN];
+        uint32_t c[kTcN];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 2 * kTcN + (second ? kTcN : 0));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
+              "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15]),
+              "=r"(c[16]), "=r"(c[17]), "=r"(c[18]), "=r"(c[19]), "=r"(c[20]), "=r"(c[21]), "=r"(c[22]),
+              "=r"(c[23]), "=r"(c[24]), "=r"(c[25]), "=r"(c[26]), "=r"(c[27]), "=r"(c[28]), "=r"(c[29]),
+              "=r"(c[30]), "=r"(c[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float sum[kTcVec];
 #pragma unroll
-        for (int i = 0; i < kTcN; i++) sum[i] = 0.f;
-#pragma unroll
-        for (int a = 0; a < kTcAccs; a++) {
-          uint32_t c[kTcN];
-          const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((b * kTcAccs + a) * kTcN);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]),
-                "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15]),
-                "=r"(c[16]), "=r"(c[17]), "=r"(c[18]), "=r"(c[19]), "=r"(c[20]), "=r"(c[21]), "=r"(c[22]),
-                "=r"(c[23]), "=r"(c[24]), "=r"(c[25]), "=r"(c[26]), "=r"(c[27]), "=r"(c[28]), "=r"(c[29]),
-                "=r"(c[30]), "=r"(c[31])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int i = 0; i < kTcN; i++) sum[i] += __uint_as_float(c[i]);
-        }
+        for (int v = 0; v < kTcVec; v++) sum[v] = __uint_as_float(c[2 * v]) + __uint_as_float(c[2 * v + 1]);
+        float* xr = xbuf + (b * 64 + 32 * (q & 1) + lane) * (kTcVec + 1);  // stride 17: no bank conflicts
         tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(accempty + b);
-        if (lane < 16) {
-          double* yr = P.y + row_off + 16 * q + lane;
+        if (second) {
+#pragma unroll
+          for (int v = 0; v < kTcVec; v++) xr[v] = sum[v];
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(xfull + b);  // release: the sums are visible to the waiting warps
+            mbar_arrive(accempty + b);
+          }
+        } else {
+          if (!tc_wait(xfull + b, (r >> 1) & 1, abort_flag, P.err, P.budget)) {
+            ok = false;
+            break;
+          }
+#pragma unroll
+          for (int v = 0; v < kTcVec; v++) sum[v] += xr[v];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(accempty + b);
+          double* yr = P.y + row_off + 32 * q + lane;
 #pragma unroll
           for (int v = 0; v < kTcVec; v++)
-            if (v < P.nv) yr[v * P.ldy] = (double)((sum[2 * v] + sum[2 * v + 1]) * inv[v]);
+            if (v < P.nv) yr[v * P.ldy] = (double)(sum[v] * inv[v]);
         }
         r++;
       }
