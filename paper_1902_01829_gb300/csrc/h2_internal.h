@@ -69,6 +69,7 @@ struct MixedLaunch {
 struct TcCall {
   const h2::StreamItem* items = nullptr;
   const int* cta_begin = nullptr;
+  const int4* brec = nullptr;   // builder records of the items
   const void* blk = nullptr;
   const void* dmat = nullptr;
   const float* x4 = nullptr;
@@ -113,6 +114,7 @@ struct MixedData {
   unsigned* tc_vmax = nullptr;   // tensor-core passes: per-vector maxima and scales
   float* tc_vscale = nullptr;
   ItemList tc_items;             // tensor-core passes: their own work items (panel layout only)
+  int4* tc_brec = nullptr;       // and the builders' records of those items
   // the table-driven kernels' tables for this matrix alone (a batch of one)
   MixedLaunch launch;
   std::vector<h2::StreamItem> items_host;  // the dense items (matrix index 0), kept for batches

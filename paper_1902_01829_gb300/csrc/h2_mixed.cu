@@ -473,9 +473,9 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
           it.shape = (unsigned)(lo[i + 1] - lo[i]) | ((unsigned)(e - g) << 8);
           it.v_off = g;
           it.row = (int)lo[i];
-          it.flags = (e == g1) ? h2::kItemFlagLast : 0;
-          titems.push_back(it);
           h2::tc_layout((int)(e - g), kp, bo, &pm, &sm);
+          it.flags = ((e == g1) ? h2::kItemFlagLast : 0) | (pm << h2::kTcPairShift);
+          titems.push_back(it);
           int64_t mmas = 0;
           for (int u = 0; u < (int)(e - g); u++)
             if (((pm | sm) >> u) & 1) mmas += kp[u] / 16;
@@ -498,11 +498,30 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
           ok = (m.src & 4) && m.cols >= 1 && m.cols <= 64 &&
                boff[it.v_off + u + 1] - boff[it.v_off + u] == h2::panel_block_bytes(m.cols);
         }
-        ok = ok && h2::tc_layout(nb, kp, bo, &pm, &sm) <= h2::kTcStageB;
+        ok = ok && h2::tc_layout(nb, kp, bo, &pm, &sm) <= h2::kTcStageB && (it.flags >> h2::kTcPairShift) == pm;
         if (!ok) return h2_fail(H2_ERR_INVALID, "internal: tensor-core work item %lld fails the layout audit", (long long)t);
       }
       for (size_t c = 0; c + 1 < tbegin.size(); c++)
         if (tbegin[c] > tbegin[c + 1]) return h2_fail(H2_ERR_INVALID, "internal: item ranges not monotone");
+      // the builders' records (kTcRecInts ints per item): block count and pair starts, then per
+      // block its vector offset, K | (vector from yhat) << 16 and scale
+      std::vector<int32_t> brec(titems.size() * h2::kTcRecInts, 0);
+      for (size_t t = 0; t < titems.size(); t++) {
+        const h2::StreamItem& it = titems[t];
+        const int nb = (int)((it.shape >> 8) & 0xFF);
+        int32_t* r = brec.data() + t * h2::kTcRecInts;
+        r[0] = nb | ((it.flags >> h2::kTcPairShift) << 8);
+        for (int u = 0; u < nb; u++) {
+          const h2::MixedBlock& m = blk[it.v_off + u];
+          if (m.voff < 0 || m.voff > INT32_MAX)
+            return h2_fail(H2_ERR_UNSUPPORTED, "vector offset %lld exceeds the tensor-core records", (long long)m.voff);
+          r[1 + 3 * u] = (int32_t)m.voff;
+          r[2 + 3 * u] = h2::panel_cols(m.cols) | ((m.src & 1) << 16);
+          std::memcpy(&r[3 + 3 * u], &m.scale, sizeof(float));
+        }
+      }
+      if ((st = upload(h, &M.tc_brec, reinterpret_cast<const int4*>(brec.data()), (int64_t)titems.size() * (h2::kTcRecInts / 4))) != H2_OK)
+        return st;
       if ((st = upload(h, &M.tc_items.items, titems.data(), (int64_t)titems.size())) != H2_OK) return st;
       if ((st = upload(h, &M.tc_items.cta_begin, tbegin.data(), (int64_t)tbegin.size())) != H2_OK) return st;
       M.tc_items.count = (int64_t)titems.size();
@@ -564,6 +583,7 @@ h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, doubl
     TcCall T;
     T.items = M.tc_items.items;
     T.cta_begin = M.tc_items.cta_begin;
+    T.brec = M.tc_brec;
     T.blk = M.dblk;
     T.dmat = M.dmat;
     T.x4 = M.x4;

@@ -118,6 +118,7 @@ h2_status tc_launch(const TcCall& T, cudaStream_t st) {
     P.x4 = T.x4;
     P.yhat = T.yhat;
     P.vscale = T.vscale;
+    P.brec = T.brec;
     P.y = T.y;
     P.ldy = T.ldy;
     P.nv = T.nv;

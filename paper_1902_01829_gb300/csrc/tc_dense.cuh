@@ -26,9 +26,10 @@
 // two halves and the two parts of each vector, divide by s_v and write y in FP64.
 //
 // Warp roles (320 threads, one CTA per SM, persistent over byte-balanced work items
-// of their own, up to four 64 x 64 blocks and U): 0 producer (TMA of the codes), 1 MMA
-// issuer (one thread), 2-5 B-tile builders, 6-9 epilogue (TMEM lane quadrants 2, 3,
-// 0, 1). Every wait is bounded; on a timeout the kernel sets the error word, the other
+// of their own, up to four 64 x 64 blocks and U): 0 producer (TMA of the codes and a
+// header for the MMA thread), 1 MMA issuer (one thread), 2-5 B-tile builders (reading
+// the items themselves, ahead of the stage ring), 6-9 epilogue (TMEM lane quadrants 2,
+// 3, 0, 1). Every wait is bounded; on a timeout the kernel sets the error word, the other
 // roles stop at their next wait, the MMA thread waits for its issued MMAs, and the
 // tensor memory is freed before the kernel returns.
 #pragma once
@@ -42,24 +43,32 @@ namespace h2 {
 constexpr int kTcVec = 16;                 // vectors per pass
 constexpr int kTcN = 2 * kTcVec;           // B rows of one block (high and low part of each vector)
 constexpr int kTcMaxBlocks = 5;            // blocks per work item (64 x 64 panels: at most 4 + U)
-constexpr int kTcStageMat = 35840;         // codes of one stage: four 64 x 64 panel blocks and a 64 x 16 one
-constexpr int kTcStageB = 18432;           // B tiles of one stage (tc_layout)
+constexpr int kTcStageMat = 35840;         // codes of one item: four 64 x 64 panel blocks and a 64 x 16 one
+constexpr int kTcStageB = 18432;           // B tiles of one item (tc_layout)
 constexpr int kTcHeader = 256;
-constexpr int kTcStage = kTcHeader + kTcStageMat + kTcStageB;
-constexpr int kTcStages = 4;
-constexpr int kTcBlkBuf = 32 * kTcMaxBlocks * 16;    // block records of 32 items (producer)
+constexpr int kTcSlotA = kTcHeader + kTcStageMat;  // a codes slot: header for the MMA thread, then the codes
+constexpr int kTcStages = 5;               // codes slots (copies in flight)
+constexpr int kTcStagesB = 2;              // B-tile slots (built shortly before their MMAs)
+constexpr int kTcRingB = kTcStages * kTcSlotA;     // offset of the B slots
+constexpr int kTcBars = kTcRingB + kTcStagesB * kTcStageB;
 constexpr int kTcXBuf = 2 * 64 * (kTcVec + 1) * 4;   // epilogue exchange of the second halves, two rows
-constexpr int kTcSmem = kTcStages * kTcStage + 256 + kTcBlkBuf + kTcXBuf;
+constexpr int kTcSmem = kTcBars + 256 + kTcXBuf;
 constexpr int kTcThreads = 320;
+constexpr int kTcPairShift = 8;            // item flags: bit 8 + t marks a pair starting at block t
+// builder record of an item (16 ints): [0] blocks | pair starts << 8; block t at 1 + 3 t:
+// vector offset (floats per vector slot), K | (vector from yhat) << 16, scale bits
+constexpr int kTcRecInts = 16;
+static_assert(1 + 3 * kTcMaxBlocks <= kTcRecInts, "builder record");
 constexpr int kTcCols = 2 * 2 * kTcN;      // tensor-memory columns: a 128 x 64 accumulator per row, two rows
 static_assert(kTcSmem <= 232448, "tensor-core stages exceed the shared memory of a CTA");
-static_assert(kTcStageMat % 16 == 0 && kTcStageB % 16 == 0 && kTcStage % 16 == 0, "stage alignment");
+static_assert(kTcStageMat % 16 == 0 && kTcStageB % 16 == 0 && kTcSlotA % 16 == 0, "slot alignment");
 
 // B tiles of a stage. The item's blocks (padded widths kp[0 .. nb-1]) form MMA units:
 // two consecutive blocks of equal width a pair, any other block a single. A unit's tile
 // holds 2 kTcN K-major rows: the first block's kTcN rows, then the second block's (a
-// pair) or zeros (a single). boff[t] is block t's first row; bit t of *pairs marks a
-// pair starting at block t, bit t of *singles a single. Returns the stage's B bytes.
+// pair) or zeros (a single); units follow each other. boff[t] is block t's first row;
+// bit t of *pairs marks a pair starting at block t, bit t of *singles a single. Returns
+// the stage's B bytes. The host stores the pair starts in the item's flags.
 __host__ __device__ inline int tc_layout(int nb, const int* kp, int* boff, int* pairs, int* singles) {
   int cur = 0, pm = 0, sm = 0;
   for (int t = 0; t < nb;) {
@@ -88,6 +97,7 @@ struct TcParams {
   const float* x4;      // FP32 vectors, leaf j at xp4_off[j] * nv (64 entries per vector)
   const float* yhat;    // [node][v][kp]
   const float* vscale;  // [16] per-vector power-of-two scale s_v
+  const int4* brec;     // builder records, kTcRecInts / 4 per item
   double* y;
   long long ldy;
   int nv, kp;
@@ -144,33 +154,34 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
   return __all_sync(0xFFFFFFFFu, ok) != 0;
 }
 
-// stage header (ints): [0] blocks, [1] flags, [2] pair starts, [3] singles (tc_layout);
-// block t at 4 + 4 t: A offset (bytes), K | (B source is yhat) << 16, panel stride (bytes),
-// scale bits; [24 + 2 t] vector offset (long long, in floats per vector slot); [34 + t]
-// B offset (bytes)
+// slot header (ints, for the MMA thread): [0] blocks, [1] item flags; block t at 4 + 3 t:
+// A offset (bytes), K, panel stride (bytes)
 template <int F>
 __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* stage0 = smem;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kTcStages * kTcStage);
-  uint64_t* hdr = full + kTcStages;
-  uint64_t* bready = hdr + kTcStages;
-  uint64_t* empty = bready + kTcStages;
-  uint64_t* accfull = empty + kTcStages;
+  unsigned char* slot0 = smem;               // codes slots
+  unsigned char* bslot0 = smem + kTcRingB;    // B-tile slots
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kTcBars);  // codes slot landed
+  uint64_t* empty = full + kTcStages;         // codes slot read by its MMAs
+  uint64_t* bready = empty + kTcStages;       // B slot written
+  uint64_t* bempty = bready + kTcStagesB;     // B slot read by its MMAs
+  uint64_t* accfull = bempty + kTcStagesB;
   uint64_t* accempty = accfull + 2;
   uint64_t* xfull = accempty + 2;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(xfull + 2);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(xfull + 2) + 1;
-  float* xbuf = reinterpret_cast<float*>(smem + kTcStages * kTcStage + 256 + kTcBlkBuf);
+  float* xbuf = reinterpret_cast<float*>(smem + kTcBars + 256);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ib = P.cta_begin[blockIdx.x], ie = P.cta_begin[blockIdx.x + 1];
   const int n_items = ie - ib;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTcStages; s++) {
       mbar_init(full + s, 1);
-      mbar_init(hdr + s, 1);
-      mbar_init(bready + s, 4);
       mbar_init(empty + s, 1);
+    }
+    for (int s = 0; s < kTcStagesB; s++) {
+      mbar_init(bready + s, 4);
+      mbar_init(bempty + s, 1);
     }
     for (int b = 0; b < 2; b++) {
       mbar_init(accfull + b, 1);
@@ -186,8 +197,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // zeroed stages: the operand rows a single block leaves unused read finite codes
-  for (int i = threadIdx.x; i < kTcStages * kTcStage / 16; i += kTcThreads)
+  // zeroed slots: the operand rows a single block leaves unused read finite codes
+  for (int i = threadIdx.x; i < kTcBars / 16; i += kTcThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
@@ -197,9 +208,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
-    // 32 items at a time: lane l loads item base + l, the items' block records (a contiguous
-    // range) go to shared memory, then the warp walks the items; lane 0 issues the copies
-    MixedBlock* blkbuf = reinterpret_cast<MixedBlock*>(smem + kTcStages * kTcStage + 256);
+    // 32 items at a time: lane l loads item base + l; per item, lanes 0 .. 15 load its builder
+    // record (the blocks' widths give their offsets); lane 0 writes the header and issues the copy
     const uint64_t pol = policy_evict_first();
     int issued = 0;
     bool ok = true;
@@ -207,61 +217,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
       const int cnt = min(32, n_items - base);
       StreamItem mine{};
       if (lane < cnt) mine = P.items[ib + base + lane];
-      const long long bfirst = __shfl_sync(0xFFFFFFFFu, mine.v_off, 0);
-      const long long blast = __shfl_sync(0xFFFFFFFFu, mine.v_off, cnt - 1) +
-                              min((int)((__shfl_sync(0xFFFFFFFFu, mine.shape, cnt - 1) >> 8) & 0xFF), kTcMaxBlocks);
-      const int nrec = (int)min(max(blast - bfirst, 0ll), (long long)(32 * kTcMaxBlocks));
-      __syncwarp();
-      for (int u = lane; u < nrec; u += 32) blkbuf[u] = P.blk[bfirst + u];
-      __syncwarp();
       for (int t = 0; t < cnt; t++) {
         const int it = base + t;
         const int s = it % kTcStages, use = it / kTcStages;
+        const int* rec = reinterpret_cast<const int*>(P.brec + (long long)(ib + it) * (kTcRecInts / 4));
+        const int rv = lane < kTcRecInts ? __ldg(rec + lane) : 0;
         if (use > 0 && !tc_wait(empty + s, (use - 1) & 1, abort_flag, P.err, P.budget)) {
           ok = false;
           break;
         }
         const long long m_off = __shfl_sync(0xFFFFFFFFu, mine.m_off, t);
         const int m_bytes = __shfl_sync(0xFFFFFFFFu, mine.m_bytes, t);
-        const unsigned shape = __shfl_sync(0xFFFFFFFFu, mine.shape, t);
-        const long long v_off = __shfl_sync(0xFFFFFFFFu, mine.v_off, t);
         const int flags = __shfl_sync(0xFFFFFFFFu, mine.flags, t);
-        const int nb = min((int)((shape >> 8) & 0xFF), kTcMaxBlocks);
-        unsigned char* st = stage0 + s * kTcStage;
-        int* hd = reinterpret_cast<int*>(st);
-        MixedBlock mb{};
-        const long long bi = v_off - bfirst + lane;
-        if (lane < nb && bi >= 0 && bi < nrec) mb = blkbuf[bi];
-        const int C = min((int)mb.cols, 64);
-        const int bytes_t = lane < nb ? panel_block_bytes(C) : 0;
-        int aoff = bytes_t;  // inclusive prefix over the item's blocks
+        const int nb = min(__shfl_sync(0xFFFFFFFFu, rv, 0) & 0xFF, kTcMaxBlocks);
+        int kp[kTcMaxBlocks];
 #pragma unroll
-        for (int d = 1; d < kTcMaxBlocks; d <<= 1) {
-          const int o = __shfl_up_sync(0xFFFFFFFFu, aoff, d);
-          if (lane >= d) aoff += o;
-        }
-        aoff -= bytes_t;
-        if (lane < nb) {
-          hd[4 + 4 * lane] = aoff;
-          hd[5 + 4 * lane] = panel_cols(C) | ((mb.src & 1) << 16);
-          hd[6 + 4 * lane] = panel_stride(C);
-          hd[7 + 4 * lane] = __float_as_int(mb.scale);
-          *reinterpret_cast<long long*>(hd + 24 + 2 * lane) = mb.voff;
-        }
-        __syncwarp();
+        for (int b = 0; b < kTcMaxBlocks; b++) kp[b] = min(__shfl_sync(0xFFFFFFFFu, rv, 2 + 3 * b) & 0xFFFF, 64);
+        int* hd = reinterpret_cast<int*>(slot0 + s * kTcSlotA);
         if (lane == 0) {
-          int kp[kTcMaxBlocks], bo[kTcMaxBlocks], pm = 0, sm = 0;
-          for (int t = 0; t < nb; t++) kp[t] = hd[5 + 4 * t] & 0xFFFF;
-          tc_layout(nb, kp, bo, &pm, &sm);
-          for (int t = 0; t < nb; t++) hd[34 + t] = bo[t];
+          int aoff = 0;
+#pragma unroll
+          for (int b = 0; b < kTcMaxBlocks; b++) {
+            if (b < nb) {
+              hd[4 + 3 * b] = aoff;
+              hd[5 + 3 * b] = kp[b];
+              hd[6 + 3 * b] = 16 * kp[b] + kPanelPad;  // panel stride
+              aoff += 8 * (16 * kp[b] + kPanelPad);
+            }
+          }
           hd[0] = nb;
           hd[1] = flags;
-          hd[2] = pm;
-          hd[3] = sm;
+          // the copy's completion also publishes the header (written before it)
           const unsigned bytes = (unsigned)min(m_bytes, kTcStageMat);
-          mbar_arrive(hdr + s);  // header ready for the builders (release)
           mbar_arrive_expect_tx(full + s, bytes);
-          bulk_g2s_stream(st + kTcHeader, P.dmat + m_off, bytes, full + s, pol);
+          bulk_g2s_stream(slot0 + s * kTcSlotA + kTcHeader, P.dmat + m_off, bytes, full + s, pol);
         }
         __syncwarp();
         issued = it + 1;
@@ -283,14 +272,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
       uint32_t acc_col = 0;
       for (int it = 0; it < n_items && ok; it++) {
         const int s = it % kTcStages, use = it / kTcStages;
+        const int sb = it % kTcStagesB, useb = it / kTcStagesB;
         if (!mbar_wait(full + s, use & 1, abort_flag, P.err, P.budget) ||
-            !mbar_wait(bready + s, use & 1, abort_flag, P.err, P.budget)) {
+            !mbar_wait(bready + sb, useb & 1, abort_flag, P.err, P.budget)) {
           ok = false;
           break;
         }
-        const unsigned char* st = stage0 + s * kTcStage;
+        const unsigned char* st = slot0 + s * kTcSlotA;
         const int* hd = reinterpret_cast<const int*>(st);
-        const int nb = min(hd[0], kTcMaxBlocks), flags = hd[1], pm = hd[2];
+        const int nb = min(hd[0], kTcMaxBlocks), flags = hd[1], pm = flags >> kTcPairShift;
         if (!row_open) {  // a new row: its accumulator must have been read out
           const int b = rows & 1;
           if (rows >= 2 && !mbar_wait(accempty + b, ((rows >> 1) - 1) & 1, abort_flag, P.err, P.budget)) {
@@ -302,12 +292,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
           first = true;
         }
         tc_fence_after();
-        const uint32_t a0 = smem_addr(st + kTcHeader), b0 = smem_addr(st + kTcHeader + kTcStageMat);
+        const uint32_t a0 = smem_addr(st + kTcHeader), b0 = smem_addr(bslot0 + sb * kTcStageB);
+        int bcur = 0;               // B tiles: units follow each other (tc_layout)
         for (int t = 0; t < nb;) {  // one MMA unit (a pair, or a single) per pass
-          const int K = max(min(hd[5 + 4 * t] & 0xFFFF, 64), 16), ps = min(hd[6 + 4 * t], panel_stride(64));
-          // the 16 panels read stay inside the stage (A and B regions), the unit's B rows inside B
-          const int aoff = max(min(hd[4 + 4 * t], kTcStageMat - 8 * ps), 0);
-          const int boff = max(min(hd[34 + t], kTcStageB - 4 * kTcN * K), 0);
+          const int K = max(min(hd[5 + 3 * t], 64), 16), ps = min(hd[6 + 3 * t], panel_stride(64));
+          const bool pair = (pm >> t) & 1;
+          // a single after the item's first block takes the upper half of the operand (its partner
+          // rows are the codes before it); the 16 panels read stay inside the slot's codes
+          int aoff = hd[4 + 3 * t] - (!pair && t > 0 ? 8 * ps : 0);
+          aoff = max(min(aoff, kTcStageMat - 16 * ps), 0);
+          const int boff = max(min(bcur, kTcStageB - 4 * kTcN * K), 0);
+          bcur += 4 * kTcN * K;
           // a K-step advances both start addresses by 256 bytes: 16 in the descriptors' address field
           // (the addresses stay below 256 KB, so the field does not carry)
           uint64_t da = tc_desc(a0 + aoff, 128, ps), db = tc_desc(b0 + boff, 128, K * 16);
@@ -315,9 +310,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
             tc_mma(tmem + acc_col, da, db, idesc, first ? 0u : 1u);  // a row's first MMA starts its sum
             first = false;
           }
-          t += ((pm >> t) & 1) ? 2 : 1;
+          t += pair ? 2 : 1;
         }
-        tc_commit(empty + s);  // the stage is free once these MMAs complete
+        tc_commit(empty + s);  // the slots are free once these MMAs complete
+        tc_commit(bempty + sb);
         issued_it = it;
         if (flags & kItemFlagLast) {
           tc_commit(accfull + (rows & 1));
@@ -338,85 +334,107 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
     // low rows of its vector for that K group. Lane l of builder warp w takes v = 4 w + (l & 3),
     // g = l >> 2, and threads with odd g store the low row first: each quarter-warp's two
     // stores then cover all eight 16-byte bank groups (rows 0 .. 7 of a core matrix), free of
-    // bank conflicts. The loads of item it + 1 are issued before item it is converted and
-    // stored (one item of look-ahead).
+    // bank conflicts. The builders read their own records of the items (brec) and load the
+    // vector entries an item ahead; only the conversion and the stores of item it wait for
+    // its B slot to be free.
     const int tid = threadIdx.x - 64, v = 4 * (tid >> 5) + (tid & 3), g = (tid >> 2) & 7;
     const float sv = P.vscale[v];
-    float4 za[2][kTcMaxBlocks], zb[2][kTcMaxBlocks];
-    auto fetch = [&](int it, float4(&ra)[kTcMaxBlocks], float4(&rb)[kTcMaxBlocks]) -> bool {
-      const int s = it % kTcStages, use = it / kTcStages;
-      if (!tc_wait(hdr + s, use & 1, abort_flag, P.err, P.budget)) return false;
-      const int* hd = reinterpret_cast<const int*>(stage0 + s * kTcStage);
-      const int nb = min(hd[0], kTcMaxBlocks);
+    const bool vok = v < P.nv;
+    struct Rec {
+      int4 q[kTcRecInts / 4];
+    };
+    auto rf = [](const Rec& R, int i) -> int {  // field i (a constant once the loops are unrolled)
+      const int4& u = R.q[i >> 2];
+      return (i & 3) == 0 ? u.x : (i & 3) == 1 ? u.y : (i & 3) == 2 ? u.z : u.w;
+    };
+    auto load_rec = [&](int it, Rec& R) {
+#pragma unroll
+      for (int u = 0; u < kTcRecInts / 4; u++)
+        R.q[u] = it < n_items ? __ldg(P.brec + (long long)(ib + it) * (kTcRecInts / 4) + u) : make_int4(0, 0, 0, 0);
+    };
+    auto load_x = [&](const Rec& R, float4(&ra)[kTcMaxBlocks], float4(&rb)[kTcMaxBlocks]) {
+      const int nb = min(rf(R, 0) & 0xFF, kTcMaxBlocks);
 #pragma unroll
       for (int t = 0; t < kTcMaxBlocks; t++) {
         ra[t] = rb[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (t < nb) {
-          const int K = min(hd[5 + 4 * t] & 0xFFFF, 64);
-          const bool from_yhat = (hd[5 + 4 * t] >> 16) & 1;
-          const long long voff = *reinterpret_cast<const long long*>(hd + 24 + 2 * t);
-          if (8 * g < K && v < P.nv) {
-            const float* src = from_yhat ? P.yhat + voff * P.nv + (long long)v * P.kp + 8 * g
-                                         : P.x4 + voff * P.nv + (long long)v * 64 + 8 * g;
-            ra[t] = __ldg(reinterpret_cast<const float4*>(src));
-            rb[t] = __ldg(reinterpret_cast<const float4*>(src + 4));
-          }
+        const int kw = rf(R, 2 + 3 * t);
+        if (t < nb && vok && 8 * g < min(kw & 0xFFFF, 64)) {
+          const long long voff = rf(R, 1 + 3 * t);
+          const float* src = ((kw >> 16) & 1) ? P.yhat + voff * P.nv + (long long)v * P.kp + 8 * g
+                                              : P.x4 + voff * P.nv + (long long)v * 64 + 8 * g;
+          ra[t] = __ldg(reinterpret_cast<const float4*>(src));
+          rb[t] = __ldg(reinterpret_cast<const float4*>(src + 4));
         }
       }
-      return true;
     };
-    auto build = [&](int it, const float4(&ra)[kTcMaxBlocks], const float4(&rb)[kTcMaxBlocks]) {
-      const int s = it % kTcStages;
-      unsigned char* st = stage0 + s * kTcStage;
-      const int* hd = reinterpret_cast<const int*>(st);
-      const int nb = min(hd[0], kTcMaxBlocks), singles = hd[3];
-      unsigned char* bt = st + kTcHeader + kTcStageMat;
+    // item it's B tiles from its records and entries (tc_layout's units, from the pair starts;
+    // a single after the first block has its rows in the upper half of its unit, as its codes)
+    auto convert_store = [&](int it, const Rec& R, const float4(&ra)[kTcMaxBlocks], const float4(&rb)[kTcMaxBlocks]) {
+      unsigned char* bt = bslot0 + (it % kTcStagesB) * kTcStageB;
+      const int nb = min(rf(R, 0) & 0xFF, kTcMaxBlocks), pm = rf(R, 0) >> 8;
+      int cur = 0, prev = 0;
+      bool second = false;
 #pragma unroll
       for (int t = 0; t < kTcMaxBlocks; t++) {
-        if (t >= nb) break;
-        const int K = min(hd[5 + 4 * t] & 0xFFFF, 64);
-        const bool single = (singles >> t) & 1;  // its partner's rows (the next 2 K kTcN bytes) are zeros
-        const int boff = max(min(hd[34 + t], kTcStageB - (single ? 4 : 2) * kTcN * K), 0);
-        const float sc = __int_as_float(hd[7 + 4 * t]) * sv;
-        if (8 * g < K) {
-          const float z[8] = {ra[t].x * sc, ra[t].y * sc, ra[t].z * sc, ra[t].w * sc,
-                              rb[t].x * sc, rb[t].y * sc, rb[t].z * sc, rb[t].w * sc};
-          uint32_t hi[4], lo[4];
-#pragma unroll
-          for (int e = 0; e < 4; e++) {
-            const float h0 = tc_round<F>(z[2 * e]), h1 = tc_round<F>(z[2 * e + 1]);
-            hi[e] = tc_pack<F>(h0, h1);
-            lo[e] = tc_pack<F>(z[2 * e] - h0, z[2 * e + 1] - h1);
+        if (t < nb) {
+          const int K = min(rf(R, 2 + 3 * t) & 0xFFFF, 64), w = 2 * kTcN * K;  // one block's rows
+          int boff, zoff = -1;  // this block's rows, and the zero partner rows of a single
+          if (second) {
+            boff = prev + w;
+            second = false;
+          } else {
+            prev = cur;
+            cur += 2 * w;
+            second = (pm >> t) & 1;
+            boff = (second || t == 0) ? prev : prev + w;
+            if (!second) zoff = t == 0 ? prev + w : prev;
           }
-          // K-major tile: row n = 2v (+1), core (n / 8, g) at (n / 8) * K * 16 + g * 128, row n % 8 at 16 bytes
-          unsigned char* dst = bt + boff + ((2 * v) >> 3) * K * 16 + g * 128 + ((2 * v) & 7) * 16;
-          const uint4 wh = make_uint4(hi[0], hi[1], hi[2], hi[3]), wl = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-          const bool low_first = g & 1;
-          *reinterpret_cast<uint4*>(dst + (low_first ? 16 : 0)) = low_first ? wl : wh;
-          *reinterpret_cast<uint4*>(dst + (low_first ? 0 : 16)) = low_first ? wh : wl;
-          if (single) {
-            const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4*>(dst + 2 * kTcN * K) = zero;
-            *reinterpret_cast<uint4*>(dst + 2 * kTcN * K + 16) = zero;
+          boff = max(min(boff, kTcStageB - w), 0);
+          zoff = zoff < 0 ? -1 : max(min(zoff, kTcStageB - w), 0);
+          if (8 * g < K) {
+            const float sc = __int_as_float(rf(R, 3 + 3 * t)) * sv;
+            const float z[8] = {ra[t].x * sc, ra[t].y * sc, ra[t].z * sc, ra[t].w * sc,
+                                rb[t].x * sc, rb[t].y * sc, rb[t].z * sc, rb[t].w * sc};
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const float h0 = tc_round<F>(z[2 * e]), h1 = tc_round<F>(z[2 * e + 1]);
+              hi[e] = tc_pack<F>(h0, h1);
+              lo[e] = tc_pack<F>(z[2 * e] - h0, z[2 * e + 1] - h1);
+            }
+            // K-major tile: row n = 2v (+1), core (n / 8, g) at (n / 8) * K * 16 + g * 128, row n % 8 at 16 bytes
+            const int inner = ((2 * v) >> 3) * K * 16 + g * 128 + ((2 * v) & 7) * 16;
+            unsigned char* dst = bt + boff + inner;
+            const uint4 wh = make_uint4(hi[0], hi[1], hi[2], hi[3]), wl = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            const bool low_first = g & 1;
+            *reinterpret_cast<uint4*>(dst + (low_first ? 16 : 0)) = low_first ? wl : wh;
+            *reinterpret_cast<uint4*>(dst + (low_first ? 0 : 16)) = low_first ? wh : wl;
+            if (zoff >= 0) {  // the partner rows of a single are zeros
+              const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+              *reinterpret_cast<uint4*>(bt + zoff + inner) = zero;
+              *reinterpret_cast<uint4*>(bt + zoff + inner + 16) = zero;
+            }
           }
         }
       }
+    };
+    // the step of item it converts entries loaded in the step before, then loads the entries of
+    // item it + 1 (records loaded in the step before) and the records of item it + 2
+    Rec rc, rn;
+    float4 xa[kTcMaxBlocks], xb[kTcMaxBlocks];
+    load_rec(0, rc);
+    load_rec(1, rn);
+    load_x(rc, xa, xb);
+    for (int it = 0; it < n_items; it++) {
+      const int sb = it % kTcStagesB, useb = it / kTcStagesB;
+      if (useb > 0 && !tc_wait(bempty + sb, (useb - 1) & 1, abort_flag, P.err, P.budget)) break;
+      convert_store(it, rc, xa, xb);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
       __syncwarp();
-      if (lane == 0) mbar_arrive(bready + s);
-    };
-    if (n_items > 0 && fetch(0, za[0], zb[0])) {
-      for (int it = 0; it < n_items; it++) {
-        // the next item's header is written only after its stage was freed, which needs the
-        // MMAs of this stage's previous use, not this item: waiting for it here cannot deadlock
-        // as long as it + 1 < it + kTcStages
-        const bool more = it + 1 < n_items;
-        bool ok = true;
-        if (more) ok = (it & 1) ? fetch(it + 1, za[0], zb[0]) : fetch(it + 1, za[1], zb[1]);
-        if (it & 1) build(it, za[1], zb[1]);
-        else build(it, za[0], zb[0]);
-        if (!ok) break;
-      }
+      if (lane == 0) mbar_arrive(bready + sb);
+      rc = rn;
+      load_x(rc, xa, xb);
+      load_rec(it + 2, rn);
     }
   } else {
     // ---------------------------------------------------------------- epilogue
