@@ -148,6 +148,17 @@ def dense_kernel_bytes(info: dict, A, nv: int, storage: str = "fp64", bases_fp32
             + 4 * A.leaves * A.k * nv)
 
 
+def dense_kernel_name(A, nv: int, storage: str, bases_fp32: bool) -> str:
+    """The kernel of the dense phase: the FP64 stream, or in the precision form the tensor-core
+    kernel (16-bit fp16 / bf16 codes and bases, k a multiple of 16, every leaf 64 points, 8 or
+    more vectors) or else the CUDA-core stream."""
+    if storage == "fp64":
+        return "k_dense_stream"
+    panel = (storage in ("fp16", "bf16") and not bases_fp32 and A.k % 16 == 0 and A.k <= 64
+             and bool(np.all(np.diff(np.asarray(A.leaf_offset)) == 64)))
+    return "k_dense_tc" if panel and nv >= 8 else "k_dense_stream_m"
+
+
 def run_oracle_baseline(A, x, budget_s: float = 12.0):
     """Time the FP64 oracle (as it stands) on the host cores over about budget_s seconds."""
     import oracle
@@ -251,7 +262,7 @@ def main():
     dense_ms = phase_ms["dense_expand"] / args.steps
     dbytes = dense_kernel_bytes(info, A, nv, args.storage, args.bases_fp32)
     achieved = dbytes / (dense_ms * 1e-3) / 1e9
-    kname = "k_dense_stream" if args.storage == "fp64" else "k_dense_stream_m"
+    kname = dense_kernel_name(A, nv, args.storage, args.bases_fp32)
     roofline = {"kernel": kname + " (dense blocks + leaf expansion)", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": (round(TRAFFIC_RATIO[(args.storage, args.bases_fp32)] * dbytes)

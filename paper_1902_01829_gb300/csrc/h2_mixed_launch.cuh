@@ -3,6 +3,7 @@
 // handle, or a batch. Each h2_mixed_<format>.cu instantiates it once, so the
 // three formats compile in parallel.
 #pragma once
+#include <algorithm>
 #include "h2_internal.h"
 #include "mixed.cuh"
 #include "tc_dense.cuh"
@@ -104,10 +105,11 @@ h2_status tc_launch(const TcCall& T, cudaStream_t st) {
     if (fp16) {
       cudaError_t e = cudaMemsetAsync(T.vmax, 0, kTcVec * sizeof(unsigned), st);
       if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-      const long long warps = T.leaves * T.nv;
+      // 32 warps per SM (152 SMs), each over a stride of leaves for one vector
+      const long long warps = (long long)T.nv * std::max<long long>(1, std::min<long long>(T.leaves, 152 * 32 / T.nv));
       k_tc_vmax<F><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
           T.x4, T.yhat, reinterpret_cast<const long long*>(T.xp4_off), T.leaves, T.leaf0, T.nv, T.kp, T.k, T.dmax,
-          T.umax, T.vmax);
+          T.umax, warps, T.vmax);
     }
     k_tc_vscale<F><<<1, 32, 0, st>>>(T.vmax, T.vscale, fp16 ? 1 : 0);
     TcParams P{};

@@ -521,20 +521,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
 
 // Per-vector power-of-two scales of a pass (fp16 codes): s_v = 2^(14 - e) with 2^e above
 // every |sigma x_v| and |sigma_U yhat_v| the builders form, so their parts stay below 2^14.
-// vmax holds float bits of the maxima (zeroed before the pass); one warp per (leaf, vector).
+// vmax holds float bits of the maxima (zeroed before the pass). `warps` (a multiple of nv)
+// warps run: warp w takes vector w % nv and leaves w / nv, w / nv + warps / nv, ..., and
+// adds its maximum with one atomic.
 template <int F>
 __global__ void k_tc_vmax(const float* __restrict__ x4, const float* __restrict__ yhat, const long long* __restrict__ xp4_off,
                           long long leaves, long long leaf0, int nv, int kp, int k, float dmax, float umax,
-                          unsigned* __restrict__ vmax) {
+                          long long warps, unsigned* __restrict__ vmax) {
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= leaves * nv) return;
-  const long long j = w / nv;
-  const int v = (int)(w - j * nv);
-  const float* xs = x4 + xp4_off[j] * nv + (long long)v * 64;
-  const float* ys = yhat + ((leaf0 + j) * nv + v) * (long long)kp;
-  float m = fmaxf(fabsf(xs[lane]), fabsf(xs[lane + 32])) * dmax;
-  for (int r = lane; r < k; r += 32) m = fmaxf(m, fabsf(ys[r]) * umax);
+  if (w >= warps || nv < 1) return;
+  const int v = (int)(w % nv);
+  const long long step = warps / nv;
+  float m = 0.f;
+  for (long long j = w / nv; j < leaves; j += step) {
+    const float* xs = x4 + xp4_off[j] * nv + (long long)v * 64;
+    const float* ys = yhat + ((leaf0 + j) * nv + v) * (long long)kp;
+    m = fmaxf(m, fmaxf(fabsf(xs[lane]), fabsf(xs[lane + 32])) * dmax);
+    for (int r = lane; r < k; r += 32) m = fmaxf(m, fabsf(ys[r]) * umax);
+  }
   for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
   if (lane == 0) atomicMax(vmax + v, __float_as_uint(m));  // non-negative floats order as their bits
 }
