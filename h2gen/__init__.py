@@ -45,6 +45,7 @@ def _load():
         lib.h2gen_info.argtypes = [vp, vp]
         lib.h2gen_fill_structure.argtypes = [vp] + [vp] * 8
         lib.h2gen_fill_values.argtypes = [vp] * 5
+        lib.h2gen_fill_cheb.argtypes = [vp, vp]
         lib.h2gen_free.argtypes = [vp]
         lib.h2gen_normal.argtypes = [ctypes.c_uint64, i64, vp]
         lib.h2gen_uniform.argtypes = [ctypes.c_uint64, i64, vp]
@@ -148,6 +149,13 @@ class H2Matrix:
         idx = np.arange(self.n, dtype=np.int64)
         out = np.empty((self.n, self.n), order="F")
         _load().h2gen_kernel_matrix(self._h, _p(idx), self.n, _p(idx), self.n, _p(out))
+        return out
+
+    def chebyshev_nodes(self) -> np.ndarray:
+        """(n_nodes, dim, p) first-kind Chebyshev nodes of every node's box per dimension; the
+        node's interpolation points are their tensor grid (dimension 0 slowest)."""
+        out = np.empty((self.n_nodes, self.dim, self.p), dtype=np.float64)
+        _load().h2gen_fill_cheb(self._h, _p(out))
         return out
 
     def free(self):

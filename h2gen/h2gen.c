@@ -330,6 +330,15 @@ void h2gen_info(void* hp, int64_t* info) {
   info[4] = g->D_valoff[g->nD]; info[5] = g->n_nodes; info[6] = g->leaves;
 }
 
+/* the first-kind Chebyshev nodes of every node's box: n_nodes*dim*p, node h
+   dimension d at (h*dim + d)*p (the interpolation points are their tensor grid,
+   dimension 0 slowest) */
+int h2gen_fill_cheb(void* hp, double* cheb) {
+  const h2gen_t* g = (const h2gen_t*)hp;
+  memcpy(cheb, g->cheb, (size_t)g->n_nodes * g->dim * g->p * sizeof(double));
+  return 0;
+}
+
 int h2gen_fill_structure(void* hp, double* pts, int64_t* perm, int64_t* leaf_offset, int32_t* S_rowptr, int32_t* S_colidx,
                          int32_t* D_rowptr, int32_t* D_colidx, int64_t* D_valoff) {
   h2gen_t* g = (h2gen_t*)hp;
