@@ -327,6 +327,9 @@ def main():
         # precision form (per-block scaled 16-bit S and D; U, V, E, F in FP32 or 16-bit) at several vector counts
         out["mixed"] = mixed_lines(h2, A, info, dev, stream, y_ref, x_np, args.steps, world, rank)
 
+        # the coupling blocks evaluated from the kernel at the interpolation points (none stored)
+        out["kernel_coupling"] = kernel_coupling_lines(h2, A, dev, stream, y_ref, x_np, args.steps, world)
+
         # many independent matrices of uneven size in one batched, graph-captured product
         if not args.no_batch:
             out["batch"] = batch_line(h2, dev, args.steps, world, rank, hbm)
@@ -385,6 +388,48 @@ def mixed_lines(h2, A, info64, dev, stream, y_ref, x_np, steps, world, rank):
                           "GBs": round(mb * world / (ms * 1e-3) / 1e9, 1),
                           "vectors_per_s": round(nv * world / (ms * 1e-3), 1),
                           "stored_bytes": mb, "rel_err_vs_fp64_oracle": err})
+        M.close()
+    return lines
+
+
+def kernel_coupling_lines(h2, A, dev, stream, y_ref, x_np, steps, world, form="int16", bases=True, nvs=(1, 16, 64)):
+    """The precision form with its coupling blocks evaluated in every product from the kernel at the
+    interpolation points (h2_create_kernel_coupling) next to the same form with the blocks stored:
+    time per product, the coupling phase, stored bytes, error vs the FP64 oracle (first column)."""
+    import oracle
+    import torch
+
+    xw = torch.from_numpy(np.ascontiguousarray(
+        np.concatenate([x_np, h2gen.vectors(913, A.n, max(nvs) - 1)], axis=1).T)).to(dev).t()
+    lines = []
+    for coupling in ("kernel", "stored"):
+        M = h2.H2Matrix.from_generator(A, storage=form, bases_fp32=bases, coupling=coupling)
+        info = M.info()
+        for nv in nvs:
+            X = xw[:, :nv]
+            Y = torch.empty((nv, A.n), dtype=torch.float64, device=dev).t()
+            M.tune(X, Y, stream=stream)
+            for _ in range(3):
+                M.matvec(X, Y, stream=stream)
+            M.check(stream)
+            k = max(3, steps // (1 + nv // 8))
+            M.profile(True)
+            M.profile_read()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(k):
+                M.matvec(X, Y, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            phase, _ = M.profile_read()
+            M.profile(False)
+            ms = e0.elapsed_time(e1) / k
+            lines.append({"coupling": coupling, "storage": form, "bases_fp32": bases, "nv": nv,
+                          "ms_per_step": round(ms, 4), "coupling_ms": round(phase["coupling"] / k, 4),
+                          "vectors_per_s": round(nv * world / (ms * 1e-3), 1), "stored_bytes": info["paper_bytes"],
+                          "device_bytes": info["device_bytes"],
+                          "rel_err_vs_fp64_oracle": oracle.rel_l2(Y[:, :1].cpu().numpy(), y_ref[:, :1])})
         M.close()
     return lines
 

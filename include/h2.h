@@ -129,6 +129,47 @@ typedef struct {
 h2_status h2_create(const h2_desc* d, h2_handle* out);
 
 /*
+ * Coupling blocks evaluated during the product instead of stored. The paper's
+ * matrices take every coupling block to be the covariance kernel at the
+ * interpolation points of its two clusters (Sec. 4.6):
+ *   S_ij[nu][mu] = K(xi_i^nu, xi_j^mu),
+ * xi_h^nu the point nu of the tensor grid of node h's first-kind Chebyshev
+ * nodes (dimension 0 slowest).
+ *   kernel   H2_KERNEL_EXP: K(r) = exp(-r / ell);
+ *            H2_KERNEL_MATERN32: K(r) = (1 + s) exp(-s), s = sqrt(3) r / ell
+ *   dim, p   1 <= dim <= 3, 1 <= p <= 16, p^dim equal to the descriptor's rank
+ *   ell      correlation length, finite and > 0
+ *   cheb     host FP64, n_nodes * dim * p finite values: the Chebyshev nodes of
+ *            node h (heap order) in dimension d at cheb + (h * dim + d) * p.
+ *            Copied; the caller keeps ownership.
+ */
+typedef enum { H2_KERNEL_EXP = 0, H2_KERNEL_MATERN32 = 1 } h2_kernel_kind;
+typedef struct {
+  int32_t kernel;
+  int32_t dim;
+  int32_t p;
+  int32_t reserved;  /* 0 */
+  double ell;
+  const double* cheb;
+} h2_coupling_kernel;
+
+/*
+ * As h2_create, but the coupling phase evaluates every S_ij from *kc in each
+ * product, and no coupling values are stored: d->S_val is ignored (it may be
+ * NULL); d->S_rowptr and d->S_colidx give the block structure. Scaled storage
+ * forms only (the dense blocks, bases and transfers are stored as h2_create
+ * stores them). Kernel values and products are FP32; each point is held as its
+ * node's centre (an FP32 pair, high and low part) plus an FP32 offset, and a
+ * distance is formed from the centres' difference and the offsets' difference,
+ * so it keeps FP32 relative precision at any separation. info[0] of h2_info
+ * then counts no coupling bytes. Such a handle cannot join a batch.
+ * Errors: those of h2_create; H2_ERR_INVALID (kc or kc->cheb NULL, kernel not an
+ * h2_kernel_kind, ell, dim or p out of range, p^dim != rank, non-finite cheb);
+ * H2_ERR_UNSUPPORTED (storage H2_FP64).
+ */
+h2_status h2_create_kernel_coupling(const h2_desc* d, const h2_coupling_kernel* kc, h2_handle* out);
+
+/*
  * y = A^H x for nv right-hand sides (Sec. 4, all phases), asynchronously on
  * `stream` (a cudaStream_t; NULL = legacy default stream).
  *   x   device FP64, n x nv, column-major, leading dimension ldx >= n
@@ -264,7 +305,8 @@ typedef struct h2_batch_s* h2_batch;
  * keep them alive until h2_batch_destroy, and do not run a product of a
  * member handle, alone or in another batch, concurrently with a product of
  * this batch (order them on one stream). Errors: H2_ERR_INVALID (NULL,
- * duplicates, mixed forms or ranks), H2_ERR_UNSUPPORTED (H2_FP64 handles),
+ * duplicates, mixed forms or ranks), H2_ERR_UNSUPPORTED (H2_FP64 handles, or
+ * handles made by h2_create_kernel_coupling),
  * H2_ERR_OOM, H2_ERR_CUDA.
  */
 h2_status h2_batch_create(const h2_handle* hs, int32_t count, h2_batch* out);

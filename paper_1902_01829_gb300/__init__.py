@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
                 5: "H2_ERR_TIMEOUT"}
 
 # every symbol include/h2.h declares
-EXPORTS = ["h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
+EXPORTS = ["h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
            "h2_profile_read", "h2_matvec_static", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
            "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_tune", "h2_batch_destroy",
            "h2_last_error"]
@@ -44,12 +44,21 @@ class h2_desc(ctypes.Structure):
                 ("check_cover", ctypes.c_int32), ("bases_fp32", ctypes.c_int32)]
 
 
+class h2_coupling_kernel(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("dim", ctypes.c_int32), ("p", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ell", ctypes.c_double), ("cheb", ctypes.c_void_p)]
+
+
+KERNELS = {"exp": 0, "matern32": 1}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
     lib = ctypes.CDLL(LIB_PATH)
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.h2_create.argtypes = [ctypes.POINTER(h2_desc), ctypes.POINTER(vp)]
+    lib.h2_create_kernel_coupling.argtypes = [ctypes.POINTER(h2_desc), ctypes.POINTER(h2_coupling_kernel), ctypes.POINTER(vp)]
     lib.h2_matvec.argtypes = [vp, i32, vp, i64, vp, i64, vp]
     lib.h2_matvec_host.argtypes = [vp, i32, vp, i64, vp, i64, vp]
     lib.h2_info.argtypes = [vp, vp]
@@ -69,7 +78,7 @@ def _load():
     lib.h2_tune.argtypes = [vp, i32, vp, i64, vp, i64, vp, vp]
     lib.h2_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.h2_last_error.restype = ctypes.c_char_p
-    for name in ("h2_create", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
+    for name in ("h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
                  "h2_profile_read", "h2_matvec_static", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
                  "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy",
                  "h2_tune", "h2_batch_tune"):
@@ -109,7 +118,10 @@ class H2Matrix:
     """An H^2 matrix resident on the current CUDA device (h2_create / h2_destroy)."""
 
     def __init__(self, *, n, depth, rank, leaf_offset, U, E, S_rowptr, S_colidx, S_val, D_rowptr, D_colidx, D_val,
-                 V=None, F=None, storage="fp64", check_cover=False, bases_fp32=False):
+                 V=None, F=None, storage="fp64", check_cover=False, bases_fp32=False, coupling_kernel=None):
+        """coupling_kernel: None (S_val stored), or dict(kernel="exp"|"matern32", ell, cheb) with cheb the
+        (n_nodes, dim, p) Chebyshev nodes of every node: the coupling blocks are then evaluated from the
+        kernel at the interpolation points in every product (h2_create_kernel_coupling), S_val unused."""
         sym = V is None and F is None
         keep = dict(leaf_offset=np.ascontiguousarray(leaf_offset, dtype=np.int64),
                     U=np.ascontiguousarray(U, dtype=np.float64), E=np.ascontiguousarray(E, dtype=np.float64),
@@ -117,7 +129,7 @@ class H2Matrix:
                     F=None if sym else np.ascontiguousarray(F, dtype=np.float64),
                     S_rowptr=np.ascontiguousarray(S_rowptr, dtype=np.int32),
                     S_colidx=np.ascontiguousarray(S_colidx, dtype=np.int32),
-                    S_val=np.ascontiguousarray(S_val, dtype=np.float64),
+                    S_val=None if coupling_kernel is not None else np.ascontiguousarray(S_val, dtype=np.float64),
                     D_rowptr=np.ascontiguousarray(D_rowptr, dtype=np.int32),
                     D_colidx=np.ascontiguousarray(D_colidx, dtype=np.int32),
                     D_val=np.ascontiguousarray(D_val, dtype=np.float64))
@@ -125,15 +137,27 @@ class H2Matrix:
                     check_cover=1 if check_cover else 0, bases_fp32=1 if bases_fp32 else 0,
                     **{key: _ptr(val) for key, val in keep.items()})
         self._h = ctypes.c_void_p()
-        _check(_lib.h2_create(ctypes.byref(d), ctypes.byref(self._h)))
+        if coupling_kernel is None:
+            _check(_lib.h2_create(ctypes.byref(d), ctypes.byref(self._h)))
+        else:
+            cheb = np.ascontiguousarray(coupling_kernel["cheb"], dtype=np.float64)
+            kc = h2_coupling_kernel(kernel=KERNELS[coupling_kernel["kernel"]], dim=int(cheb.shape[1]),
+                                    p=int(cheb.shape[2]), reserved=0, ell=float(coupling_kernel["ell"]), cheb=_ptr(cheb))
+            _check(_lib.h2_create_kernel_coupling(ctypes.byref(d), ctypes.byref(kc), ctypes.byref(self._h)))
         self.n = int(n)
 
     @classmethod
-    def from_generator(cls, A, storage="fp64", check_cover=False, bases_fp32=False) -> "H2Matrix":
-        """From an object with the generator's arrays (h2gen.H2Matrix)."""
+    def from_generator(cls, A, storage="fp64", check_cover=False, bases_fp32=False, coupling="stored") -> "H2Matrix":
+        """From an object with the generator's arrays (h2gen.H2Matrix). coupling="kernel" evaluates the
+        coupling blocks from the generator's kernel at its interpolation points in every product."""
+        ck = None
+        if coupling == "kernel":
+            ck = dict(kernel=A.kernel, ell=A.ell, cheb=A.chebyshev_nodes())
+        elif coupling != "stored":
+            raise ValueError(f"coupling={coupling!r}: 'stored' or 'kernel'")
         return cls(n=A.n, depth=A.q, rank=A.k, leaf_offset=A.leaf_offset, U=A.U, E=A.E, S_rowptr=A.S_rowptr,
                    S_colidx=A.S_colidx, S_val=A.S_val, D_rowptr=A.D_rowptr, D_colidx=A.D_colidx, D_val=A.D_val,
-                   storage=storage, check_cover=check_cover, bases_fp32=bases_fp32)
+                   storage=storage, check_cover=check_cover, bases_fp32=bases_fp32, coupling_kernel=ck)
 
     def matvec(self, x, y=None, stream=None):
         """y = A^H x on the device. x, y: torch float64 CUDA tensors, shape (n,) or (n, nv) column-major."""

@@ -108,7 +108,8 @@ h2_status check_cover(const h2_desc* d, int64_t leaves) {
   return H2_OK;
 }
 
-h2_status validate(const h2_desc* d, int64_t* nS, int64_t* nD, int64_t* nDval, int* m_max) {
+// s_values: the coupling values are part of the description (not evaluated from a kernel)
+h2_status validate(const h2_desc* d, bool s_values, int64_t* nS, int64_t* nD, int64_t* nDval, int* m_max) {
   if (!d) return fail(H2_ERR_INVALID, "desc is NULL");
   if (d->n < 1) return fail(H2_ERR_INVALID, "n = %lld < 1", (long long)d->n);
   if (d->n >= ((int64_t)1 << 31)) return fail(H2_ERR_UNSUPPORTED, "n = %lld >= 2^31", (long long)d->n);
@@ -135,7 +136,8 @@ h2_status validate(const h2_desc* d, int64_t* nS, int64_t* nD, int64_t* nDval, i
   for (int64_t r = 0; r < n_nodes; r++)
     if (d->S_rowptr[r + 1] < d->S_rowptr[r]) return fail(H2_ERR_INVALID, "S_rowptr decreases at row %lld", (long long)r);
   *nS = d->S_rowptr[n_nodes];
-  if (*nS > 0 && (!d->S_colidx || !d->S_val)) return fail(H2_ERR_INVALID, "S_colidx/S_val NULL with %lld blocks", (long long)*nS);
+  if (*nS > 0 && (!d->S_colidx || (s_values && !d->S_val)))
+    return fail(H2_ERR_INVALID, "S_colidx/S_val NULL with %lld blocks", (long long)*nS);
   for (int64_t r = 0; r < n_nodes; r++) {
     const int l = level_of(r);
     const int64_t first = ((int64_t)1 << l) - 1, last = ((int64_t)2 << l) - 2;
@@ -163,7 +165,8 @@ h2_status validate(const h2_desc* d, int64_t* nS, int64_t* nD, int64_t* nDval, i
     if (!values_ok(d->V, d->n * k, &bad)) return fail(H2_ERR_INVALID, "V[%lld] is not finite or too large", (long long)bad);
     if (!values_ok(d->F, (n_nodes - 1) * k * k, &bad)) return fail(H2_ERR_INVALID, "F[%lld] is not finite or too large", (long long)bad);
   }
-  if (*nS && !values_ok(d->S_val, *nS * k * k, &bad)) return fail(H2_ERR_INVALID, "S_val[%lld] is not finite or too large", (long long)bad);
+  if (s_values && *nS && !values_ok(d->S_val, *nS * k * k, &bad))
+    return fail(H2_ERR_INVALID, "S_val[%lld] is not finite or too large", (long long)bad);
   if (*nD && !values_ok(d->D_val, dv, &bad)) return fail(H2_ERR_INVALID, "D_val[%lld] is not finite or too large", (long long)bad);
   if (d->check_cover) return check_cover(d, leaves);
   return H2_OK;
@@ -528,17 +531,15 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
 
 }  // namespace
 
-extern "C" {
-
-const char* h2_last_error(void) { return g_err.c_str(); }
-
-h2_status h2_create(const h2_desc* d, h2_handle* out) {
-  g_err.clear();
+// h2_create, or h2_create_kernel_coupling with kc (already checked): the coupling phase then
+// evaluates the blocks from the kernel and stores none
+h2_status create_handle(const h2_desc* d, const h2_coupling_kernel* kc, h2_handle* out) {
+  if (!kc) g_err.clear();
   if (!out) return fail(H2_ERR_INVALID, "out is NULL");
   *out = nullptr;
   int64_t nS = 0, nD = 0, nDval = 0;
   int m_max = 0;
-  h2_status st = validate(d, &nS, &nD, &nDval, &m_max);
+  h2_status st = validate(d, kc == nullptr, &nS, &nD, &nDval, &m_max);
   if (st != H2_OK) return st;
   h2_matrix_s* h = new (std::nothrow) h2_matrix_s();
   if (!h) return fail(H2_ERR_OOM, "host allocation failed");
@@ -555,24 +556,62 @@ h2_status h2_create(const h2_desc* d, h2_handle* out) {
   h->m_max = m_max;
   h->lr = h->k > 32 ? 32 : pow2ceil(h->k);
   h->storage = d->storage;
+  h->kc = kc;
+  h->kf = kc != nullptr;
+  if (kc) {
+    h->kf_kind = kc->kernel;
+    h->kf_inv_ell = (float)(1.0 / kc->ell);
+  }
   try {
     st = build_device(h, d);
   } catch (const std::bad_alloc&) {
     st = fail(H2_ERR_OOM, "host allocation failed");
   }
+  h->kc = nullptr;  // the caller's description is not kept
   if (st != H2_OK) {
     free_all(h);
     delete h;
     return st;
   }
-  const int64_t kk = (int64_t)h->k * h->k, entries = 2 * h->n * h->k + 2 * (h->n_nodes - 1) * kk + nS * kk + nDval;
+  const int64_t kk = (int64_t)h->k * h->k, sS = h->kf ? 0 : nS;  // coupling blocks stored
+  const int64_t entries = 2 * h->n * h->k + 2 * (h->n_nodes - 1) * kk + sS * kk + nDval;
   if (h->storage == H2_FP64)
     h->paper_bytes = 8 * entries;
   else  // 16-bit codes plus one FP32 scale per block of U, V, E, F, S and D
-    h->paper_bytes = d->bases_fp32 ? 2 * (nS * kk + nDval) + 4 * (nS + nD) + 4 * (2 * h->n * h->k + 2 * (h->n_nodes - 1) * kk)
-                                   : 2 * entries + 4 * (2 * h->leaves + 2 * (h->n_nodes - 1) + nS + nD);
+    h->paper_bytes = d->bases_fp32 ? 2 * (sS * kk + nDval) + 4 * (sS + nD) + 4 * (2 * h->n * h->k + 2 * (h->n_nodes - 1) * kk)
+                                   : 2 * entries + 4 * (2 * h->leaves + 2 * (h->n_nodes - 1) + sS + nD);
   *out = h;
   return H2_OK;
+}
+
+extern "C" {
+
+const char* h2_last_error(void) { return g_err.c_str(); }
+
+h2_status h2_create(const h2_desc* d, h2_handle* out) { return create_handle(d, nullptr, out); }
+
+h2_status h2_create_kernel_coupling(const h2_desc* d, const h2_coupling_kernel* kc, h2_handle* out) {
+  g_err.clear();
+  if (!out) return fail(H2_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!d || !kc || !kc->cheb) return fail(H2_ERR_INVALID, "desc, kernel description or cheb is NULL");
+  if (kc->kernel != H2_KERNEL_EXP && kc->kernel != H2_KERNEL_MATERN32)
+    return fail(H2_ERR_INVALID, "kernel = %d is not an h2_kernel_kind", kc->kernel);
+  if (!(kc->ell > 0.0) || !std::isfinite(kc->ell) || (float)(1.0 / kc->ell) > 3.0e38f)
+    return fail(H2_ERR_INVALID, "ell = %g is not a finite positive length", kc->ell);
+  if (kc->dim < 1 || kc->dim > 3 || kc->p < 1 || kc->p > 16)
+    return fail(H2_ERR_INVALID, "dim = %d, p = %d outside 1..3, 1..16", kc->dim, kc->p);
+  int64_t kpow = 1;
+  for (int e = 0; e < kc->dim; e++) kpow *= kc->p;
+  if (kpow != d->rank) return fail(H2_ERR_INVALID, "p^dim = %lld differs from the rank %d", (long long)kpow, d->rank);
+  if (d->storage == H2_FP64)
+    return fail(H2_ERR_UNSUPPORTED, "coupling blocks from the kernel need a scaled storage form (FP32 arithmetic)");
+  if (d->depth < 0 || d->depth > 24) return fail(H2_ERR_INVALID, "depth = %d outside 0..24", d->depth);
+  const int64_t n_nodes = ((int64_t)2 << d->depth) - 1;
+  int64_t bad = 0;
+  if (!values_ok(kc->cheb, n_nodes * kc->dim * kc->p, &bad))
+    return fail(H2_ERR_INVALID, "cheb[%lld] is not finite or too large", (long long)bad);
+  return create_handle(d, kc, out);
 }
 
 h2_status h2_matvec(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream) {

@@ -62,6 +62,7 @@ struct MixedLaunch {
   int k = 0;
   bool bases_fp32 = false;
   int cw = 8;                        // consumer warps of the dense stream (8, or 16 for passes of <= 8 vectors)
+  bool kf = false;                   // coupling blocks evaluated from the kernel (no stored S)
   Profiler* prof = nullptr;          // profiler whose events mark the phases (or none)
 };
 
@@ -114,6 +115,9 @@ struct MixedData {
   unsigned* tc_vmax = nullptr;   // tensor-core passes: per-vector maxima and scales
   float* tc_vscale = nullptr;
   ItemList tc_items;             // tensor-core passes: their own work items (panel layout only)
+  float4* kf_chi = nullptr;      // coupling from the kernel: node centres (FP32 high parts, x y z 0)
+  float4* kf_clo = nullptr;      // and their low parts
+  float4* kf_off = nullptr;      // [node][k] offsets of the interpolation points from the centre
   int4* tc_brec = nullptr;       // and the builders' records of those items
   // the table-driven kernels' tables for this matrix alone (a batch of one)
   MixedLaunch launch;
@@ -150,6 +154,10 @@ struct h2_matrix_s {
   int64_t n = 0, leaves = 0, n_nodes = 0, leaf0 = 0, nS = 0, nD = 0, nDval = 0;
   int q = 0, k = 0, kp = 0, m_max = 0, lr = 32, grid = 0;
   int storage = H2_FP64;
+  const h2_coupling_kernel* kc = nullptr;  // while h2_create_kernel_coupling builds the handle
+  bool kf = false;                         // coupling blocks evaluated from the kernel
+  int kf_kind = 0;
+  float kf_inv_ell = 0.f;
   int64_t paper_bytes = 0, device_bytes = 0;
   std::vector<void*> allocs;
   int64_t* leaf_off = nullptr;

@@ -146,6 +146,11 @@ h2::MatDesc fill_desc(const h2_matrix_s* h, int tree_L) {
   D.LR = h->lr;
   D.q = h->q;
   D.L = tree_L;
+  D.kf_chi = M.kf_chi;
+  D.kf_clo = M.kf_clo;
+  D.kf_off = M.kf_off;
+  D.kf_inv_ell = h->kf_inv_ell;
+  D.kf_kind = h->kf_kind;
   return D;
 }
 
@@ -305,7 +310,46 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
       if ((st = upload(h, &M.escale, sc.data(), nodes - 1)) != H2_OK) return st;
     }
   }
-  {  // coupling blocks S (always 16-bit codes)
+  if (h->kc) {
+    // coupling blocks evaluated in the product from the kernel at the interpolation points
+    // (Sec. 4.6): per node its centre c (midpoint of its Chebyshev nodes per dimension) as an
+    // FP32 pair hi + lo, and its k points as FP32 offsets from c (tensor index, dimension 0
+    // slowest); unused dimensions are 0
+    const h2_coupling_kernel* kc = h->kc;
+    const int dim = kc->dim, p = kc->p;
+    std::vector<float4> chi((size_t)nodes), clo((size_t)nodes), off((size_t)(nodes * k));
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < nodes; n++) {
+      double c[3] = {0.0, 0.0, 0.0};
+      float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+      for (int e = 0; e < dim; e++) {
+        const double* cd = kc->cheb + (n * dim + e) * p;
+        double a = cd[0], b = cd[0];
+        for (int t = 1; t < p; t++) {
+          a = std::min(a, cd[t]);
+          b = std::max(b, cd[t]);
+        }
+        c[e] = 0.5 * (a + b);
+        hi[e] = (float)c[e];
+        lo[e] = (float)(c[e] - (double)hi[e]);
+      }
+      chi[(size_t)n] = make_float4(hi[0], hi[1], hi[2], 0.f);
+      clo[(size_t)n] = make_float4(lo[0], lo[1], lo[2], 0.f);
+      for (int nu = 0; nu < k; nu++) {
+        float o[3] = {0.f, 0.f, 0.f};
+        int rem = nu;
+        for (int e = dim - 1; e >= 0; e--) {
+          const int a = rem % p;
+          rem /= p;
+          o[e] = (float)(kc->cheb[(n * dim + e) * p + a] - c[e]);
+        }
+        off[(size_t)(n * k + nu)] = make_float4(o[0], o[1], o[2], 0.f);
+      }
+    }
+    if ((st = upload(h, &M.kf_chi, chi.data(), nodes)) != H2_OK) return st;
+    if ((st = upload(h, &M.kf_clo, clo.data(), nodes)) != H2_OK) return st;
+    if ((st = upload(h, &M.kf_off, off.data(), nodes * k)) != H2_OK) return st;
+  } else {  // coupling blocks S (always 16-bit codes)
     std::vector<uint16_t> codes((size_t)std::max<int64_t>(1, h->nS * kk8), 0);
     std::vector<float> sc((size_t)std::max<int64_t>(1, h->nS), 0.f);
 #pragma omp parallel for schedule(dynamic, 256)
@@ -557,6 +601,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   L.err = h->err;
   L.k = k;
   L.bases_fp32 = M.bases_fp32;
+  L.kf = h->kf;
   // defaults (h2_tune may choose others): 16 dense consumer warps for leaves of at most 32 points
   // (little arithmetic per item, more warps hide more latency), 128 coupling blocks per chunk
   return mixed_configure(h, kDefaultChunkOpt, h->m_max <= 32 ? 2 * h2::kMixedCW : h2::kMixedCW, 0);
@@ -779,6 +824,9 @@ h2_status h2_batch_create(const h2_handle* hs, int32_t count, h2_batch* out) {
   }
   if (v[0]->storage == H2_FP64)
     return h2_fail(H2_ERR_UNSUPPORTED, "batches take the scaled storage forms only (handle 0 is H2_FP64)");
+  for (int32_t i = 0; i < count; i++)
+    if (v[(size_t)i]->kf)
+      return h2_fail(H2_ERR_UNSUPPORTED, "handle %d evaluates its coupling blocks from the kernel (not batched)", i);
   for (int32_t i = 1; i < count; i++) {
     const h2_matrix_s* h = v[(size_t)i];
     if (h->storage != v[0]->storage || h->mx.bases_fp32 != v[0]->mx.bases_fp32 || h->k != v[0]->k)

@@ -30,7 +30,9 @@ void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st) {
   } else if (phase == 1 && L.nchunks > 0) {
     const unsigned cgrid = (unsigned)((L.nchunks + 3) / 4);
     const int k = L.k;
-    if (k == 16 || k == 32 || k == 64) {
+    if (L.kf) {  // coupling blocks evaluated from the kernel
+      k_coupling_kf<RPL, NVB><<<cgrid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
+    } else if (k == 16 || k == 32 || k == 64) {
       // up to four vectors per warp; 8 and 16 vectors take two and four warps per chunk
       constexpr int NVW = NVB < 4 ? NVB : 4, VG = NVB / NVW;
       const unsigned grid = (unsigned)((L.nchunks * VG + 3) / 4);

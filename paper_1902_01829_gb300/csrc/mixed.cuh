@@ -80,6 +80,13 @@ struct MatDesc {
   int* ticket;
   long long kk8, n_nodes;
   int k, kp, LR, q, L, pad0;
+  // coupling blocks from the kernel (k_coupling_kf): node centres as FP32 high and low parts,
+  // the interpolation points' offsets from the centre, 1 / ell and the kernel kind
+  const float4* kf_chi;
+  const float4* kf_clo;
+  const float4* kf_off;
+  float kf_inv_ell;
+  int kf_kind;
   // per product
   const double* x;
   long long ldx;
@@ -633,6 +640,89 @@ __global__ void __launch_bounds__(128) k_coupling_m_generic(const MatDesc* __res
     }
     group_reduce_m(acc, LR);
     store_node_m<RPL, NVB, false>(yhat + (int64_t)(row0 + r) * nv * kp, k, kp, LR, nv, acc, lane);
+  }
+}
+
+// ---------------------------------------------------------------- coupling from the kernel
+// The coupling blocks evaluated instead of read (the paper's matrices take every block as the
+// kernel at the interpolation points of its two clusters, Sec. 4.6): yhat_i = sum_j S_ij xhat_j,
+// S_ij[nu][mu] = K(|xi_i^nu - xi_j^mu|), K(r) = exp(-r / ell) or, for the Matern-3/2 kernel,
+// (1 + s) exp(-s) with s = sqrt(3) r / ell. A point is its node's centre c (FP32 pair hi + lo)
+// plus an FP32 offset o; a coordinate difference is ((hi_i - hi_j) + (lo_i - lo_j)) + (o_i - o_j),
+// which keeps FP32 relative precision of the distance at any separation. Lanes as warp_mv_m:
+// lane g * LR + rl owns rows rl + 32 r and takes the columns g, g + G, ..., G = 32 / LR; a row's
+// sums are reduced over the column groups once, after its last block. The column node's vectors
+// and point offsets are staged in the warp's shared memory; r = r2 * rsqrt(r2) and
+// exp(-t) = __expf(-t) (CUDA's fast intrinsics: relative errors of a few 1e-6 here, below the
+// form's FP32 accumulation bound).
+template <int RPL, int NVB>
+__global__ void __launch_bounds__(128) k_coupling_kf(const MatDesc* __restrict__ mats, const int4* __restrict__ chunks,
+                                                    int64_t nchunks, int nvlo, int nvhi) {
+  __shared__ __align__(16) float wstage[4][NVB * 64];
+  __shared__ float4 ostage[4][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* wbuf = wstage[warp];
+  float4* obuf = ostage[warp];
+  const int64_t cidx = (int64_t)blockIdx.x * 4 + warp;
+  if (cidx >= nchunks) return;
+  const int4 ch = __ldg(chunks + cidx);
+  const MatDesc& D = mats[ch.x];
+  const int nv = D.nv;
+  if (nv < nvlo || nv > nvhi) return;
+  const int k = min(D.k, 64), kp = D.kp, LR = D.LR, G = 32 / LR, g = lane / LR, rl = lane - g * LR;
+  const float4* __restrict__ chi = D.kf_chi;
+  const float4* __restrict__ clo = D.kf_clo;
+  const float4* __restrict__ off = D.kf_off;
+  const float inv_ell = D.kf_inv_ell;
+  const bool matern = D.kf_kind == 1;
+  const int32_t* __restrict__ Scol = D.Scol;
+  const float* __restrict__ xhat = D.xhat;
+  float* __restrict__ yhat = D.yhat;
+  const int row0 = ch.y, rows = min(ch.z, kChunkRows);
+  const ChunkRows cr = chunk_rows(D.Srow, yhat, row0, rows, nv, kp, lane, 0, nv);
+  for (unsigned m = cr.nonempty; m; m &= m - 1u) {
+    const int r = __ffs(m) - 1;
+    const int64_t i = row0 + r;
+    const int32_t b0 = __shfl_sync(0xFFFFFFFFu, cr.sr, r), b1 = __shfl_sync(0xFFFFFFFFu, cr.sr, r + 1);
+    float4 oi[RPL];
+#pragma unroll
+    for (int rr = 0; rr < RPL; rr++) {
+      const int nu = rl + 32 * rr;
+      oi[rr] = nu < k ? __ldg(off + i * k + nu) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float4 hi_i = __ldg(chi + i), lo_i = __ldg(clo + i);
+    float acc[RPL][NVB];
+#pragma unroll
+    for (int rr = 0; rr < RPL; rr++)
+#pragma unroll
+      for (int v = 0; v < NVB; v++) acc[rr][v] = 0.f;
+    const float tscale = matern ? 1.7320508f * inv_ell : inv_ell;
+    for (int32_t b = b0; b < b1; b++) {
+      const int64_t j = Scol[b];
+      for (int t = lane; t < k; t += 32) obuf[t] = __ldg(off + j * k + t);  // the column node's points
+      stage_vectors<false>(wbuf, xhat + j * nv * kp, nv * kp, lane);     // and vectors (syncs the warp)
+      const float4 hi_j = __ldg(chi + j), lo_j = __ldg(clo + j);
+      const float cx = (hi_i.x - hi_j.x) + (lo_i.x - lo_j.x), cy = (hi_i.y - hi_j.y) + (lo_i.y - lo_j.y),
+                  cz = (hi_i.z - hi_j.z) + (lo_i.z - lo_j.z);
+#pragma unroll 4
+      for (int mu = g; mu < k; mu += G) {
+        const float4 oj = obuf[mu];
+#pragma unroll
+        for (int rr = 0; rr < RPL; rr++) {
+          const float dx = cx + (oi[rr].x - oj.x), dy = cy + (oi[rr].y - oj.y), dz = cz + (oi[rr].z - oj.z);
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float t = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * tscale;
+          const float e = __expf(-t);
+          const float s = matern ? (1.f + t) * e : e;
+#pragma unroll
+          for (int v = 0; v < NVB; v++)
+            if (v < nv) acc[rr][v] = fmaf(s, wbuf[v * kp + mu], acc[rr][v]);
+        }
+      }
+      __syncwarp();
+    }
+    group_reduce_m(acc, LR);
+    store_node_m<RPL, NVB, false>(yhat + i * nv * kp, k, kp, LR, nv, acc, lane);
   }
 }
 

@@ -144,3 +144,34 @@ def test_batch_entry_points_reject_null_arguments(h2):
     assert lib.h2_batch_destroy(None) == h2.H2_OK
     assert lib.h2_batch_tune(None, None, None, None, None, None, None, None) == h2.H2_ERR_INVALID
     assert lib.h2_tune(None, 1, None, 1, None, 1, None, None) == h2.H2_ERR_INVALID
+
+
+def test_kernel_coupling_rejects_bad_descriptions(h2, small):
+    """h2_create_kernel_coupling checks its kernel description before touching the device."""
+    kw = _kw(small)
+    cheb = small.chebyshev_nodes()  # 2D, p = 3: rank 9
+
+    def expect(status, storage="int16", **over):
+        ck = dict(kernel="exp", ell=0.1, cheb=cheb)
+        ck.update(over)
+        with pytest.raises(h2.H2Error) as ei:
+            h2.H2Matrix(storage=storage, coupling_kernel=ck, **kw)
+        assert ei.value.status == status, str(ei.value)
+        return str(ei.value)
+
+    assert "scaled storage" in expect(h2.H2_ERR_UNSUPPORTED, storage="fp64")
+    assert "ell" in expect(h2.H2_ERR_INVALID, ell=0.0)
+    assert "ell" in expect(h2.H2_ERR_INVALID, ell=float("nan"))
+    assert "rank" in expect(h2.H2_ERR_INVALID, cheb=cheb[:, :, :2].copy())   # 2^2 = 4 points, rank 9
+    assert "rank" in expect(h2.H2_ERR_INVALID, cheb=cheb[:, :1, :].copy())   # 3^1 = 3 points
+    bad = cheb.copy()
+    bad[5, 1, 2] = np.inf
+    assert "cheb" in expect(h2.H2_ERR_INVALID, cheb=bad)
+    lib = h2._lib
+    out = ctypes.c_void_p()
+    assert lib.h2_create_kernel_coupling(None, None, ctypes.byref(out)) == h2.H2_ERR_INVALID
+    d = h2.h2_desc(n=small.n, depth=small.q, rank=small.k, storage=4)
+    kc = h2.h2_coupling_kernel(kernel=7, dim=2, p=3, reserved=0, ell=0.1, cheb=cheb.ctypes.data_as(ctypes.c_void_p))
+    assert lib.h2_create_kernel_coupling(ctypes.byref(d), ctypes.byref(kc), ctypes.byref(out)) == h2.H2_ERR_INVALID
+    assert "kernel" in lib.h2_last_error().decode()
+    assert out.value is None
