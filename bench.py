@@ -37,6 +37,8 @@ WORKLOADS = {
     "2d_n256k": "2D exp(-r/0.1) covariance H^2 matvec, n=2^18 uniform points, m=64, k=16, eta=0.9, FP64",
     "3d_n512k": "3D exp(-r/0.2) covariance H^2 matvec, n=2^19 uniform points in the unit cube, m=64, k=64 (4x4x4 Chebyshev), "
                 "eta=0.9, FP64",
+    "3d_n1M_kc": "3D exp(-r/0.2) covariance H^2 matvec, n=2^20 uniform points in the unit cube, m=64, k=64 (4x4x4 "
+                 "Chebyshev), eta=0.9, int16 + per-block f32 scale (S none: evaluated from the kernel), f32 bases",
     "batch256": "256 independent 2D exp(-r/0.1) covariance H^2 matvecs, n log-uniform in [2^12, 2^17], m=32, k=16, "
                 "eta=0.9, nv in {1, 4, 16}, fp16 storage + f32 arithmetic, one graph-captured batched product",
 }
@@ -44,6 +46,7 @@ WORKLOADS = {
 
 def replica_config(workload: str, rank: int) -> dict:
     """Weak scaling: every rank multiplies its own independent matrix of the same workload (seed per rank)."""
+    workload = {"3d_n1M_kc": "3d_n1M"}.get(workload, workload)
     if workload not in h2gen.CONFIGS:
         return {}
     cfg = dict(h2gen.CONFIGS[workload])
@@ -214,6 +217,8 @@ def main():
 
     if args.workload == "batch256":
         return batch_main(h2, args, dev, dist, world, rank, hbm, peak_kind)
+    if args.workload == "3d_n1M_kc":
+        return kernel_coupling_main(h2, args, cfg, dev, dist, world, rank)
     A = h2gen.generate(**cfg)
     M = h2.H2Matrix.from_generator(A, storage=args.storage, bases_fp32=args.bases_fp32)
     info = M.info()
@@ -557,12 +562,86 @@ def batch_main(h2, args, dev, dist, world, rank, hbm, peak_kind):
         dist.destroy_process_group()
 
 
+def kernel_coupling_main(h2, args, cfg, dev, dist, world, rank):
+    """--workload 3d_n1M_kc: the 3D k = 64 workload at its full size, n = 2^20, which one GPU holds
+    with the coupling blocks evaluated from the kernel (their 126 GB of FP64 values are never made):
+    int16 codes + FP32 bases, nv in {1, 8, 32, 64}. The error is taken on sampled rows against the
+    exact kernel matrix, as the paper measures its large problems (Sec. 4.6)."""
+    import torch
+
+    t0 = time.perf_counter()
+    A = h2gen.generate(**cfg, coupling_values=False)
+    M = h2.H2Matrix.from_generator(A, storage="int16", bases_fp32=True, coupling="kernel")
+    build_s = time.perf_counter() - t0
+    A.D_val = None  # the device holds the codes; free the host copy
+    info = M.info()
+    rng = np.random.default_rng(7 + rank)
+    leaves = rng.choice(A.leaves, size=16, replace=False)
+    rows = np.concatenate([np.arange(A.leaf_offset[i], A.leaf_offset[i + 1]) for i in sorted(leaves)])
+    x_np = h2gen.vectors(51 + rank, A.n, 64)
+    xw = torch.from_numpy(np.ascontiguousarray(x_np.T)).to(dev).t()
+    exact = A.exact_matvec_rows(rows, x_np[:, :1])
+    lines = []
+    with ClockSampler(dev.index) as clk:
+        for nv in (1, 8, 32, 64):
+            X = xw[:, :nv]
+            Y = torch.empty((nv, A.n), dtype=torch.float64, device=dev).t()
+            tuned = M.tune(X, Y)
+            for _ in range(3):
+                M.matvec(X, Y)
+            M.check()
+            k = max(3, args.steps // (1 + nv // 4))
+            M.profile(True)
+            M.profile_read()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(k):
+                M.matvec(X, Y)
+            e1.record()
+            torch.cuda.synchronize()
+            phase, launches = M.profile_read()
+            M.profile(False)
+            ms = max_over_ranks(e0.elapsed_time(e1) / k, dist, dev)
+            yr = Y[:, 0].cpu().numpy()[rows]
+            err = float(np.linalg.norm(yr - exact[:, 0]) / np.linalg.norm(exact[:, 0]))
+            lines.append({"nv": nv, "tuned": tuned, "ms_per_step": round(ms, 4),
+                          "GBs": round(info["paper_bytes"] * world / (ms * 1e-3) / 1e9, 1),
+                          "vectors_per_s": round(nv * world / (ms * 1e-3), 1),
+                          "phase_ms": {key: round(v / k, 4) for key, v in phase.items()},
+                          "launches_per_step": int(launches) // k,
+                          "rel_err_vs_exact_kernel_sampled_rows": err})
+    head = lines[0]
+    out = {"metric": METRIC, "value": head["GBs"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+           "warmup": 3, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int16 + per-block f32 scale (stored), f32 bases / f32 (computed)",
+           "data": "synthetic",
+           "config": {"workload": WORKLOADS["3d_n1M_kc"], "n": A.n, "q": A.q, "k": A.k, "nS": A.nS, "nD": A.nD,
+                      "paper_bytes": info["paper_bytes"], "device_bytes": info["device_bytes"],
+                      "l2": "matrix (%.1f GB) >> 129 MB L2: no flush needed" % (info["paper_bytes"] / 1e9),
+                      "error_sample": f"{rows.size} rows of 16 random leaves, first vector",
+                      "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+           "vectors_per_s": max(l["vectors_per_s"] for l in lines), "gpu_launches": head["launches_per_step"] * args.steps,
+           "lines": lines, "build_s": round(build_s, 1), "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    M.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def reference_arm(args, cfg, world):
     """The FP64 CPU oracle, timed as it stands on the host cores, same workload and metric."""
     import oracle
 
     if args.workload == "batch256":
         return reference_batch(args, world)
+    if args.workload == "3d_n1M_kc":
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle needs the 126 GB of stored coupling "
+                          "values that this workload never makes (it evaluates them from the kernel)"}), flush=True)
+        return
     A = h2gen.generate(**dict(h2gen.CONFIGS[args.workload]))
     x = h2gen.vectors(77, A.n, args.nv)
     paper_bytes = 8 * (2 * A.n * A.k + 2 * (A.n_nodes - 1) * A.k * A.k + A.nS * A.k * A.k + int(A.D_valoff[-1]))
