@@ -189,6 +189,8 @@ def main():
     ap.add_argument("--storage", default="fp64", choices=["fp64", "fp16", "bf16", "int16"],
                     help="storage form of the timed product (the extras always use fp64 and list the scaled forms)")
     ap.add_argument("--bases-fp32", action="store_true", help="scaled forms: keep U, V, E, F in FP32")
+    ap.add_argument("--coupling", default="stored", choices=["stored", "kernel"],
+                    help="scaled forms: coupling blocks stored, or evaluated from the kernel in every product")
     ap.add_argument("--no-batch", action="store_true", help="extras without the batched-workload line")
     args = ap.parse_args()
 
@@ -220,7 +222,7 @@ def main():
     if args.workload == "3d_n1M_kc":
         return kernel_coupling_main(h2, args, cfg, dev, dist, world, rank)
     A = h2gen.generate(**cfg)
-    M = h2.H2Matrix.from_generator(A, storage=args.storage, bases_fp32=args.bases_fp32)
+    M = h2.H2Matrix.from_generator(A, storage=args.storage, bases_fp32=args.bases_fp32, coupling=args.coupling)
     info = M.info()
     nv = args.nv
     x_np = h2gen.vectors(77 + rank, A.n, nv)
@@ -282,6 +284,7 @@ def main():
                      f"{args.storage} + per-block f32 scale (stored{', f32 bases' if args.bases_fp32 else ''}) / f32 (computed)"),
            "data": "synthetic",
            "config": {"workload": WORKLOADS[args.workload], "n": A.n, "nv": nv, "q": A.q, "k": A.k,
+                      "coupling": args.coupling,
                       "nS": A.nS, "nD": A.nD, "paper_bytes": info["paper_bytes"],
                       "l2": "matrix (%.1f GB) >> 129 MB L2: no flush needed" % (info["paper_bytes"] / 1e9),
                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
