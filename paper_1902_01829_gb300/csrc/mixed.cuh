@@ -650,12 +650,13 @@ __global__ void __launch_bounds__(128) k_coupling_m_generic(const MatDesc* __res
 // (1 + s) exp(-s) with s = sqrt(3) r / ell. A point is its node's centre c (FP32 pair hi + lo)
 // plus an FP32 offset o; a coordinate difference is ((hi_i - hi_j) + (lo_i - lo_j)) + (o_i - o_j),
 // which keeps FP32 relative precision of the distance at any separation. Rows as warp_mv_m: lane
-// g * LR + rl owns rows rl + 32 r; the columns go to the G = 32 / LR lane groups in runs of four
-// (group g takes columns 4 g .. 4 g + 3, 4 (g + G) .., ...), so a vector's four entries are one
-// float4 read of the staged vectors. A row's sums are reduced over the groups once, after its last
-// block. The column node's vectors and point offsets are staged in the warp's shared memory;
-// r = r2 * rsqrt(r2) and exp(-t) = __expf(-t) (CUDA's fast intrinsics: relative errors of a few
-// 1e-6 here, below the form's FP32 accumulation bound).
+// g * LR + rl owns rows rl + 32 r. The G = 32 / LR lane groups take different blocks of the row
+// (group g the blocks b0 + g, b0 + g + G, ...; GB <= G groups, so that their staged data fit),
+// each lane all k columns of its group's block in runs of four, so a vector's four entries are one
+// float4 read. A row's sums are reduced over the groups once, after its last block. Each group
+// stages its block's column points and vectors in the warp's shared memory; r = r2 * rsqrt(r2)
+// and exp(-t) = __expf(-t) (CUDA's fast intrinsics: relative errors of a few 1e-6 here, below the
+// form's FP32 accumulation bound).
 template <int RPL, int NVB>
 __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const MatDesc* __restrict__ mats,
                                                                      const int4* __restrict__ chunks, int64_t nchunks,
@@ -663,8 +664,6 @@ __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const Mat
   __shared__ __align__(16) float wstage[4][NVB * 64];
   __shared__ float4 ostage[4][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* wbuf = wstage[warp];
-  float4* obuf = ostage[warp];
   const int64_t cidx = (int64_t)blockIdx.x * 4 + warp;
   if (cidx >= nchunks) return;
   const int4 ch = __ldg(chunks + cidx);
@@ -672,6 +671,10 @@ __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const Mat
   const int nv = D.nv;
   if (nv < nvlo || nv > nvhi) return;
   const int k = min(D.k, 64), kp = D.kp, LR = D.LR, G = 32 / LR, g = lane / LR, rl = lane - g * LR;
+  const int GB = max(1, min(G, 64 / kp));  // groups with a block: GB * kp <= 64 staged columns
+  const bool active = g < GB;
+  float* wbuf = wstage[warp] + g * nv * kp;  // this group's block: vectors (nv x kp) and points (k)
+  float4* obuf = ostage[warp] + g * kp;
   const float4* __restrict__ chi = D.kf_chi;
   const float4* __restrict__ clo = D.kf_clo;
   const float4* __restrict__ off = D.kf_off;
@@ -699,44 +702,52 @@ __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const Mat
     for (int rr = 0; rr < RPL; rr++)
 #pragma unroll
       for (int v = 0; v < NVB; v++) acc[rr][v] = 0.f;
-    for (int32_t b = b0; b < b1; b++) {
-      const int64_t j = Scol[b];
-      for (int t = lane; t < k; t += 32) obuf[t] = __ldg(off + j * k + t);  // the column node's points
-      stage_vectors<false>(wbuf, xhat + j * nv * kp, nv * kp, lane);     // and vectors (syncs the warp)
-      const float4 hi_j = __ldg(chi + j), lo_j = __ldg(clo + j);
-      const float cx = (hi_i.x - hi_j.x) + (lo_i.x - lo_j.x), cy = (hi_i.y - hi_j.y) + (lo_i.y - lo_j.y),
-                  cz = (hi_i.z - hi_j.z) + (lo_i.z - lo_j.z);
-      for (int mu0 = 4 * g; mu0 < k; mu0 += 4 * G) {  // columns mu0 .. mu0 + 3 (mu0 + 3 < kp)
-        float sv[RPL][4];
+    for (int32_t bb = b0; bb < b1; bb += GB) {  // GB blocks at a time, one per group
+      const int32_t b = bb + g;
+      const bool mine = active && b < b1;
+      const int64_t j = mine ? (int64_t)Scol[b] : 0;
+      if (mine) {  // the group's lanes stage its block's column points and vectors
+        for (int t = rl; t < k; t += LR) obuf[t] = __ldg(off + j * k + t);
+        const float4* src = reinterpret_cast<const float4*>(xhat + j * nv * kp);
+        for (int t = rl; t < nv * kp / 4; t += LR) reinterpret_cast<float4*>(wbuf)[t] = src[t];
+      }
+      __syncwarp();
+      if (mine) {
+        const float4 hi_j = __ldg(chi + j), lo_j = __ldg(clo + j);
+        const float cx = (hi_i.x - hi_j.x) + (lo_i.x - lo_j.x), cy = (hi_i.y - hi_j.y) + (lo_i.y - lo_j.y),
+                    cz = (hi_i.z - hi_j.z) + (lo_i.z - lo_j.z);
+        for (int mu0 = 0; mu0 < k; mu0 += 4) {  // columns mu0 .. mu0 + 3 (mu0 + 3 < kp)
+          float sv[RPL][4];
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-          const float4 oj = obuf[min(mu0 + e, k - 1)];
+          for (int e = 0; e < 4; e++) {
+            const float4 oj = obuf[min(mu0 + e, k - 1)];
 #pragma unroll
-          for (int rr = 0; rr < RPL; rr++) {
-            const float dx = cx + (oi[rr].x - oj.x), dy = cy + (oi[rr].y - oj.y), dz = cz + (oi[rr].z - oj.z);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float t = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * tscale;
-            const float ex = __expf(-t);
-            sv[rr][e] = mu0 + e < k ? (matern ? (1.f + t) * ex : ex) : 0.f;
-          }
-        }
-#pragma unroll
-        for (int v = 0; v < NVB; v++) {
-          if (v >= nv) break;
-          float4 xv = *reinterpret_cast<const float4*>(wbuf + v * kp + mu0);
-          if (mu0 + 3 >= k) {  // entries past k (the vectors' padding) take no part
-            xv.w = 0.f;
-            if (mu0 + 2 >= k) xv.z = 0.f;
-            if (mu0 + 1 >= k) xv.y = 0.f;
+            for (int rr = 0; rr < RPL; rr++) {
+              const float dx = cx + (oi[rr].x - oj.x), dy = cy + (oi[rr].y - oj.y), dz = cz + (oi[rr].z - oj.z);
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const float t = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * tscale;
+              const float ex = __expf(-t);
+              sv[rr][e] = mu0 + e < k ? (matern ? (1.f + t) * ex : ex) : 0.f;
+            }
           }
 #pragma unroll
-          for (int rr = 0; rr < RPL; rr++)
-            acc[rr][v] = fmaf(sv[rr][3], xv.w, fmaf(sv[rr][2], xv.z, fmaf(sv[rr][1], xv.y, fmaf(sv[rr][0], xv.x, acc[rr][v]))));
+          for (int v = 0; v < NVB; v++) {
+            if (v >= nv) break;
+            float4 xv = *reinterpret_cast<const float4*>(wbuf + v * kp + mu0);
+            if (mu0 + 3 >= k) {  // entries past k (the vectors' padding) take no part
+              xv.w = 0.f;
+              if (mu0 + 2 >= k) xv.z = 0.f;
+              if (mu0 + 1 >= k) xv.y = 0.f;
+            }
+#pragma unroll
+            for (int rr = 0; rr < RPL; rr++)
+              acc[rr][v] = fmaf(sv[rr][3], xv.w, fmaf(sv[rr][2], xv.z, fmaf(sv[rr][1], xv.y, fmaf(sv[rr][0], xv.x, acc[rr][v]))));
+          }
         }
       }
       __syncwarp();
     }
-    // the column groups' partial sums: lanes rl, rl + LR, ... hold the same rows
+    // the groups' partial sums: lanes rl, rl + LR, ... hold the same rows
     group_reduce_m(acc, LR);
     store_node_m<RPL, NVB, false>(yhat + i * nv * kp, k, kp, LR, nv, acc, lane);
   }
