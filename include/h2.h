@@ -177,6 +177,11 @@ h2_status h2_create_kernel_coupling(const h2_desc* d, const h2_coupling_kernel* 
  *       overwritten (never accumulated into); must not overlap x
  * The handle's workspace is reused: calls on one handle must be ordered (same
  * stream or externally synchronized). No host synchronization happens inside.
+ * The product runs in passes of up to 16 vectors. In the scaled forms with
+ * fp16 or bf16 codes, 16-bit bases, k a multiple of 16 (at most 64) and every
+ * leaf of 64 points, a pass of 8 or more vectors runs the dense blocks on the
+ * tensor cores (vector operands split into two 16-bit parts, so the result
+ * keeps the FP32 accumulation accuracy of the other path).
  * Errors: H2_ERR_INVALID (NULL, nv < 1, ld < n), H2_ERR_CUDA (launch failed).
  */
 h2_status h2_matvec(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream);
