@@ -11,6 +11,7 @@
 // leaf expansion (Sec. 2.2, Eq. 4). Vectors x, xhat, yhat are FP32 with
 // strides rounded up to multiples of 4 (16-byte chunks for the bulk copies).
 #pragma once
+#include <type_traits>
 #include <cuda_fp16.h>
 
 #include "stream_fp64.cuh"
@@ -716,26 +717,29 @@ __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const Mat
         const float4 hi_j = __ldg(chi + j), lo_j = __ldg(clo + j);
         const float cx = (hi_i.x - hi_j.x) + (lo_i.x - lo_j.x), cy = (hi_i.y - hi_j.y) + (lo_i.y - lo_j.y),
                     cz = (hi_i.z - hi_j.z) + (lo_i.z - lo_j.z);
-        for (int mu0 = 0; mu0 < k; mu0 += 4) {  // columns mu0 .. mu0 + 3 (mu0 + 3 < kp)
+        // one run of four columns; FULL: all four below k (no clamping or masking)
+        auto run = [&](int mu0, auto full_tag) {
+          constexpr bool FULL = decltype(full_tag)::value;
           float sv[RPL][4];
 #pragma unroll
           for (int e = 0; e < 4; e++) {
-            const float4 oj = obuf[min(mu0 + e, k - 1)];
+            const float4 oj = obuf[FULL ? mu0 + e : min(mu0 + e, k - 1)];
 #pragma unroll
             for (int rr = 0; rr < RPL; rr++) {
               const float dx = cx + (oi[rr].x - oj.x), dy = cy + (oi[rr].y - oj.y), dz = cz + (oi[rr].z - oj.z);
               const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
               const float t = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * tscale;
               const float ex = __expf(-t);
-              sv[rr][e] = mu0 + e < k ? (matern ? (1.f + t) * ex : ex) : 0.f;
+              const float val = matern ? (1.f + t) * ex : ex;
+              sv[rr][e] = (FULL || mu0 + e < k) ? val : 0.f;
             }
           }
 #pragma unroll
           for (int v = 0; v < NVB; v++) {
             if (v >= nv) break;
             float4 xv = *reinterpret_cast<const float4*>(wbuf + v * kp + mu0);
-            if (mu0 + 3 >= k) {  // entries past k (the vectors' padding) take no part
-              xv.w = 0.f;
+            if (!FULL) {  // entries past k (the vectors' padding) take no part
+              if (mu0 + 3 >= k) xv.w = 0.f;
               if (mu0 + 2 >= k) xv.z = 0.f;
               if (mu0 + 1 >= k) xv.y = 0.f;
             }
@@ -743,7 +747,10 @@ __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const Mat
             for (int rr = 0; rr < RPL; rr++)
               acc[rr][v] = fmaf(sv[rr][3], xv.w, fmaf(sv[rr][2], xv.z, fmaf(sv[rr][1], xv.y, fmaf(sv[rr][0], xv.x, acc[rr][v]))));
           }
-        }
+        };
+        int mu0 = 0;
+        for (; mu0 + 3 < k; mu0 += 4) run(mu0, std::true_type{});  // columns mu0 .. mu0 + 3
+        if (mu0 < k) run(mu0, std::false_type{});                   // the last, partial run (mu0 + 3 < kp)
       }
       __syncwarp();
     }
