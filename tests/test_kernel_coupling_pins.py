@@ -90,3 +90,15 @@ def test_interpolation_property_pins_the_point_order():
     wrong = blocks[:, perm][:, :, perm].transpose(0, 2, 1).ravel()
     assert not np.array_equal(wrong, good)
     assert _interp_error(A, wrong) > 1e-2
+
+
+def test_generation_without_coupling_values_keeps_the_rest():
+    """The generator's coupling_values=False (used when the coupling blocks are evaluated from the
+    kernel) leaves S_val out and every other array as the full generation makes it."""
+    cfg = dict(dim=3, n=3000, m=32, p=3, eta=0.9, kernel="exp", ell=0.2, seed=21)
+    full = h2gen.generate(**cfg)
+    part = h2gen.generate(**cfg, coupling_values=False)
+    assert part.S_val is None
+    for name in ("U", "E", "D_val", "leaf_offset", "S_rowptr", "S_colidx", "D_rowptr", "D_colidx", "points"):
+        assert np.array_equal(getattr(full, name), getattr(part, name)), name
+    assert np.array_equal(full.chebyshev_nodes(), part.chebyshev_nodes())
