@@ -247,17 +247,22 @@ h2_status h2_profile_read(h2_handle h, double ms[H2_NPHASES], int64_t* launches)
  * code on a latency-critical path where cudaMalloc / cudaFree could
  * synchronize the device.)
  *   d               the matrix in the h2_desc format above, but every array
- *                   pointer is DEVICE memory owned by the caller; the
- *                   structure is not validated (build it as for h2_create)
- *   n_dense_blocks  D_rowptr[2^q], the number of dense blocks
+ *                   pointer is DEVICE memory owned by the caller
+ *   n_dense_blocks  D_rowptr[2^q], the number of dense blocks (<= 2^20)
  *   x, y            device FP64, n x nv column-major (ldx, ldy >= n); y is
  *                   overwritten; x and y must not overlap
  * The working memory is one static 16 MiB device array in the library, held
  * by every GPU that loads it until the process exits. The call is rejected
- * with H2_ERR_UNSUPPORTED unless
- *   2 * (2^(q+1) - 1) * nv * k * 8 + (n_dense_blocks + 1) * 8 <= 16 MiB.
- * Every call shares that array; each word is written before it is read in
- * the same call, so nothing carries over, but calls that overlap on the GPU
+ * with H2_ERR_UNSUPPORTED when k > 64, n_dense_blocks > 2^20, or unless
+ *   256 + 2 * (2^(q+1) - 1) * nv * k * 8 + (n_dense_blocks + 1) * 8 <= 16 MiB.
+ * The kernel first checks the structure arrays it indexes with (leaf offsets
+ * from 0 to n with sizes 1..64, block row pointers from 0 and non-decreasing,
+ * coupling columns on the row's level, dense columns among the leaves,
+ * D_rowptr[2^q] == n_dense_blocks); if one fails it writes nothing but a
+ * sticky error word and leaves y untouched: h2_matvec_static_check reports it.
+ * Arithmetic is native FP64 (any finite values). Every call shares that
+ * array; each word is written before it is read in the same call, so nothing
+ * but the error word carries over, and calls that overlap on the GPU
  * (different streams, different threads) race and corrupt each other.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
@@ -267,6 +272,15 @@ h2_status h2_profile_read(h2_handle h, double ms[H2_NPHASES], int64_t* launches)
  */
 h2_status h2_matvec_static(const h2_desc* d, int64_t n_dense_blocks, int32_t nv, const double* x, int64_t ldx, double* y,
                            int64_t ldy, void* stream);
+
+/*
+ * Report a malformed description seen by h2_matvec_static since the last
+ * check (the paper has no counterpart). Synchronizes `stream`, reads the
+ * static array's error word and clears it; allocates nothing.
+ * Returns H2_OK, H2_ERR_INVALID (some product since the last check found a
+ * malformed description and left its y untouched) or H2_ERR_CUDA.
+ */
+h2_status h2_matvec_static_check(void* stream);
 
 /*
  * Autotuning of the launch parameters of the scaled storage forms. Runs the

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
 
 # every symbol include/h2.h declares
 EXPORTS = ["h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
-           "h2_profile_read", "h2_matvec_static", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
+           "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
            "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_tune", "h2_batch_destroy",
            "h2_last_error"]
 PHASES = ["upsweep", "coupling", "downsweep", "dense_expand"]
@@ -66,6 +66,7 @@ def _load():
     lib.h2_profile.argtypes = [vp, i32]
     lib.h2_check.argtypes = [vp, vp]
     lib.h2_matvec_static.argtypes = [ctypes.POINTER(h2_desc), i64, i32, vp, i64, vp, i64, vp]
+    lib.h2_matvec_static_check.argtypes = [vp]
     lib.h2_debug_withhold_copy.argtypes = [vp, i32, i64]
     lib.h2_profile_read.argtypes = [vp, vp, vp]
     lib.h2_batch_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
@@ -79,7 +80,7 @@ def _load():
     lib.h2_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.h2_last_error.restype = ctypes.c_char_p
     for name in ("h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
-                 "h2_profile_read", "h2_matvec_static", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
+                 "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
                  "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy",
                  "h2_tune", "h2_batch_tune"):
         getattr(lib, name).restype = ctypes.c_int
@@ -328,13 +329,15 @@ class H2Batch:
 
 
 def matvec_static(n, depth, rank, leaf_offset, U, E, S_rowptr, S_colidx, S_val, D_rowptr, D_colidx, D_val, x, y,
-                  V=None, F=None, stream=None):
+                  V=None, F=None, stream=None, n_dense_blocks=None):
     """y = A^H x through h2_matvec_static, which allocates nothing.
 
     For callers that may not allocate device memory: every array is a torch
     CUDA tensor the caller already owns (int64 leaf_offset, int32 index arrays,
     float64 values); x and y are (n, nv) column-major float64 CUDA tensors.
     The library's only working memory is a static 16 MiB device array.
+    n_dense_blocks defaults to D_colidx.numel(). A malformed description is
+    reported by matvec_static_check(), not by this call.
     """
     sym = V is None and F is None
     d = h2_desc(n=int(n), depth=int(depth), rank=int(rank), symmetric=1 if sym else 0, storage=STORAGE["fp64"],
@@ -347,6 +350,12 @@ def matvec_static(n, depth, rank, leaf_offset, U, E, S_rowptr, S_colidx, S_val, 
     nv = X.shape[1]
     ldx = X.stride(1) if nv > 1 else int(n)
     ldy = Y.stride(1) if nv > 1 else int(n)
-    _check(_lib.h2_matvec_static(ctypes.byref(d), int(D_colidx.numel()), nv, _ptr(X), ldx, _ptr(Y), ldy,
-                                 _stream_ptr(stream)))
+    nd = int(D_colidx.numel()) if n_dense_blocks is None else int(n_dense_blocks)
+    _check(_lib.h2_matvec_static(ctypes.byref(d), nd, nv, _ptr(X), ldx, _ptr(Y), ldy, _stream_ptr(stream)))
     return y
+
+
+def matvec_static_check(stream=None):
+    """Raise H2Error (H2_ERR_INVALID) if a static product since the last check found a malformed
+    description; synchronizes the stream and clears the error."""
+    _check(_lib.h2_matvec_static_check(_stream_ptr(stream)))

@@ -9,12 +9,19 @@
 // loads the library holds until the process exits.
 //
 // It is one kernel launched as a single CTA: the product's phases run in
-// order inside it, separated by __syncthreads. It is written for correctness
-// and small matrices, not speed.
+// order inside it, separated by __syncthreads, in native FP64 arithmetic
+// (any finite FP64 values). It is written for correctness and small
+// matrices, not speed. Before it touches the scratch it checks the structure
+// arrays it indexes with (leaf offsets, block row pointers, column indices,
+// the dense block count); a malformed description sets a sticky error word
+// in the scratch, leaves y untouched, and h2_matvec_static_check reports it.
+#include <atomic>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 
-#include "df64.cuh"
+#include <cuda_runtime.h>
+
 #include "h2.h"
 
 // shared with h2_last_error (defined in h2_api.cu)
@@ -22,38 +29,31 @@ void h2_internal_set_error(const char* msg);
 
 namespace {
 
-// 16 MiB of scratch: the xhat and yhat vector trees and the dense-block offsets.
+// 16 MiB of scratch: a control block, the xhat and yhat vector trees and the dense-block offsets.
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+constexpr size_t kControlBytes = 256;                     // [0]: error word (sticky until checked)
+constexpr int64_t kStaticMaxDenseBlocks = (int64_t)1 << 20;
+constexpr int kStaticMaxRank = 64, kStaticMaxLeaf = 64;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kStaticWarps = 32;
 constexpr int kMaxDevices = 64;
 
-void* g_scratch_ptr[kMaxDevices] = {nullptr};  // device address of g_static_scratch, per device
+std::atomic<void*> g_scratch_ptr[kMaxDevices];  // device address of g_static_scratch, per device (null until looked up)
 
 h2_status fail_static(h2_status st, const char* msg) {
   h2_internal_set_error(msg);
   return st;
 }
 
-// (s, c) += a * x for a double-float x (xh, xl) and an FP64 matrix entry a
-__device__ __forceinline__ void acc(float& s, float& c, double a, float2 x) {
-  float ah, al;
-  h2::split_f64(a, ah, al);
-  h2::df_fma(s, c, ah, al, x.x, x.y);
-}
-
-// warp-wide sum of a double-float value; every lane gets the total
-__device__ __forceinline__ void warp_sum(float& s, float& c) {
-  for (int off = 16; off > 0; off >>= 1) {
-    const float s2 = __shfl_xor_sync(0xFFFFFFFFu, s, off);
-    const float c2 = __shfl_xor_sync(0xFFFFFFFFu, c, off);
-    h2::df_add(s, c, s2, c2);
-  }
+// warp-wide sum; every lane gets the total
+__device__ __forceinline__ double warp_sum(double s) {
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  return s;
 }
 
 struct StaticArgs {
-  int64_t n;
+  int64_t n, n_dense_blocks;
   int q, k, nv, symmetric;
   const int64_t* leaf_offset;
   const double *U, *V, *E, *F;
@@ -65,22 +65,64 @@ struct StaticArgs {
   int64_t ldx;
   double* y;
   int64_t ldy;
-  float2* xhat;  // scratch: [node][v][k]
-  float2* yhat;  // scratch: [node][v][k]
-  int64_t* doff; // scratch: dense block offsets
+  int* err;       // scratch: sticky error word
+  double* xhat;   // scratch: [node][v][k]
+  double* yhat;   // scratch: [node][v][k]
+  int64_t* doff;  // scratch: dense block offsets [n_dense_blocks + 1]
 };
+
+// level of heap node h
+__device__ __forceinline__ int node_level(int64_t h) { return 63 - __clzll(h + 1); }
+
+// The structure arrays the kernel indexes with must describe a tree of depth q
+// over n points, leaf sizes 1..64, block rows with non-decreasing pointers
+// that start at 0, coupling columns on the row's level, dense columns among
+// the leaves and exactly n_dense_blocks dense blocks.
+__device__ bool structure_ok(const StaticArgs& a, int* bad) {
+  const int64_t leaves = (int64_t)1 << a.q, n_nodes = ((int64_t)2 << a.q) - 1;
+  if (threadIdx.x == 0) {
+    if (a.leaf_offset[0] != 0 || a.leaf_offset[leaves] != a.n || a.D_rowptr[0] != 0 ||
+        a.D_rowptr[leaves] != a.n_dense_blocks || a.S_rowptr[0] != 0)
+      *bad = 1;
+  }
+  for (int64_t i = threadIdx.x; i < leaves; i += blockDim.x) {
+    const int64_t s = a.leaf_offset[i + 1] - a.leaf_offset[i];
+    if (s < 1 || s > kStaticMaxLeaf || a.D_rowptr[i + 1] < a.D_rowptr[i]) *bad = 1;
+  }
+  for (int64_t r = threadIdx.x; r < n_nodes; r += blockDim.x)
+    if (a.S_rowptr[r + 1] < a.S_rowptr[r]) *bad = 1;
+  __syncthreads();
+  if (*bad) return false;
+  for (int64_t r = threadIdx.x; r < n_nodes; r += blockDim.x) {
+    const int l = node_level(r);
+    const int64_t first = ((int64_t)1 << l) - 1, last = ((int64_t)2 << l) - 2;
+    for (int32_t b = a.S_rowptr[r]; b < a.S_rowptr[r + 1]; b++)
+      if (a.S_colidx[b] < first || a.S_colidx[b] > last) *bad = 1;
+  }
+  for (int64_t b = threadIdx.x; b < a.n_dense_blocks; b += blockDim.x)
+    if (a.D_colidx[b] < 0 || a.D_colidx[b] >= leaves) *bad = 1;
+  __syncthreads();
+  return *bad == 0;
+}
 
 // One CTA computes y = A^H x: leaf projection and upsweep (Eq. 2), coupling
 // (Eq. 3), downsweep (Eq. 5), leaf expansion (Eq. 4) and the dense blocks.
 // Every dot product is spread over a warp's lanes and reduced with shuffles.
 __global__ void __launch_bounds__(kStaticWarps * 32) k_matvec_static(StaticArgs a) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  if (!structure_ok(a, &bad)) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    return;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k = a.k, nv = a.nv;
   const int64_t leaves = (int64_t)1 << a.q, n_nodes = ((int64_t)2 << a.q) - 1, leaf0 = leaves - 1;
   const double* V = a.symmetric ? a.U : a.V;
   const double* F = a.symmetric ? a.E : a.F;
 
-  // dense block offsets (serial prefix sum by thread 0; the sizes are small by construction)
+  // dense block offsets (serial prefix sum by thread 0; n_dense_blocks = D_rowptr[2^q] was checked)
   if (threadIdx.x == 0) {
     int64_t off = 0;
     for (int64_t i = 0; i < leaves; i++)
@@ -95,10 +137,10 @@ __global__ void __launch_bounds__(kStaticWarps * 32) k_matvec_static(StaticArgs 
     const int64_t off = a.leaf_offset[j], sj = a.leaf_offset[j + 1] - off;
     for (int v = 0; v < nv; v++)
       for (int nu = 0; nu < k; nu++) {
-        float s = 0.f, c = 0.f;
-        for (int64_t r = lane; r < sj; r += 32) acc(s, c, V[off * k + r + sj * nu], h2::f64_to_df(a.x[v * a.ldx + off + r]));
-        warp_sum(s, c);
-        if (lane == 0) a.xhat[((leaf0 + j) * nv + v) * k + nu] = h2::df_norm(s, c);
+        double s = 0.0;
+        for (int64_t r = lane; r < sj; r += 32) s = fma(V[off * k + r + sj * nu], a.x[v * a.ldx + off + r], s);
+        s = warp_sum(s);
+        if (lane == 0) a.xhat[((leaf0 + j) * nv + v) * k + nu] = s;
       }
   }
   __syncthreads();
@@ -109,14 +151,14 @@ __global__ void __launch_bounds__(kStaticWarps * 32) k_matvec_static(StaticArgs 
       const int64_t p = pfirst + t;
       for (int v = 0; v < nv; v++)
         for (int nu = 0; nu < k; nu++) {
-          float s = 0.f, c = 0.f;
+          double s = 0.0;
           for (int ci = 1; ci <= 2; ci++) {
             const int64_t ch = 2 * p + ci;
             for (int mu = lane; mu < k; mu += 32)
-              acc(s, c, F[(ch - 1) * k * k + mu + (int64_t)k * nu], a.xhat[(ch * nv + v) * k + mu]);
+              s = fma(F[(ch - 1) * k * k + mu + (int64_t)k * nu], a.xhat[(ch * nv + v) * k + mu], s);
           }
-          warp_sum(s, c);
-          if (lane == 0) a.xhat[(p * nv + v) * k + nu] = h2::df_norm(s, c);
+          s = warp_sum(s);
+          if (lane == 0) a.xhat[(p * nv + v) * k + nu] = s;
         }
     }
     __syncthreads();
@@ -125,14 +167,14 @@ __global__ void __launch_bounds__(kStaticWarps * 32) k_matvec_static(StaticArgs 
   for (int64_t i = warp; i < n_nodes; i += kStaticWarps)
     for (int v = 0; v < nv; v++)
       for (int nu = 0; nu < k; nu++) {
-        float s = 0.f, c = 0.f;
+        double s = 0.0;
         for (int32_t b = a.S_rowptr[i]; b < a.S_rowptr[i + 1]; b++) {
           const int64_t col = a.S_colidx[b];
           for (int mu = lane; mu < k; mu += 32)
-            acc(s, c, a.S_val[(int64_t)b * k * k + nu + (int64_t)k * mu], a.xhat[(col * nv + v) * k + mu]);
+            s = fma(a.S_val[(int64_t)b * k * k + nu + (int64_t)k * mu], a.xhat[(col * nv + v) * k + mu], s);
         }
-        warp_sum(s, c);
-        if (lane == 0) a.yhat[(i * nv + v) * k + nu] = h2::df_norm(s, c);
+        s = warp_sum(s);
+        if (lane == 0) a.yhat[(i * nv + v) * k + nu] = s;
       }
   __syncthreads();
   // downsweep: yhat_c[mu] += sum_nu E_c[mu, nu] yhat_parent[nu]
@@ -142,15 +184,11 @@ __global__ void __launch_bounds__(kStaticWarps * 32) k_matvec_static(StaticArgs 
       const int64_t ch = cfirst + t, par = (ch - 1) / 2;
       for (int v = 0; v < nv; v++)
         for (int mu = 0; mu < k; mu++) {
-          float s = 0.f, c = 0.f;
+          double s = 0.0;
           for (int nu = lane; nu < k; nu += 32)
-            acc(s, c, a.E[(ch - 1) * k * k + mu + (int64_t)k * nu], a.yhat[(par * nv + v) * k + nu]);
-          warp_sum(s, c);
-          if (lane == 0) {
-            const float2 old = a.yhat[(ch * nv + v) * k + mu];
-            h2::df_add(s, c, old.x, old.y);
-            a.yhat[(ch * nv + v) * k + mu] = h2::df_norm(s, c);
-          }
+            s = fma(a.E[(ch - 1) * k * k + mu + (int64_t)k * nu], a.yhat[(par * nv + v) * k + nu], s);
+          s = warp_sum(s);
+          if (lane == 0) a.yhat[(ch * nv + v) * k + mu] += s;
         }
     }
     __syncthreads();
@@ -160,19 +198,40 @@ __global__ void __launch_bounds__(kStaticWarps * 32) k_matvec_static(StaticArgs 
     const int64_t off = a.leaf_offset[i], si = a.leaf_offset[i + 1] - off;
     for (int v = 0; v < nv; v++)
       for (int64_t r = 0; r < si; r++) {
-        float s = 0.f, c = 0.f;
-        for (int nu = lane; nu < k; nu += 32)
-          acc(s, c, a.U[off * k + r + si * nu], a.yhat[((leaf0 + i) * nv + v) * k + nu]);
+        double s = 0.0;
+        for (int nu = lane; nu < k; nu += 32) s = fma(a.U[off * k + r + si * nu], a.yhat[((leaf0 + i) * nv + v) * k + nu], s);
         for (int32_t b = a.D_rowptr[i]; b < a.D_rowptr[i + 1]; b++) {
           const int32_t j = a.D_colidx[b];
           const int64_t offj = a.leaf_offset[j], sj = a.leaf_offset[j + 1] - offj;
-          for (int64_t cc = lane; cc < sj; cc += 32)
-            acc(s, c, a.D_val[a.doff[b] + r + si * cc], h2::f64_to_df(a.x[v * a.ldx + offj + cc]));
+          for (int64_t cc = lane; cc < sj; cc += 32) s = fma(a.D_val[a.doff[b] + r + si * cc], a.x[v * a.ldx + offj + cc], s);
         }
-        warp_sum(s, c);
-        if (lane == 0) a.y[v * a.ldy + off + r] = h2::df_to_f64(s, c);
+        s = warp_sum(s);
+        if (lane == 0) a.y[v * a.ldy + off + r] = s;
       }
   }
+}
+
+// device address of the scratch on the current device (looked up once per device)
+h2_status scratch_base(unsigned char** base) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_static(H2_ERR_CUDA, "cudaGetDevice failed");
+  if (dev < 0 || dev >= kMaxDevices) {
+    char msg[128];
+    snprintf(msg, sizeof msg, "device %d: the allocation-free entry points support devices 0..%d", dev, kMaxDevices - 1);
+    return fail_static(H2_ERR_UNSUPPORTED, msg);
+  }
+  void* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {  // once per device, with that device current; concurrent first calls store the same address
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail_static(H2_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
+    }
+    g_scratch_ptr[dev].store(p, std::memory_order_release);
+  }
+  *base = (unsigned char*)p;
+  return H2_OK;
 }
 
 }  // namespace
@@ -185,33 +244,29 @@ h2_status h2_matvec_static(const h2_desc* d, int64_t n_dense_blocks, int32_t nv,
   if (!d || !x || !y) return fail_static(H2_ERR_INVALID, "NULL desc or vector");
   if (nv < 1 || d->n < 1 || d->rank < 1 || d->depth < 0 || d->depth > 24 || n_dense_blocks < 0)
     return fail_static(H2_ERR_INVALID, "invalid size (nv, n, rank, depth or dense block count)");
+  if (d->rank > kStaticMaxRank) return fail_static(H2_ERR_UNSUPPORTED, "rank above 64");
+  if (n_dense_blocks > kStaticMaxDenseBlocks) return fail_static(H2_ERR_UNSUPPORTED, "more than 2^20 dense blocks");
   if (ldx < d->n || ldy < d->n) return fail_static(H2_ERR_INVALID, "leading dimension below n");
   if (d->storage != H2_FP64) return fail_static(H2_ERR_UNSUPPORTED, "only FP64 storage");
-  if (!d->leaf_offset || !d->U || !d->E || !d->S_rowptr || !d->D_rowptr || (!d->symmetric && (!d->V || !d->F)))
+  if (!d->leaf_offset || !d->U || !d->E || !d->S_rowptr || !d->D_rowptr || (!d->symmetric && (!d->V || !d->F)) ||
+      (n_dense_blocks > 0 && (!d->D_colidx || !d->D_val)))
     return fail_static(H2_ERR_INVALID, "NULL array in desc");
+  // scratch need, one factor at a time so nothing overflows: control + 2 trees + offsets
   const int64_t n_nodes = ((int64_t)2 << d->depth) - 1;
-  const int64_t tree = n_nodes * nv * d->rank * (int64_t)sizeof(float2);
-  const int64_t need = 2 * tree + (n_dense_blocks + 1) * (int64_t)sizeof(int64_t);
-  if (need > (int64_t)kStaticScratchBytes)
+  const int64_t per_vector = n_nodes * d->rank * (int64_t)sizeof(double);  // <= 2^25 * 64 * 8
+  const int64_t room = (int64_t)kStaticScratchBytes - (int64_t)kControlBytes - (n_dense_blocks + 1) * (int64_t)sizeof(int64_t);
+  if (room < 0 || (int64_t)nv > room / (2 * per_vector))
     return fail_static(H2_ERR_UNSUPPORTED,
                        "the product needs more scratch than the static 16 MiB: "
-                       "2 * (2^(q+1) - 1) * nv * k * 8 + (dense blocks + 1) * 8 bytes must fit");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail_static(H2_ERR_CUDA, "cudaGetDevice failed");
-  if (!g_scratch_ptr[dev]) {  // once per device, with that device current
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail_static(H2_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
-    }
-    g_scratch_ptr[dev] = p;
-  }
-  unsigned char* base = (unsigned char*)g_scratch_ptr[dev];
+                       "256 + 2 * (2^(q+1) - 1) * nv * k * 8 + (dense blocks + 1) * 8 bytes must fit");
+  const int64_t tree = per_vector * nv;
+  unsigned char* base = nullptr;
+  h2_status st = scratch_base(&base);
+  if (st != H2_OK) return st;
   StaticArgs a;
   std::memset(&a, 0, sizeof a);
   a.n = d->n;
+  a.n_dense_blocks = n_dense_blocks;
   a.q = d->depth;
   a.k = d->rank;
   a.nv = nv;
@@ -231,12 +286,37 @@ h2_status h2_matvec_static(const h2_desc* d, int64_t n_dense_blocks, int32_t nv,
   a.ldx = ldx;
   a.y = y;
   a.ldy = ldy;
-  a.xhat = (float2*)base;
-  a.yhat = (float2*)(base + tree);
-  a.doff = (int64_t*)(base + 2 * tree);
+  a.err = (int*)base;
+  a.xhat = (double*)(base + kControlBytes);
+  a.yhat = (double*)(base + kControlBytes + tree);
+  a.doff = (int64_t*)(base + kControlBytes + 2 * tree);
   k_matvec_static<<<1, kStaticWarps * 32, 0, (cudaStream_t)stream>>>(a);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_static(H2_ERR_CUDA, "kernel launch failed");
+  return H2_OK;
+}
+
+h2_status h2_matvec_static_check(void* stream) {
+  h2_internal_set_error("");
+  unsigned char* base = nullptr;
+  h2_status st = scratch_base(&base);
+  if (st != H2_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int err = 0;
+  if (cudaMemcpyAsync(&err, base, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return fail_static(H2_ERR_CUDA, "reading the error word of the static product failed");
+  }
+  if (err) {
+    if (cudaMemsetAsync(base, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      return fail_static(H2_ERR_CUDA, "clearing the error word of the static product failed");
+    }
+    return fail_static(H2_ERR_INVALID,
+                       "a static product since the last check found a malformed description (leaf offsets, block "
+                       "row pointers, column indices or the dense block count); its y was left untouched");
+  }
   return H2_OK;
 }
 
