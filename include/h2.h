@@ -55,7 +55,12 @@ typedef enum {
  */
 typedef enum {
   H2_FP64 = 0,          /* plain form: FP64 storage; products in double-float
-                           (pairs of FP32 with error-free transformations, 46+ bits) */
+                           (pairs of FP32 with error-free transformations, 46+ bits).
+                           Any finite FP64 values: every block and every vector
+                           enters the float pairs scaled by a power of two chosen
+                           from bounds of the product's intermediates, so no
+                           float overflows; entries below 2^-103 times their
+                           output's bound (and FP64 subnormals) count as zero */
   H2_FP16_SCALED = 2,   /* IEEE binary16 codes + per-block FP32 scale, FP32 arithmetic */
   H2_BF16_SCALED = 3,   /* bfloat16 codes + per-block FP32 scale, FP32 arithmetic */
   H2_INT16_SCALED = 4   /* int16 codes + per-block FP32 scale, FP32 arithmetic */
@@ -123,8 +128,8 @@ typedef struct {
  * memory until h2_destroy.
  * Errors: H2_ERR_INVALID (NULL pointers, sizes, non-monotone row pointers,
  * column indices off the row's level or out of range, leaf sizes, non-finite
- * values or |value| >= 2^126, cover violation), H2_ERR_UNSUPPORTED (k > 64,
- * leaf size > 64), H2_ERR_OOM, H2_ERR_CUDA.
+ * values, |value| >= 2^126 in a scaled storage form, cover violation),
+ * H2_ERR_UNSUPPORTED (k > 64, leaf size > 64), H2_ERR_OOM, H2_ERR_CUDA.
  */
 h2_status h2_create(const h2_desc* d, h2_handle* out);
 

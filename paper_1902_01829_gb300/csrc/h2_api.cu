@@ -1,6 +1,7 @@
 // C ABI of the H^2 matrix-vector product library: validation, device layout,
 // launch sequence. See include/h2.h for the contract of each entry point.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -55,23 +56,165 @@ int level_of(int64_t node) {
   return l;
 }
 
-// true if some entry is zero or below 2^-103 in magnitude (the fast split needs 2^-103 <= |v|)
-bool has_tiny(const double* v, int64_t count) {
-  const double lim = std::ldexp(1.0, -103);
-  for (int64_t i = 0; i < count; i++)
-    if (!(std::fabs(v[i]) >= lim)) return true;
-  return false;
-}
-
-// values must be finite with |v| < 2^126 (the double-float split keeps the exponent in float range)
-bool values_ok(const double* v, int64_t count, int64_t* bad) {
-  const double lim = std::ldexp(1.0, 126);
+// values must be finite; the scaled storage forms (FP32 block scales) also need |v| < 2^126
+bool values_ok(const double* v, int64_t count, int64_t* bad, bool fp32_range = true) {
+  const double lim = fp32_range ? std::ldexp(1.0, 126) : HUGE_VAL;
   for (int64_t i = 0; i < count; i++)
     if (!(std::fabs(v[i]) < lim)) {
       *bad = i;
       return false;
     }
   return true;
+}
+
+// ---- range of the FP64 form (exponent offsets, see df64.cuh)
+//
+// With every vector scaled so that |x'| < 1, the host bounds each intermediate
+// of the product by the infinity norms of the blocks that produce it:
+//   xhat_leaf <= ||V_j^T||, xhat_p <= sum_c ||F_c^T|| xhat_c          (Alg. 2, Eq. 2)
+//   yhat_i <= sum_b ||S_b|| xhat_col(b) + ||E_i|| yhat_parent(i)       (Eq. 3, Eq. 5)
+//   y(i) <= sum_b ||D_b|| + ||U_i|| yhat_i                              (Sec. 2.2, Eq. 4)
+// Each node's vector is held scaled by 2^-e (2^e >= its bound), and each block
+// enters its product split with the exponent offset that maps its input scale
+// to its output scale, so every float of the product stays at most about 1.
+// Logarithms (base 2) keep the bounds finite for any finite input.
+
+struct BlockStat {
+  double lnorm = -HUGE_VAL;  // log2 of the largest row sum of |a| (-inf for a zero block)
+  int emax = 0;              // frexp exponent of the largest |a| (0 for a zero block)
+  int emin = 0;              // frexp exponent of the smallest nonzero normal |a|
+  bool zero = false;         // some entry is zero or an FP64 subnormal
+};
+
+// rows x cols block with element (r, c) at a[r * rs + c * cs]
+BlockStat block_stat(const double* a, int64_t rows, int64_t cols, int64_t rs, int64_t cs) {
+  BlockStat st;
+  double mx = 0.0, mn = HUGE_VAL;
+  for (int64_t r = 0; r < rows; r++)
+    for (int64_t c = 0; c < cols; c++) {
+      const double v = std::fabs(a[r * rs + c * cs]);
+      if (!(v >= DBL_MIN)) st.zero = true;
+      else mn = std::min(mn, v);
+      mx = std::max(mx, v);
+    }
+  if (!(mx >= DBL_MIN)) {
+    st.zero = true;
+    return st;
+  }
+  std::frexp(mx, &st.emax);
+  std::frexp(mn, &st.emin);
+  double best = 0.0;
+  for (int64_t r = 0; r < rows; r++) {
+    double sum = 0.0;
+    for (int64_t c = 0; c < cols; c++) sum += std::ldexp(std::fabs(a[r * rs + c * cs]), -st.emax);
+    best = std::max(best, sum);
+  }
+  st.lnorm = st.emax + std::log2(best);
+  return st;
+}
+
+// log2(2^a + 2^b)
+double lse2(double a, double b) {
+  if (a == -HUGE_VAL) return b;
+  if (b == -HUGE_VAL) return a;
+  const double m = std::max(a, b);
+  return m + std::log2(std::exp2(a - m) + std::exp2(b - m));
+}
+
+// exponent e with 2^L <= 2^e (0 when the bound is zero)
+int exp_of_bound(double L) { return L == -HUGE_VAL ? 0 : (int)std::ceil(L); }
+
+// offset o for a block: the wanted one, raised so that |a'| = |a| 2^-o stays below 2^100
+// (that only acts on blocks whose input is zero by its bound)
+int block_offset(int want, const BlockStat& st) { return st.zero && st.lnorm == -HUGE_VAL ? 0 : std::max(want, st.emax - 100); }
+
+// some |a'| of the block is below 2^-103 (or zero): the kernel needs the zero-safe split
+bool needs_safe_split(const BlockStat& st, int o) { return st.zero || st.emin - 1 - o < -103; }
+
+struct Fp64Ranges {
+  std::vector<int32_t> oV, oF, oE, oS, oD, oU, eY;
+  std::vector<char> d_safe;
+  bool s_tiny = false;
+};
+
+Fp64Ranges fp64_ranges(const h2_desc* d, int64_t leaves, int64_t n_nodes, int64_t nS, int64_t nD,
+                       const std::vector<int64_t>& doff) {
+  const int q = d->depth, k = d->rank;
+  const int64_t kk = (int64_t)k * k, leaf0 = leaves - 1;
+  const double* V = d->symmetric ? d->U : d->V;
+  const double* F = d->symmetric ? d->E : d->F;
+  const int64_t* lo = d->leaf_offset;
+  std::vector<BlockStat> sV((size_t)leaves), sU((size_t)leaves), sF((size_t)n_nodes), sE((size_t)n_nodes),
+      sS((size_t)nS), sD((size_t)nD);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t j = 0; j < leaves; j++) {
+    const int64_t s = lo[j + 1] - lo[j];
+    sV[j] = block_stat(V + lo[j] * k, k, s, s, 1);  // V_j^T: rows nu
+    sU[j] = block_stat(d->U + lo[j] * k, s, k, 1, s);
+  }
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t c = 1; c < n_nodes; c++) {
+    sF[c] = block_stat(F + (c - 1) * kk, k, k, k, 1);  // F_c^T: rows nu
+    sE[c] = block_stat(d->E + (c - 1) * kk, k, k, 1, k);
+  }
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t b = 0; b < nS; b++) sS[b] = block_stat(d->S_val + b * kk, k, k, 1, k);
+  std::vector<int32_t> drow((size_t)nD);
+  for (int64_t r = 0; r < leaves; r++)
+    for (int32_t b = d->D_rowptr[r]; b < d->D_rowptr[r + 1]; b++) drow[b] = (int32_t)r;
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t b = 0; b < nD; b++) {
+    const int64_t si = lo[drow[b] + 1] - lo[drow[b]];
+    const int64_t sj = (doff[b + 1] - doff[b]) / si;
+    sD[b] = block_stat(d->D_val + doff[b], si, sj, 1, si);
+  }
+  // bounds (log2) of xhat, yhat and y rows
+  std::vector<double> bx((size_t)n_nodes, -HUGE_VAL), by((size_t)n_nodes, -HUGE_VAL), bY((size_t)leaves, -HUGE_VAL);
+  for (int64_t j = 0; j < leaves; j++) bx[leaf0 + j] = sV[j].lnorm;
+  for (int64_t p = leaf0 - 1; p >= 0; p--)
+    bx[p] = lse2(sF[2 * p + 1].lnorm + bx[2 * p + 1], sF[2 * p + 2].lnorm + bx[2 * p + 2]);
+  for (int64_t i = 0; i < n_nodes; i++)
+    for (int32_t b = d->S_rowptr[i]; b < d->S_rowptr[i + 1]; b++) by[i] = lse2(by[i], sS[b].lnorm + bx[d->S_colidx[b]]);
+  for (int64_t c = 1; c < n_nodes; c++) by[c] = lse2(by[c], sE[c].lnorm + by[(c - 1) / 2]);
+  for (int64_t j = 0; j < leaves; j++) {
+    for (int32_t b = d->D_rowptr[j]; b < d->D_rowptr[j + 1]; b++) bY[j] = lse2(bY[j], sD[b].lnorm);
+    bY[j] = lse2(bY[j], sU[j].lnorm + by[leaf0 + j]);
+  }
+  std::vector<int> ex((size_t)n_nodes), ey((size_t)n_nodes);
+  for (int64_t h = 0; h < n_nodes; h++) {
+    ex[h] = exp_of_bound(bx[h]);
+    ey[h] = exp_of_bound(by[h]);
+  }
+  Fp64Ranges R;
+  R.oV.resize((size_t)leaves);
+  R.oU.resize((size_t)leaves);
+  R.eY.resize((size_t)leaves);
+  R.oF.assign((size_t)n_nodes, 0);
+  R.oE.assign((size_t)n_nodes, 0);
+  R.oS.resize((size_t)nS);
+  R.oD.resize((size_t)nD);
+  R.d_safe.resize((size_t)nD);
+  for (int64_t j = 0; j < leaves; j++) {
+    R.eY[j] = exp_of_bound(bY[j]);
+    R.oV[j] = block_offset(ex[leaf0 + j], sV[j]);
+    R.oU[j] = block_offset(R.eY[j] - ey[leaf0 + j], sU[j]);
+  }
+  for (int64_t c = 1; c < n_nodes; c++) {
+    const int64_t p = (c - 1) / 2;
+    R.oF[c] = block_offset(ex[p] - ex[c], sF[c]);
+    R.oE[c] = block_offset(ey[c] - ey[p], sE[c]);
+  }
+  for (int64_t i = 0; i < n_nodes; i++)
+    for (int32_t b = d->S_rowptr[i]; b < d->S_rowptr[i + 1]; b++) {
+      R.oS[b] = block_offset(ey[i] - ex[d->S_colidx[b]], sS[b]);
+      if (needs_safe_split(sS[b], R.oS[b])) R.s_tiny = true;
+    }
+  for (int64_t b = 0; b < nD; b++) {
+    R.oD[b] = block_offset(R.eY[drow[b]], sD[b]);
+    R.d_safe[b] = needs_safe_split(sD[b], R.oD[b]);
+  }
+  (void)q;
+  return R;
 }
 
 // every (row leaf, column leaf) pair covered exactly once by a dense block or
@@ -159,15 +302,19 @@ h2_status validate(const h2_desc* d, bool s_values, int64_t* nS, int64_t* nD, in
     }
   *nDval = dv;
   int64_t bad = 0;
-  if (!values_ok(d->U, d->n * k, &bad)) return fail(H2_ERR_INVALID, "U[%lld] is not finite or too large", (long long)bad);
-  if (!values_ok(d->E, (n_nodes - 1) * k * k, &bad)) return fail(H2_ERR_INVALID, "E[%lld] is not finite or too large", (long long)bad);
+  const bool f32 = d->storage != H2_FP64;  // FP64: any finite value; scaled forms: |v| < 2^126
+  if (!values_ok(d->U, d->n * k, &bad, f32)) return fail(H2_ERR_INVALID, "U[%lld] is not finite or too large", (long long)bad);
+  if (!values_ok(d->E, (n_nodes - 1) * k * k, &bad, f32))
+    return fail(H2_ERR_INVALID, "E[%lld] is not finite or too large", (long long)bad);
   if (!d->symmetric) {
-    if (!values_ok(d->V, d->n * k, &bad)) return fail(H2_ERR_INVALID, "V[%lld] is not finite or too large", (long long)bad);
-    if (!values_ok(d->F, (n_nodes - 1) * k * k, &bad)) return fail(H2_ERR_INVALID, "F[%lld] is not finite or too large", (long long)bad);
+    if (!values_ok(d->V, d->n * k, &bad, f32)) return fail(H2_ERR_INVALID, "V[%lld] is not finite or too large", (long long)bad);
+    if (!values_ok(d->F, (n_nodes - 1) * k * k, &bad, f32))
+      return fail(H2_ERR_INVALID, "F[%lld] is not finite or too large", (long long)bad);
   }
-  if (s_values && *nS && !values_ok(d->S_val, *nS * k * k, &bad))
+  if (s_values && *nS && !values_ok(d->S_val, *nS * k * k, &bad, f32))
     return fail(H2_ERR_INVALID, "S_val[%lld] is not finite or too large", (long long)bad);
-  if (*nD && !values_ok(d->D_val, dv, &bad)) return fail(H2_ERR_INVALID, "D_val[%lld] is not finite or too large", (long long)bad);
+  if (*nD && !values_ok(d->D_val, dv, &bad, f32))
+    return fail(H2_ERR_INVALID, "D_val[%lld] is not finite or too large", (long long)bad);
   if (d->check_cover) return check_cover(d, leaves);
   return H2_OK;
 }
@@ -319,6 +466,10 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
   T.xhat = h->xhat;
   T.yhat = h->yhat;
   T.ticket = h->ticket;
+  T.oV = h->oV;
+  T.oF = h->oF;
+  T.oE = h->oE;
+  T.vexp = h->vexp;
   T.k = k;
   T.kp = kp;
   T.LR = LR;
@@ -327,18 +478,19 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
   T.nv = nv;
   const unsigned tree_grid = 1u << h->tree_L, tree_threads = kTreeWarps * 32;
   cudaError_t me = mark(&h->prof, st);
+  k_vec_scale<<<kScaleBlocks, kScaleThreads, 0, st>>>(x, ldx, h->n, nv, h->vpart, h->vticket, h->vexp);
   k_upsweep_tree<RPL_K, NVB><<<tree_grid, tree_threads, 0, st>>>(T);
   if (me == cudaSuccess) me = mark(&h->prof, st);
   if (h->pair_rows) {
     constexpr int CB = NVB <= 2 ? 4 : (NVB <= 4 ? 2 : 1);
     if (h->s_tiny)
-      k_coupling<NVB, CB, true><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, h->n_nodes, nv,
+      k_coupling<NVB, CB, true><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Sco, k, kp, h->n_nodes, nv,
                                                                   h->xhat, h->yhat);
     else
-      k_coupling<NVB, CB, false><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, h->n_nodes, nv,
+      k_coupling<NVB, CB, false><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Sco, k, kp, h->n_nodes, nv,
                                                                    h->xhat, h->yhat);
   } else {
-    k_coupling_generic<RPL_K, NVB><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Scol, k, kp, LR, h->n_nodes,
+    k_coupling_generic<RPL_K, NVB><<<grid(h->n_nodes), wb, 0, st>>>(h->smat, kkp, h->Srow, h->Sco, k, kp, LR, h->n_nodes,
                                                                      nv, h->xhat, h->yhat);
   }
   if (me == cudaSuccess) me = mark(&h->prof, st);
@@ -353,6 +505,7 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
   P.nv = nv;
   P.y = y;
   P.ldy = ldy;
+  P.vexp = h->vexp;
   P.err = h->err;
   P.budget = h->budget;
   P.inject = h->inject;
@@ -362,7 +515,7 @@ h2_status run_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double*
     h->budget = kWaitBudget;
   }
   if (me == cudaSuccess) me = mark(&h->prof, st);
-  h->prof.launches += 4;
+  h->prof.launches += 5;
   if (me != cudaSuccess) return fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(H2_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
@@ -430,6 +583,7 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
     if ((st = upload(h, &h->E, d->E, (h->n_nodes - 1) * kk)) != H2_OK) return st;
   }
 
+  Fp64Ranges R;
   {  // dense blocks + U, each padded to an even count of doubles, and their item list
     std::vector<int64_t> doff((size_t)h->nD + 1, 0), dpo((size_t)h->nD + 1, 0), upo((size_t)h->leaves + 1, 0);
     for (int64_t r = 0, b = 0; r < h->leaves; r++)
@@ -440,6 +594,10 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
       }
     for (int64_t i = 0; i < h->leaves; i++) upo[i + 1] = upo[i] + even((lo[i + 1] - lo[i]) * k);
     const int64_t dtot = dpo[h->nD], total = dtot + upo[h->leaves];
+    R = fp64_ranges(d, h->leaves, h->n_nodes, h->nS, h->nD, doff);
+    for (const std::vector<int32_t>* v : {&R.oV, &R.oF, &R.oE, &R.oS, &R.oD, &R.oU, &R.eY})
+      for (int32_t e : *v)
+        if (e < -h2::kItemExpMax || e > h2::kItemExpMax) return fail(H2_ERR_INVALID, "internal: exponent offset %d out of range", e);
     double* dm = nullptr;
     if ((st = dalloc(h, &dm, total)) != H2_OK) return st;
     h->dmat = (char*)dm;
@@ -485,7 +643,7 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
         it.shape = (unsigned)si | ((unsigned)sj << 8) | ((unsigned)even(sj) << 16) | (1u << 24);
         it.v_off = xp[j];
         it.row = (int)lo[i];
-        it.flags = has_tiny(d->D_val + doff[b], doff[b + 1] - doff[b]) ? h2::kItemFlagSafe : 0;
+        it.flags = (R.d_safe[b] ? h2::kItemFlagSafe : 0) | h2::item_pack_exp(R.oD[b], 0);
         items.push_back(it);
         bytes += it.m_bytes + 8 * sj;
       }
@@ -495,7 +653,7 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
       it.shape = (unsigned)si | ((unsigned)k << 8) | ((unsigned)h->kp << 16) | (1u << 24);
       it.v_off = (h->leaf0 + i) * h->kp;
       it.row = (int)lo[i];
-      it.flags = h2::kItemFlagLast | h2::kItemFlagSrc1 | h2::kItemFlagSafe;
+      it.flags = h2::kItemFlagLast | h2::kItemFlagSrc1 | h2::kItemFlagSafe | h2::item_pack_exp(R.oU[i], R.eY[i]);
       items.push_back(it);
       row_bytes[i] = bytes + it.m_bytes + 8 * h->kp + 16 * si;
     }
@@ -520,8 +678,20 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
       }
     }
     h->pair_rows = k >= 2 && k <= 64 && (k & (k - 1)) == 0;
-    h->s_tiny = h->nS > 0 && has_tiny(d->S_val, h->nS * kk);
+    h->s_tiny = R.s_tiny;
   }
+  if ((st = upload(h, &h->oV, R.oV.data(), h->leaves)) != H2_OK) return st;
+  if ((st = upload(h, &h->oF, R.oF.data(), h->n_nodes)) != H2_OK) return st;
+  if ((st = upload(h, &h->oE, R.oE.data(), h->n_nodes)) != H2_OK) return st;
+  {
+    std::vector<int2> sco((size_t)h->nS);
+    for (int64_t b = 0; b < h->nS; b++) sco[b] = make_int2(d->S_colidx[b], R.oS[b]);
+    if ((st = upload(h, &h->Sco, (const int2*)sco.data(), h->nS)) != H2_OK) return st;
+  }
+  if ((st = dalloc(h, &h->vexp, h2i::kPassVectors)) != H2_OK) return st;
+  if ((st = dalloc(h, &h->vpart, (int64_t)h2::kScaleBlocks * 16)) != H2_OK) return st;
+  if ((st = dalloc(h, &h->vticket, 1)) != H2_OK) return st;
+  CUDA_TRY(cudaMemset(h->vticket, 0, sizeof(unsigned)));
 
   if ((st = dalloc(h, &h->x2, xp[h->leaves] * kPassVectors)) != H2_OK) return st;
   if ((st = dalloc(h, &h->xhat, h->n_nodes * kPassVectors * h->kp)) != H2_OK) return st;

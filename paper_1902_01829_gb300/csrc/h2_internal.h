@@ -169,10 +169,19 @@ struct h2_matrix_s {
   double* smat = nullptr;     // coupling blocks, each padded to an even count of doubles
   int32_t* Srow = nullptr;
   int32_t* Scol = nullptr;
+  // FP64 form: exponent offsets (a' = a * 2^-o) of the blocks of V (per leaf), F, E (per node), and
+  // per coupling block its column node with its offset
+  int32_t* oV = nullptr;
+  int32_t* oF = nullptr;
+  int32_t* oE = nullptr;
+  int2* Sco = nullptr;
+  int* vexp = nullptr;                // per vector of the current pass: x scaled by 2^-vexp[v]
+  unsigned long long* vpart = nullptr;  // per-block maxima of the scale pass
+  unsigned* vticket = nullptr;        // last-block ticket of the scale pass, zero between products
   h2i::ItemList dense_items;
   h2i::MixedData mx;          // precision form (storage != H2_FP64)
   bool pair_rows = false;     // k = 2^j (j >= 1): the coupling kernel reads row pairs
-  bool s_tiny = true;         // some coupling entry is zero or below 2^-103
+  bool s_tiny = true;         // some coupling entry is zero or below 2^-103 after its block's offset
   int* err = nullptr;         // device error word (bounded waits)
   int* ticket = nullptr;      // upsweep climb counters, one per node
   int tree_L = 0;             // subtree root level of the fused tree kernels

@@ -10,6 +10,10 @@
 // broadcast, and products accumulate in double-float. Loads of several columns
 // are issued before any of them is used, so a warp keeps many in flight.
 //
+// Range: every block is split with its exponent offset o (a' = a * 2^-o, see
+// df64.cuh) and x is scaled per vector by 2^-vexp[v], so that x, xhat and yhat
+// hold values of magnitude at most about 1 (bounds computed by h2_create).
+//
 // Workspace layouts (float2 = double-float hi, lo; kp = k rounded up to even):
 //   x2    leaf j's chunk at xp_off[j] * nv: [v][spad_j] (spad = leaf size rounded up to even)
 //   xhat  [(node * nv + v) * kp + row]   vector trees of Sec. 4.2 - 4.4
@@ -25,7 +29,7 @@ constexpr int kWarps = 4;  // warps per CTA for the per-node kernels
 // rl + 32 r (r < RPL) and columns col = g, g + G, ... with G = 32 / LR groups.
 // RPL = 2 requires LR = 32 (R <= 64); RPL = 1 allows LR = 1 .. 32 (R <= LR).
 template <int RPL, int NVB, bool CG = false>
-__device__ __forceinline__ void warp_mv_impl(const double* __restrict__ A, int R, int C, int LR, const float2* xin,
+__device__ __forceinline__ void warp_mv_impl(const double* __restrict__ A, int o, int R, int C, int LR, const float2* xin,
                                              int64_t xstride, int nv, float (&s)[RPL][NVB], float (&c)[RPL][NVB], int lane) {
   constexpr int UB = (NVB <= 2) ? 8 : (NVB <= 4 ? 4 : 2);  // columns whose loads are issued together
   const int G = 32 / LR;
@@ -51,7 +55,7 @@ __device__ __forceinline__ void warp_mv_impl(const double* __restrict__ A, int R
 #pragma unroll
       for (int r = 0; r < RPL; r++) {
         float ah, al;
-        split_f64(a[u][r], ah, al);
+        split_f64(a[u][r], o, ah, al);
 #pragma unroll
         for (int v = 0; v < NVB; v++) df_fma(s[r][v], c[r][v], ah, al, xv[u][v].x, xv[u][v].y);
       }
@@ -61,9 +65,19 @@ __device__ __forceinline__ void warp_mv_impl(const double* __restrict__ A, int R
 
 // xin is read with plain loads: it may have been written earlier in the same kernel by this CTA
 template <int RPL, int NVB>
-__device__ __forceinline__ void warp_mv(const double* __restrict__ A, int R, int C, int LR, const float2* xin, int64_t xstride,
-                                        int nv, float (&s)[RPL][NVB], float (&c)[RPL][NVB], int lane) {
-  warp_mv_impl<RPL, NVB, false>(A, R, C, LR, xin, xstride, nv, s, c, lane);
+__device__ __forceinline__ void warp_mv(const double* __restrict__ A, int o, int R, int C, int LR, const float2* xin,
+                                        int64_t xstride, int nv, float (&s)[RPL][NVB], float (&c)[RPL][NVB], int lane) {
+  warp_mv_impl<RPL, NVB, false>(A, o, R, C, LR, xin, xstride, nv, s, c, lane);
+}
+
+// (S, C) += (s, c) elementwise, (s, c) = 0
+template <int RPL, int NVB>
+__device__ __forceinline__ void acc_fold(float (&S)[RPL][NVB], float (&C)[RPL][NVB], float (&s)[RPL][NVB],
+                                         float (&c)[RPL][NVB]) {
+#pragma unroll
+  for (int r = 0; r < RPL; r++)
+#pragma unroll
+    for (int v = 0; v < NVB; v++) df_fold(S[r][v], C[r][v], s[r][v], c[r][v]);
 }
 
 template <int RPL, int NVB>
@@ -128,6 +142,10 @@ struct TreeParams {
   float2* xhat;
   float2* yhat;
   int* ticket;             // one counter per node above level L, zero between products
+  const int* oV;           // leaf j: exponent offset of V_j (projection)
+  const int* oF;           // node h >= 1: exponent offset of F_h (upsweep into the parent)
+  const int* oE;           // node h >= 1: exponent offset of E_h (downsweep from the parent)
+  const int* vexp;         // per vector of the pass: x enters scaled by 2^-vexp[v]
   int k, kp, LR, q, L, nv;
 };
 
@@ -139,12 +157,14 @@ __device__ __forceinline__ void project_leaf(const TreeParams& P, int64_t j, int
   const int sj = (int)(P.leaf_off[j + 1] - off);
   const int spad = sj + (sj & 1);
   float2* x2j = P.x2 + P.xp_off[j] * P.nv;
-  for (int v = 0; v < P.nv; v++)
-    for (int a = lane; a < sj; a += 32) x2j[v * spad + a] = f64_to_df(P.x[v * P.ldx + off + a]);
+  for (int v = 0; v < P.nv; v++) {
+    const int sv = P.vexp[v];
+    for (int a = lane; a < sj; a += 32) x2j[v * spad + a] = f64_to_df(scale2(P.x[v * P.ldx + off + a], -sv));
+  }
   __syncwarp();
   float s[RPL][NVB], c[RPL][NVB];
   acc_zero(s, c);
-  warp_mv<RPL, NVB>(P.Vt + off * P.k, P.k, sj, P.LR, x2j, spad, P.nv, s, c, lane);
+  warp_mv<RPL, NVB>(P.Vt + off * P.k, P.oV[j], P.k, sj, P.LR, x2j, spad, P.nv, s, c, lane);
   group_reduce(s, c, P.LR);
   store_node<RPL, NVB, false>(P.xhat + (leaf0 + j) * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, s, c, lane);
 }
@@ -156,8 +176,8 @@ __device__ __forceinline__ void up_node(const TreeParams& P, int64_t p, int lane
   acc_zero(s, c);
   for (int ci = 1; ci <= 2; ci++) {
     const int64_t ch = 2 * p + ci;
-    warp_mv_impl<RPL, NVB, CG>(P.Ft + (ch - 1) * P.k * P.k, P.k, P.k, P.LR, P.xhat + ch * P.nv * P.kp, P.kp, P.nv, s, c,
-                               lane);
+    warp_mv_impl<RPL, NVB, CG>(P.Ft + (ch - 1) * P.k * P.k, P.oF[ch], P.k, P.k, P.LR, P.xhat + ch * P.nv * P.kp, P.kp,
+                               P.nv, s, c, lane);
   }
   group_reduce(s, c, P.LR);
   store_node<RPL, NVB, false>(P.xhat + p * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, s, c, lane);
@@ -205,7 +225,7 @@ template <int RPL, int NVB>
 __device__ __forceinline__ void down_node(const TreeParams& P, int64_t ch, const float2* ypar, int lane) {
   float s[RPL][NVB], c[RPL][NVB];
   acc_zero(s, c);
-  warp_mv<RPL, NVB>(P.E + (ch - 1) * P.k * P.k, P.k, P.k, P.LR, ypar, P.kp, P.nv, s, c, lane);
+  warp_mv<RPL, NVB>(P.E + (ch - 1) * P.k * P.k, P.oE[ch], P.k, P.k, P.LR, ypar, P.kp, P.nv, s, c, lane);
   group_reduce(s, c, P.LR);
   store_node<RPL, NVB, true>(P.yhat + ch * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, s, c, lane);
 }
@@ -231,7 +251,7 @@ __global__ void __launch_bounds__(kTreeWarps * 32) k_downsweep_tree(TreeParams P
       const int64_t a = ((root + 1) >> (P.L - l)) - 1;
       float s[RPL][NVB], c[RPL][NVB];
       acc_zero(s, c);
-      warp_mv<RPL, NVB>(P.E + (a - 1) * P.k * P.k, P.k, P.k, P.LR, &path[cur][0][0], 64, P.nv, s, c, lane);
+      warp_mv<RPL, NVB>(P.E + (a - 1) * P.k * P.k, P.oE[a], P.k, P.k, P.LR, &path[cur][0][0], 64, P.nv, s, c, lane);
       group_reduce(s, c, P.LR);
       if (lane < P.LR) {
 #pragma unroll
@@ -272,11 +292,15 @@ __global__ void __launch_bounds__(kTreeWarps * 32) k_downsweep_tree(TreeParams P
 // take columns g, g + G, ... The row's blocks are walked in batches of CB
 // columns per lane, two batches in flight: the next batch's matrix and xhat
 // loads are issued before the current batch is multiplied. Blocks are padded
-// to kkp doubles. Every node row is written (zero when it has no blocks).
-// SAFE: some coupling entry is zero or below 2^-103 (zero-safe split).
+// to kkp doubles; Sco[b] = (column node, exponent offset) of block b. Every node row
+// is written (zero when it has no blocks). A lane's products form chains of
+// at most 64 (kFoldProducts) that are folded into a long-term pair, so the
+// FP32 sum of the small parts never runs over a whole row.
+// SAFE: some coupling entry is zero or below 2^-103 after its offset (zero-safe split).
+constexpr int kFoldProducts = 64;
 template <int NVB, int CB, bool SAFE>
 __global__ void __launch_bounds__(kWarps * 32) k_coupling(const double* __restrict__ S, int kkp,
-                                                        const int32_t* __restrict__ Srow, const int32_t* __restrict__ Scol,
+                                                        const int32_t* __restrict__ Srow, const int2* __restrict__ Sco,
                                                         int k, int kp, int64_t n_nodes, int nv,
                                                         const float2* __restrict__ xhat, float2* __restrict__ yhat) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -289,18 +313,20 @@ __global__ void __launch_bounds__(kWarps * 32) k_coupling(const double* __restri
   const int ncb = (cpl + CB - 1) / CB;  // batches per block
   const int32_t b0 = Srow[i];
   const int nbatch = (Srow[i + 1] - b0) * ncb;
-  float s[2][NVB], c[2][NVB];
-#pragma unroll
-  for (int r = 0; r < 2; r++)
-#pragma unroll
-    for (int v = 0; v < NVB; v++) s[r][v] = c[r][v] = 0.f;
+  constexpr int FB = kFoldProducts / CB;  // batches per chain
+  float s[2][NVB], c[2][NVB], S2[2][NVB], C2[2][NVB];
+  acc_zero(s, c);
+  acc_zero(S2, C2);
 
   double2 a0[CB], a1[CB];
   float2 x0[CB][NVB], x1[CB][NVB];
-  auto load = [&](int bt, double2(&a)[CB], float2(&xv)[CB][NVB]) {
+  int o0 = 0, o1 = 0;
+  auto load = [&](int bt, double2(&a)[CB], float2(&xv)[CB][NVB], int& o) {
     const int b = bt / ncb, cb = bt - b * ncb;
     const double* A = S + (int64_t)(b0 + b) * kkp;
-    const float2* X = xhat + (int64_t)__ldg(Scol + b0 + b) * nv * kp;
+    const int2 co = __ldg(Sco + b0 + b);
+    const float2* X = xhat + (int64_t)co.x * nv * kp;
+    o = co.y;
 #pragma unroll
     for (int u = 0; u < CB; u++) {
       const int col = g + G * (cb * CB + u);
@@ -310,16 +336,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_coupling(const double* __restri
       for (int v = 0; v < NVB; v++) xv[u][v] = (ok && v < nv) ? __ldg(X + v * kp + col) : make_float2(0.f, 0.f);
     }
   };
-  auto compute = [&](const double2(&a)[CB], const float2(&xv)[CB][NVB]) {
+  auto compute = [&](const double2(&a)[CB], const float2(&xv)[CB][NVB], int o) {
 #pragma unroll
     for (int u = 0; u < CB; u++) {
       float h0, l0, h1, l1;
       if (SAFE) {
-        split_f64(a[u].x, h0, l0);
-        split_f64(a[u].y, h1, l1);
+        split_f64(a[u].x, o, h0, l0);
+        split_f64(a[u].y, o, h1, l1);
       } else {
-        split_f64_fast(a[u].x, h0, l0);
-        split_f64_fast(a[u].y, h1, l1);
+        split_f64_fast(a[u].x, o, h0, l0);
+        split_f64_fast(a[u].y, o, h1, l1);
       }
 #pragma unroll
       for (int v = 0; v < NVB; v++) {
@@ -328,13 +354,22 @@ __global__ void __launch_bounds__(kWarps * 32) k_coupling(const double* __restri
       }
     }
   };
-  if (nbatch > 0) load(0, a0, x0);
+  if (nbatch > 0) load(0, a0, x0, o0);
   for (int bt = 0; bt < nbatch; bt += 2) {
-    if (bt + 1 < nbatch) load(bt + 1, a1, x1);
-    compute(a0, x0);
-    if (bt + 2 < nbatch) load(bt + 2, a0, x0);
-    if (bt + 1 < nbatch) compute(a1, x1);
+    if (bt + 1 < nbatch) load(bt + 1, a1, x1, o1);
+    compute(a0, x0, o0);
+    if (bt + 2 < nbatch) load(bt + 2, a0, x0, o0);
+    if (bt + 1 < nbatch) compute(a1, x1, o1);
+    if ((bt + 2) % FB == 0) acc_fold(S2, C2, s, c);
   }
+  acc_fold(S2, C2, s, c);
+#pragma unroll
+  for (int r = 0; r < 2; r++)
+#pragma unroll
+    for (int v = 0; v < NVB; v++) {
+      s[r][v] = S2[r][v];
+      c[r][v] = C2[r][v];
+    }
   // sum the column groups (lanes h, h + H, ...)
   for (int off = H; off < 32; off <<= 1) {
 #pragma unroll
@@ -357,22 +392,85 @@ __global__ void __launch_bounds__(kWarps * 32) k_coupling(const double* __restri
   }
 }
 
-// Any other k: the generic row mapping of warp_mv, one block at a time.
+// Any other k: the generic row mapping of warp_mv, one block at a time (each
+// block's chain folded into the row's long-term pair).
 template <int RPL, int NVB>
 __global__ void __launch_bounds__(kWarps * 32) k_coupling_generic(const double* __restrict__ S, int kkp,
                                                             const int32_t* __restrict__ Srow,
-                                                            const int32_t* __restrict__ Scol, int k, int kp, int LR,
+                                                            const int2* __restrict__ Sco, int k, int kp, int LR,
                                                             int64_t n_nodes, int nv, const float2* __restrict__ xhat,
                                                             float2* __restrict__ yhat) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * kWarps + warp;
   if (i >= n_nodes) return;
-  float s[RPL][NVB], c[RPL][NVB];
+  float s[RPL][NVB], c[RPL][NVB], S2[RPL][NVB], C2[RPL][NVB];
   acc_zero(s, c);
-  for (int32_t b = Srow[i]; b < Srow[i + 1]; b++)
-    warp_mv<RPL, NVB>(S + (int64_t)b * kkp, k, k, LR, xhat + (int64_t)Scol[b] * nv * kp, kp, nv, s, c, lane);
-  group_reduce(s, c, LR);
+  acc_zero(S2, C2);
+  for (int32_t b = Srow[i]; b < Srow[i + 1]; b++) {
+    const int2 co = Sco[b];
+    warp_mv<RPL, NVB>(S + (int64_t)b * kkp, co.y, k, k, LR, xhat + (int64_t)co.x * nv * kp, kp, nv, s, c, lane);
+    acc_fold(S2, C2, s, c);
+  }
+  group_reduce(S2, C2, LR);
+#pragma unroll
+  for (int r = 0; r < RPL; r++)
+#pragma unroll
+    for (int v = 0; v < NVB; v++) {
+      s[r][v] = S2[r][v];
+      c[r][v] = C2[r][v];
+    }
   store_node<RPL, NVB, false>(yhat + i * nv * kp, k, kp, LR, nv, s, c, lane);
+}
+
+// ---------------------------------------------------------------- per-vector scale
+// vexp[v] = s with max_i |x[i, v]| * 2^-s < 1 (frexp exponent; 0 for a zero or
+// non-finite maximum), so that the pass works on x * 2^-s. Each block writes
+// its maxima to partial[block][v]; the last block to finish (atomic ticket)
+// reduces them and resets the ticket for the next launch. A thread keeps
+// eight loads in flight; one round covers n = 2^20 on 152 blocks.
+constexpr int kScaleBlocks = 152, kScaleThreads = 1024, kScaleUnroll = 8;
+__device__ __forceinline__ unsigned long long abs_bits(double a) { return (unsigned long long)__double_as_longlong(fabs(a)); }
+__global__ void __launch_bounds__(kScaleThreads) k_vec_scale(const double* __restrict__ x, int64_t ldx, int64_t n, int nv,
+                                                            unsigned long long* partial, unsigned* ticket, int* vexp) {
+  __shared__ unsigned long long wmax[kScaleThreads / 32][16];
+  __shared__ int last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * kScaleThreads;
+  for (int v = 0; v < nv; v++) {
+    const double* xv = x + v * ldx;
+    unsigned long long m = 0;
+    int64_t i = (int64_t)blockIdx.x * kScaleThreads + threadIdx.x;
+    for (; i + (kScaleUnroll - 1) * stride < n; i += kScaleUnroll * stride) {
+      double a[kScaleUnroll];
+#pragma unroll
+      for (int u = 0; u < kScaleUnroll; u++) a[u] = __ldcs(xv + i + u * stride);
+#pragma unroll
+      for (int u = 0; u < kScaleUnroll; u++) m = max(m, abs_bits(a[u]));
+    }
+    for (; i < n; i += stride) m = max(m, abs_bits(__ldcs(xv + i)));
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
+    if (lane == 0) wmax[warp][v] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    unsigned long long m = 0;
+    for (int w = 0; w < kScaleThreads / 32; w++) m = max(m, wmax[w][threadIdx.x]);
+    partial[blockIdx.x * 16 + threadIdx.x] = m;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int v = warp; v < nv; v += kScaleThreads / 32) {
+    unsigned long long m = 0;
+#pragma unroll 4
+    for (int b = lane; b < (int)gridDim.x; b += 32) m = max(m, __ldcg(partial + b * 16 + v));
+    for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
+    if (lane == 0) vexp[v] = vec_exponent(m);
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
 }  // namespace h2

@@ -29,13 +29,21 @@ struct __align__(16) StreamItem {
   long long v_off;  // vector chunk offset, in float2 per vector slot
   int row;          // first point of the row leaf (y offset)
   int flags;        // bit 0: last item of its row; bit 1: vector chunk from the second source (yhat);
-                    // bit 2: the block holds zeros or magnitudes below 2^-103 (zero-safe split needed)
+                    // bit 2: the block holds zeros or magnitudes below 2^-103 after its offset (zero-safe split);
+                    // FP64 form: bits 4-17 the block's exponent offset, bits 18-31 (last item) the row's
+                    // output exponent (both signed 14-bit)
 };
 
 constexpr int kStageHeader = 128;
 constexpr int kStageMat = 32768;
 constexpr int kSmemLimit = 232448;  // opt-in shared memory per CTA on sm_103a
 constexpr int kItemFlagLast = 1, kItemFlagSrc1 = 2, kItemFlagSafe = 4;
+constexpr int kItemOffsetShift = 4, kItemRowExpShift = 18, kItemExpMax = 8191;  // 14-bit signed fields
+__host__ __device__ constexpr int item_offset(int flags) { return (int)((unsigned)flags << 14) >> 18; }
+__host__ __device__ constexpr int item_row_exp(int flags) { return flags >> kItemRowExpShift; }
+__host__ __device__ constexpr int item_pack_exp(int offset, int row_exp) {
+  return (int)(((unsigned)offset & 0x3FFFu) << kItemOffsetShift) | (int)((unsigned)row_exp << kItemRowExpShift);
+}
 
 // a stage holds one item: header, matrix block (<= 64 x 64 doubles), vector chunk (<= 64 x NVB float2)
 __host__ __device__ constexpr int stage_vec_bytes(int nvb) { return 512 * nvb; }
@@ -62,6 +70,7 @@ struct StreamParams {
   int nv;                // vectors of this pass (<= NVB)
   double* y;             // output
   long long ldy;
+  const int* vexp;       // per vector: the pass's x was scaled by 2^-vexp[v]
   int* err;              // device error word
   long long budget;      // clock64 cycles a single wait may take
   int inject;            // >= 0: CTA 0 withholds the copy of this local item (bounded-wait test)
@@ -184,6 +193,13 @@ __device__ __forceinline__ void stream_produce(const StreamParams& P, const Stre
 }
 
 // ---------------------------------------------------------------- dense near field + expansion
+// Each block is split with its item's exponent offset; the row's sum is
+// scaled by 2^(row exponent + vexp[v]) when it is written. A lane's
+// accumulator sets are folded every FI items (chains of about 64 products)
+// into its long-term pairs, which live in its own slots of the row-partial
+// area (red) rather than in registers. A fold inside a row happens only once
+// the previous row's partials have been consumed (tested without waiting, so
+// warps keep a row of slack); the fold at the row's end waits for that.
 template <int NVB, int CW>
 __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream(StreamParams P) {
   constexpr int NST = stream_stages(NVB, CW);
@@ -200,6 +216,9 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream(StreamParams 
     return;
   }
   const int nv = P.nv;
+  int* vexp_s = reinterpret_cast<int*>(const_cast<int*>(S.abort_flag)) + 1;  // [NVB], in the barrier area
+  if (threadIdx.x < NVB) vexp_s[threadIdx.x] = threadIdx.x < nv ? P.vexp[threadIdx.x] : 0;
+  asm volatile("bar.sync 1, %0;" ::"r"(CW * 32) : "memory");  // consumer warps only
   // lane owns rows 2 lane and 2 lane + 1 of every block; set u takes columns c0 + u, c0 + u + SETS, ...
   float s[SETS][2][NVB], c[SETS][2][NVB];
 #pragma unroll
@@ -208,14 +227,41 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream(StreamParams 
     for (int r = 0; r < 2; r++)
 #pragma unroll
       for (int v = 0; v < NVB; v++) s[u][r][v] = c[u][r][v] = 0.f;
+  constexpr int FI = 8 * SETS;  // items per chain: (64 / CW) / SETS products per item
   const int r0 = 2 * lane;
-  int rows_done = 0;
+  int rows_done = 0, chain = 0;
+  bool red_mine = false;  // this warp's red slots hold the current row's long-term pairs
+  // red slot of (v, rows r0 and r0 + 1): one float4 (s, c of row r0, then of row r0 + 1)
+  // fold; inside a row (row_end false) only if the slots are free already: returns false when it did not fold
+  auto fold = [&](bool row_end) -> bool {
+    if (!red_mine && rows_done > 0) {
+      if (!row_end) {
+        if (!__all_sync(0xFFFFFFFFu, mbar_test_wait(S.rowfree, (rows_done - 1) & 1))) return false;
+      } else if (!warp_wait(S.rowfree, (rows_done - 1) & 1, P, S.abort_flag)) {
+        return false;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NVB; v++) {
+      float4* slot = reinterpret_cast<float4*>(S.red + (warp * NVB + v) * 64 + r0);
+      float4 p = red_mine ? *slot : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < SETS; u++) {
+        df_fold(p.x, p.y, s[u][0][v], c[u][0][v]);
+        df_fold(p.z, p.w, s[u][1][v], c[u][1][v]);
+      }
+      *slot = p;
+    }
+    red_mine = true;
+    return true;
+  };
   for (int it = 0; it < ie - ib; it++) {
     const int st = it % NST, use = it / NST;
     if (!warp_wait(S.full + st, use & 1, P, S.abort_flag)) break;
     const unsigned char* stage = S.stage0 + st * SB;
     const int* h = reinterpret_cast<const int*>(stage);
     const int R = min(h[0], 64), C = min(h[1], 64), vs = min(h[2], 64), row = h[4], flags = h[5];
+    const int o = item_offset(flags);
     const double* A = reinterpret_cast<const double*>(stage + kStageHeader);
     const float2* X = reinterpret_cast<const float2*>(stage + kStageHeader + kStageMat);
     const int c0 = (C * warp) / CW, c1 = (C * (warp + 1)) / CW;
@@ -229,8 +275,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream(StreamParams 
       for (int u = 0; u < CPW; u++) {
         const double2 a = *reinterpret_cast<const double2*>(Ab + 64 * u);
         float h0, l0, h1, l1;
-        split_f64_fast(a.x, h0, l0);
-        split_f64_fast(a.y, h1, l1);
+        split_f64_fast(a.x, o, h0, l0);
+        split_f64_fast(a.y, o, h1, l1);
 #pragma unroll
         for (int v = 0; v < NVB; v++) {
           const float2 xv = (v < nv) ? Xb[v * 64 + u] : make_float2(0.f, 0.f);
@@ -255,8 +301,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream(StreamParams 
               if (r0 + 1 < R) a1 = A[r0 + 1 + R * col];
             }
             float h0, l0, h1, l1;
-            split_f64(a0, h0, l0);
-            split_f64(a1, h1, l1);
+            split_f64(a0, o, h0, l0);
+            split_f64(a1, o, h1, l1);
 #pragma unroll
             for (int v = 0; v < NVB; v++) {
               const float2 xv = (v < nv) ? X[v * vs + col] : make_float2(0.f, 0.f);
@@ -269,22 +315,15 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream(StreamParams 
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(S.empty + st);
+    if (++chain >= FI && !(flags & kItemFlagLast) && fold(false)) chain = 0;
     if (flags & kItemFlagLast) {
       // row end: the R = leaf-size rows of y at point offset `row`
-      if (rows_done > 0 && !warp_wait(S.rowfree, (rows_done - 1) & 1, P, S.abort_flag)) break;
-#pragma unroll
-      for (int r = 0; r < 2; r++)
-#pragma unroll
-        for (int v = 0; v < NVB; v++) {
-#pragma unroll
-          for (int u = 1; u < SETS; u++) df_add(s[0][r][v], c[0][r][v], s[u][r][v], c[u][r][v]);
-          S.red[(warp * NVB + v) * 64 + r0 + r] = make_float2(s[0][r][v], c[0][r][v]);
-#pragma unroll
-          for (int u = 0; u < SETS; u++) s[u][r][v] = c[u][r][v] = 0.f;
-        }
+      if (!fold(true)) break;
+      chain = 0;
       __syncwarp();
       if (lane == 0) mbar_arrive(S.rowfull);
       if (!warp_wait(S.rowfull, rows_done & 1, P, S.abort_flag)) break;
+      const int ey = item_row_exp(flags);
       for (int idx = threadIdx.x; idx < R * nv; idx += CW * 32) {
         const int r = idx % R, v = idx / R;
         float ss = 0.f, cc = 0.f;
@@ -293,11 +332,12 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream(StreamParams 
           const float2 p = S.red[(w * NVB + v) * 64 + r];
           df_add(ss, cc, p.x, p.y);
         }
-        P.y[v * P.ldy + row + r] = df_to_f64(ss, cc);
+        P.y[v * P.ldy + row + r] = scale2(df_to_f64(ss, cc), ey + vexp_s[v]);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(S.rowfree);
       rows_done++;
+      red_mine = false;
     }
   }
 }

@@ -89,8 +89,13 @@ def test_rejects_non_finite_values(h2, small):
     kw["D_val"][17] = np.nan
     _expect(h2, h2.H2_ERR_INVALID, **kw)
     kw = _kw(small)
-    kw["D_val"][3] = 2.0 ** 127
+    kw["D_val"][3] = np.inf
     _expect(h2, h2.H2_ERR_INVALID, **kw)
+    # the scaled storage forms keep FP32 block scales: magnitudes from 2^126 on are out of their range
+    # (the FP64 form takes any finite value)
+    kw = _kw(small)
+    kw["D_val"][3] = 2.0 ** 127
+    _expect(h2, h2.H2_ERR_INVALID, storage="int16", **kw)
 
 
 def test_cover_check_finds_missing_and_doubled_blocks(h2, small):

@@ -70,6 +70,74 @@ def test_3d_k64_m64(h2):
     assert oracle.rel_l2(gpu_matvec(h2, A, x), oracle.matvec(A, x)) <= TOL
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("nv", [1, 16])
+def test_3d_k64_long_accumulation_chains(h2, nv):
+    """3D n = 2^17, m = 64, k = 64 (4x4x4 Chebyshev), exp(-r/0.2), eta = 0.9.
+
+    The coupling rows here hold up to a few hundred 64 x 64 blocks, so one
+    lane's products form chains of ten thousand terms; summing the small
+    parts of a double-float pair in FP32 over a whole row grows the error
+    with the chain (a CPU emulation of that arithmetic gives 1.3e-12 for the
+    coupling phase alone at this size). The kernels fold every chain of at
+    most 64 products into a long-term pair."""
+    A = h2gen.generate(dim=3, n=1 << 17, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=3)
+    x = h2gen.vectors(320 + nv, A.n, nv)
+    err = oracle.rel_l2(gpu_matvec(h2, A, x), oracle.matvec(A, x))
+    print(f"3D n=2^17 k=64 nv={nv}: rel l2 {err:.3e}")
+    assert err <= TOL, f"rel l2 {err:.3e} > {TOL}"
+
+
+def _rel_l2_scaled(y, y_ref):
+    """Per-column relative l2 error, each column divided by its largest |y_ref| first (no overflow)."""
+    s = np.max(np.abs(y_ref), axis=0)
+    s[s == 0] = 1.0
+    return oracle.rel_l2(y / s, y_ref / s)
+
+
+def test_full_fp64_range(h2, c1):
+    """Values far outside the FP32 exponent range: vector columns scaled by 2^-300 ... 2^300, dense and
+    coupling blocks by 2^-200, 1 or 2^200, leaf bases by 2^-40 ... 2^40 and transfers by 2^-3 ... 2^3
+    (each block its own factor; the result is still an H^2 matrix). Every block and vector enters the
+    double-float pairs scaled by a power of two, so the product keeps its accuracy at any scale."""
+    rng = np.random.default_rng(21)
+    k, q = c1.k, c1.q
+    D = c1.D_val.copy()
+    for b in range(c1.nD):
+        D[c1.D_valoff[b]:c1.D_valoff[b + 1]] *= 2.0 ** rng.choice([-200, 0, 200])
+    S = (c1.S_val.reshape(c1.nS, k * k) * 2.0 ** rng.choice([-200, 0, 200], size=(c1.nS, 1))).ravel()
+    U = c1.U.copy()
+    for j in range(1 << q):
+        U[c1.leaf_offset[j] * k:c1.leaf_offset[j + 1] * k] *= 2.0 ** rng.choice([-40, 0, 40])
+    n_nodes = (2 << q) - 1
+    E = (c1.E.reshape(n_nodes - 1, k * k) * 2.0 ** rng.integers(-3, 4, size=(n_nodes - 1, 1))).ravel()
+    x = h2gen.vectors(309, c1.n, 5) * np.ldexp(1.0, np.array([-300, -150, 0, 150, 300]))[None, :]
+    M = h2.H2Matrix(n=c1.n, depth=q, rank=k, leaf_offset=c1.leaf_offset, U=U, E=E, S_rowptr=c1.S_rowptr,
+                    S_colidx=c1.S_colidx, S_val=S, D_rowptr=c1.D_rowptr, D_colidx=c1.D_colidx, D_val=D)
+    y = M.matvec(to_dev(x)).cpu().numpy()
+    M.check()
+    M.close()
+    y_ref = oracle.matvec(c1, x, U=U, E=E, S_val=S, D_val=D)
+    assert np.all(np.isfinite(y))
+    err = _rel_l2_scaled(y, y_ref)
+    print(f"full FP64 range: rel l2 {err:.3e}")
+    assert err <= TOL, f"rel l2 {err:.3e} > {TOL}"
+
+
+def test_zero_column_and_tiny_vectors(h2, c1):
+    """A zero column gives an exact zero; a column of magnitude 2^-1000 (subnormal products in FP64
+    arithmetic of the unscaled values) keeps full accuracy."""
+    x = h2gen.vectors(310, c1.n, 3)
+    x[:, 1] = 0.0
+    x[:, 2] *= 2.0 ** -1000
+    y = gpu_matvec(h2, c1, x)
+    assert np.all(y[:, 1] == 0.0)
+    y_ref = oracle.matvec(c1, x)
+    for v in (0, 2):
+        err = _rel_l2_scaled(y[:, v:v + 1], y_ref[:, v:v + 1])
+        assert err <= TOL, (v, err)
+
+
 def test_2d_n65536_m64(h2):
     """Many leaves (1024) and 10 levels: every kernel runs multi-CTA grids with ragged tails."""
     A = h2gen.generate(dim=2, n=65536, m=64, p=4, eta=0.9, kernel="exp", ell=0.1, seed=9)
