@@ -4,8 +4,11 @@ through the C ABI.
 The reference is the O-tree oracle on the same matrix with the dequantized stored blocks (U, V,
 E, F, D as the handle stores them) and the coupling blocks from ``oracle.kernel_coupling`` (FP64,
 from the definition; pinned against the generator's blocks on the CPU). The handle evaluates
-the same blocks in FP32, so only FP32 rounding separates the two: relative l2 error <= 2e-5,
-the precision form's bound. Cases cover every lane layout of the kernel (k = 16 and 9: column
+the same blocks in FP32, so only FP32 rounding separates the two: the FP32 accumulation bound
+2 u sqrt(N) of the stored precision form (fp32_tol.py) plus the blocks' own evaluation error
+(kernel values from FP32 distances and the exp intrinsic: relative errors of about 1e-6 per value,
+of random sign, so their effect on an output stays below KERNEL_EVAL = 2e-6). Cases cover every
+lane layout of the kernel (k = 16 and 9: column
 groups; k = 27: one group; k = 64: two rows per lane), both kernels, all code types, passes of
 several vector counts and ragged leaves.
 """
@@ -16,9 +19,14 @@ import h2gen
 import oracle
 from oracle import kernel_coupling as kc
 from oracle import quant
+from fp32_tol import acc_tol, check
 
 pytestmark = pytest.mark.gpu
-TOL = 2e-5
+KERNEL_EVAL = 2e-6
+
+
+def tol(A):
+    return acc_tol(A) + KERNEL_EVAL
 
 torch = pytest.importorskip("torch")
 
@@ -62,8 +70,7 @@ def test_kernel_coupling_matches_oracle(h2, cfg, form, bases, nvs):
         x = h2gen.vectors(1000 + nv, A.n, nv)
         y = M.matvec(to_dev(x)).cpu().numpy()
         M.check()
-        err = oracle.rel_l2(y, reference(A, x, form, bases))
-        assert err <= TOL, (cfg, form, nv, err)
+        check(oracle.rel_l2(y, reference(A, x, form, bases)), tol(A), (cfg["dim"], cfg["n"], A.k, form, nv))
     M.close()
 
 
@@ -109,7 +116,7 @@ def test_kernel_coupling_tune_and_graph_capture(h2):
     g.replay()
     torch.cuda.synchronize()
     M.check()
-    assert oracle.rel_l2(y.cpu().numpy(), reference(A, x_np, "int16", True)) <= TOL
+    check(oracle.rel_l2(y.cpu().numpy(), reference(A, x_np, "int16", True)), tol(A), "graph replay")
     del g
     M.close()
 
@@ -122,7 +129,7 @@ def test_kernel_coupling_full_size_2d(h2):
     x = h2gen.vectors(31, A.n, 1)
     y = M.matvec(to_dev(x)).cpu().numpy()
     M.check()
-    assert oracle.rel_l2(y, reference(A, x, "int16", True)) <= TOL
+    check(oracle.rel_l2(y, reference(A, x, "int16", True)), tol(A), "2d n=2^20")
     # and against the FP64 oracle of the stored matrix: within the int16 form's 1e-4
     assert oracle.rel_l2(y, oracle.matvec(A, x)) <= 1e-4
     M.close()
