@@ -43,6 +43,11 @@ h2_status (&fail)(h2_status, const char*, ...) = h2_fail;
 
 void free_all(h2_matrix_s* h) {
   profile_free(&h->prof);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  h->side = nullptr;
+  h->ev_fork = h->ev_join = nullptr;
   for (void* p : h->allocs) cudaFree(p);
   h->allocs.clear();
   if (h->hx) cudaFree(h->hx);

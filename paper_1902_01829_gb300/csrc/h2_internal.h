@@ -64,6 +64,11 @@ struct MixedLaunch {
   int cw = 8;                        // consumer warps of the dense stream (8, or 16 for passes of <= 8 vectors)
   bool kf = false;                   // coupling blocks evaluated from the kernel (no stored S)
   Profiler* prof = nullptr;          // profiler whose events mark the phases (or none)
+  const void* rjobs = nullptr;       // h2::RowJob per leaf row of every matrix (split x, leaf expansion)
+  int64_t nrjobs = 0;
+  // the tree phases run on `side` beside the dense phase (CUDA-core passes, not profiling)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // the tensor-core dense phase of one pass (one matrix, panel layout, fp16 / bf16 codes)
@@ -119,6 +124,8 @@ struct MixedData {
   float4* kf_clo = nullptr;      // and their low parts
   float4* kf_off = nullptr;      // [node][k] offsets of the interpolation points from the centre
   int4* tc_brec = nullptr;       // and the builders' records of those items
+  void* rjobs = nullptr;         // h2::RowJob per leaf row (matrix index 0)
+  std::vector<unsigned char> rjobs_host;  // the same, kept for batches
   // the table-driven kernels' tables for this matrix alone (a batch of one)
   MixedLaunch launch;
   std::vector<h2::StreamItem> items_host;  // the dense items (matrix index 0), kept for batches
@@ -191,6 +198,9 @@ struct h2_matrix_s {
   long long budget = h2i::kWaitBudget;
   int inject = -1;
   h2i::Profiler prof;
+  // precision form: the tree phases run on `side` beside the dense phase
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // host-buffer staging (h2_matvec_host)
   double* hx = nullptr;
   double* hy = nullptr;
@@ -257,4 +267,6 @@ struct h2_batch_s {
   h2i::Profiler prof;
   int64_t n_items = 0, device_bytes = 0;
   std::vector<void*> allocs;
+  cudaStream_t side = nullptr;  // the tree phases beside the dense phase
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };

@@ -151,6 +151,8 @@ h2::MatDesc fill_desc(const h2_matrix_s* h, int tree_L) {
   D.kf_off = M.kf_off;
   D.kf_inv_ell = h->kf_inv_ell;
   D.kf_kind = h->kf_kind;
+  D.rjobs = static_cast<const h2::RowJob*>(M.rjobs);
+  D.blk = static_cast<const h2::MixedBlock*>(M.dblk);
   return D;
 }
 
@@ -176,6 +178,21 @@ h2_status set_calls(h2::MatDesc* mats, int64_t count, const int* nv, const doubl
 }  // namespace
 
 static_assert(h2i::kDenseCW == h2::kMixedCW, "dense-stream consumer warps");
+
+// The dense stream's producer stages the block records of 32 consecutive items of a CTA at a
+// time; their block range must fit its buffer (kMixedBatchBlocks records).
+h2_status audit_producer_batches(const std::vector<h2::StreamItem>& items, const std::vector<int>& begin) {
+  for (size_t c = 0; c + 1 < begin.size(); c++)
+    for (int base = begin[c]; base < begin[c + 1]; base += 32) {
+      const h2::StreamItem& a = items[(size_t)base];
+      const h2::StreamItem& z = items[(size_t)std::min(base + 31, begin[c + 1] - 1)];
+      const long long span = z.v_off + ((z.shape >> 8) & 0xFF) - a.v_off;
+      if (span < 0 || span > h2::kMixedBatchBlocks)
+        return h2_fail(H2_ERR_INVALID, "internal: 32 work items span %lld block records", span);
+    }
+  return H2_OK;
+}
+
 
 namespace h2i {
 
@@ -442,13 +459,17 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
     if ((st = upload(h, &dblk, blk.data(), nblk)) != H2_OK) return st;
     M.dblk = dblk;
 
-    // work items: consecutive blocks of one row, at most kMixedMaxBlocks blocks, 32 KB of
-    // entries and kMixedVecCols vector columns per item
+    // work items: consecutive dense blocks of one row, at most kMixedMaxBlocks blocks, 32 KB of
+    // entries and kMixedVecCols vector columns per item. U_i (the row's last block) is not
+    // streamed: the leaf expansion multiplies it after the downsweep (k_expand_m), so that the
+    // dense phase does not wait for the tree phases.
     std::vector<h2::StreamItem> items;
     std::vector<int64_t> row_bytes((size_t)leaves), row_item0((size_t)leaves + 1);
+    std::vector<h2::RowJob> rj((size_t)leaves);
     for (int64_t i = 0; i < leaves; i++) {
       row_item0[i] = (int64_t)items.size();
-      const int64_t g0 = row_blk0[i], g1 = row_blk0[i + 1];
+      const int64_t g0 = row_blk0[i], g1 = row_blk0[i + 1] - 1;  // [g0, g1) dense blocks, g1 = U_i
+      rj[i] = h2::RowJob{boff[g1], 0, (int)i, (int)g1, g1 > g0 ? 1 : 0, {0, 0}};
       int64_t bytes = 0;
       for (int64_t g = g0; g < g1;) {
         int64_t e = g, mb = 0, vc = 0;
@@ -473,6 +494,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
     }
     row_item0[leaves] = (int64_t)items.size();
     const std::vector<int> begin = balance(row_bytes, row_item0, h->grid);
+    if ((st = audit_producer_batches(items, begin)) != H2_OK) return st;
     // audit: every copy in bounds, 16-byte aligned, and within its stage slot
     for (size_t c = 0; c + 1 < begin.size(); c++)
       if (begin[c] > begin[c + 1]) return h2_fail(H2_ERR_INVALID, "internal: item ranges not monotone");
@@ -575,6 +597,11 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
     M.dense_items.count = (int64_t)items.size();
     M.nblk = nblk;
     M.items_host = std::move(items);
+    h2::RowJob* drj = nullptr;
+    if ((st = upload(h, &drj, rj.data(), leaves)) != H2_OK) return st;
+    M.rjobs = drj;
+    M.rjobs_host.assign(reinterpret_cast<const unsigned char*>(rj.data()),
+                        reinterpret_cast<const unsigned char*>(rj.data() + leaves));
     M.row_bytes = std::move(row_bytes);
     M.row_item0 = std::move(row_item0);
   }
@@ -602,6 +629,14 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   L.k = k;
   L.bases_fp32 = M.bases_fp32;
   L.kf = h->kf;
+  L.rjobs = M.rjobs;
+  L.nrjobs = leaves;
+  CUDA_TRY(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  L.side = h->side;
+  L.ev_fork = h->ev_fork;
+  L.ev_join = h->ev_join;
   // defaults (h2_tune may choose others): 16 dense consumer warps for leaves of at most 32 points
   // (little arithmetic per item, more warps hide more latency), 128 coupling blocks per chunk
   return mixed_configure(h, kDefaultChunkOpt, h->m_max <= 32 ? 2 * h2::kMixedCW : h2::kMixedCW, 0);
@@ -648,10 +683,10 @@ h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, doubl
     T.nv = nv;
     T.err = h->err;
     T.budget = h->budget;
-    h->prof.launches += h->storage == H2_FP16_SCALED ? 7 : 6;
+    h->prof.launches += h->storage == H2_FP16_SCALED ? 8 : 7;  // set_calls, split, 3 tree, (vmax,) vscale, tc
     return mixed_launch(h->storage, L, 1u << bucket_of(nv), st, &T);
   }
-  h->prof.launches += 5;
+  h->prof.launches += 6;  // set_calls, split, upsweep, coupling, downsweep (+ expansion), dense
   return mixed_launch(h->storage, L, 1u << bucket_of(nv), st);
 }
 
@@ -679,6 +714,11 @@ h2_status balloc(h2_batch_s* b, T** p, int64_t count, const T* src = nullptr) {
 }
 
 void batch_free(h2_batch_s* b) {
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  b->side = nullptr;
+  b->ev_fork = b->ev_join = nullptr;
   for (void* p : b->allocs) cudaFree(p);
   b->allocs.clear();
   profile_free(&b->prof);
@@ -718,7 +758,11 @@ h2_status batch_configure(h2_batch_s* b, int chunk_opt, int tree_opt, int cw) {
   }
   if (!L.mats || tree_opt != b->tree_opt) {  // the descriptors carry each member's subtree level
     std::vector<h2::MatDesc> descs((size_t)count);
-    for (int64_t i = 0; i < count; i++) descs[(size_t)i] = fill_desc(b->hs[(size_t)i], std::max(0, b->hs[(size_t)i]->q - T));
+    for (int64_t i = 0, r0 = 0; i < count; r0 += b->hs[(size_t)i]->leaves, i++) {
+      descs[(size_t)i] = fill_desc(b->hs[(size_t)i], std::max(0, b->hs[(size_t)i]->q - T));
+      descs[(size_t)i].rjobs = static_cast<const h2::RowJob*>(L.rjobs) + r0;  // the batch's row jobs and records
+      descs[(size_t)i].blk = static_cast<const h2::MixedBlock*>(L.blk);
+    }
     if (!L.mats) {
       h2::MatDesc* md = nullptr;
       if ((st = balloc(b, &md, count, descs.data())) != H2_OK) return st;
@@ -744,6 +788,7 @@ h2_status batch_build(h2_batch_s* b) {
   h2_status st;
   std::vector<h2::StreamItem> items;
   std::vector<int64_t> row_bytes, row_item0;
+  std::vector<h2::RowJob> rjobs;
   int64_t blk0 = 0;
   for (int64_t i = 0; i < count; i++) {
     const h2_matrix_s* h = b->hs[(size_t)i];
@@ -753,6 +798,14 @@ h2_status batch_build(h2_batch_s* b) {
       it.v_off += blk0;
       it.flags = (it.flags & 0xFF) | (int)(i << 8);
       items.push_back(it);
+    }
+    const h2::RowJob* mr = reinterpret_cast<const h2::RowJob*>(M.rjobs_host.data());
+    for (size_t r = 0; r < M.rjobs_host.size() / sizeof(h2::RowJob); r++) {
+      h2::RowJob J = mr[r];
+      J.mat = (int)i;
+      if (blk0 + J.ublk >= INT32_MAX) return h2_fail(H2_ERR_UNSUPPORTED, "batch too large: block records");
+      J.ublk += (int)blk0;
+      rjobs.push_back(J);
     }
     for (size_t r = 0; r + 1 < M.row_item0.size(); r++) {
       row_item0.push_back(item0 + M.row_item0[r]);
@@ -764,6 +817,7 @@ h2_status batch_build(h2_batch_s* b) {
   if ((int64_t)items.size() >= INT32_MAX)
     return h2_fail(H2_ERR_UNSUPPORTED, "batch too large: %lld dense items", (long long)items.size());
   const std::vector<int> begin = balance(row_bytes, row_item0, h0->grid);
+  if ((st = audit_producer_batches(items, begin)) != H2_OK) return st;
   for (size_t c = 0; c + 1 < begin.size(); c++)
     if (begin[c] > begin[c + 1]) return h2_fail(H2_ERR_INVALID, "internal: item ranges not monotone");
   for (const h2::StreamItem& it : items)  // the member audits hold; only the block index moved
@@ -782,6 +836,16 @@ h2_status batch_build(h2_batch_s* b) {
   int* err = nullptr;
   if ((st = balloc(b, &err, 1)) != H2_OK) return st;
   CUDA_TRY(cudaMemset(err, 0, sizeof(int)));
+  h2::RowJob* drj = nullptr;
+  if ((st = balloc(b, &drj, (int64_t)rjobs.size(), rjobs.data())) != H2_OK) return st;
+  L.rjobs = drj;
+  L.nrjobs = (int64_t)rjobs.size();
+  CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+  L.side = b->side;
+  L.ev_fork = b->ev_fork;
+  L.ev_join = b->ev_join;
   L.items = di;
   L.cta_begin = db;
   L.blk = blk;
@@ -892,7 +956,7 @@ h2_status h2_batch_matvec(h2_batch b, const int32_t* nv, const double* const* x,
     h2_status s = set_calls(static_cast<h2::MatDesc*>(L.mats), count, pnv.data(), px.data(), pldx.data(), py.data(),
                             pldy.data(), st);
     if (s != H2_OK) return s;
-    b->prof.launches += (count + kCallChunk - 1) / kCallChunk + 3 * bucket_count(buckets) + 1;
+    b->prof.launches += (count + kCallChunk - 1) / kCallChunk + 3 * bucket_count(buckets) + 2;
     s = mixed_launch(b->storage, L, buckets, st);
     if (s != H2_OK) return s;
   }

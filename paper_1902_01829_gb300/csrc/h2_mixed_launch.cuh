@@ -19,10 +19,30 @@ cudaError_t set_mixed_smem() {
   return done;
 }
 
+// Kernels that run beside the dense stream prefer its L1 / shared memory split (the largest shared
+// part): an SM holds CTAs of one configuration at a time.
+template <class K>
+void prefer_max_shared(K kernel) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
 // the tree and coupling launches of one vector-count bucket (phase 0: upsweep, 1: coupling, 2: downsweep)
+// expand: the downsweep ends with the leaf expansion (y was zeroed and the dense phase adds its part)
 template <int F, int FB, int RPL, int NVB>
-void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st) {
+void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st, bool expand) {
   using namespace h2;
+  static const bool carveout = [] {
+    constexpr int NVW = NVB < 4 ? NVB : 4, VG = NVB / NVW;
+    prefer_max_shared(k_upsweep_tree_m<FB, RPL, NVB>);
+    prefer_max_shared(k_downsweep_tree_m<FB, RPL, NVB>);
+    prefer_max_shared(k_coupling_kf<RPL, NVB>);
+    prefer_max_shared(k_coupling_m<F, 16, NVW, (NVW <= 2 ? 4 : 2), VG>);
+    prefer_max_shared(k_coupling_m<F, 32, NVW, (NVW <= 1 ? 2 : 1), VG>);
+    prefer_max_shared(k_coupling_m<F, 64, NVW, (NVW <= 1 ? 2 : 1), VG>);
+    prefer_max_shared(k_coupling_m_generic<F, RPL, NVB>);
+    return true;
+  }();
+  (void)carveout;
   const MatDesc* mats = static_cast<const MatDesc*>(L.mats);
   const unsigned tree_threads = kTreeWarpsM * 32;
   if (phase == 0 && L.njobs > 0) {
@@ -50,18 +70,18 @@ void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st) {
       k_coupling_m_generic<F, RPL, NVB><<<cgrid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
     }
   } else if (phase == 2 && L.njobs > 0) {
-    k_downsweep_tree_m<FB, RPL, NVB><<<(unsigned)L.njobs, tree_threads, 0, st>>>(mats, L.jobs, nvlo, NVB);
+    k_downsweep_tree_m<FB, RPL, NVB><<<(unsigned)L.njobs, tree_threads, 0, st>>>(mats, L.jobs, nvlo, NVB, expand ? 1 : 0);
   }
 }
 
 template <int F, int FB, int RPL>
-void bucket_dispatch(const MixedLaunch& L, int phase, int b, cudaStream_t st) {
+void bucket_dispatch(const MixedLaunch& L, int phase, int b, cudaStream_t st, bool expand) {
   switch (b) {
-    case 0: return bucket_phase<F, FB, RPL, 1>(L, phase, kBucketLo[0], st);
-    case 1: return bucket_phase<F, FB, RPL, 2>(L, phase, kBucketLo[1], st);
-    case 2: return bucket_phase<F, FB, RPL, 4>(L, phase, kBucketLo[2], st);
-    case 3: return bucket_phase<F, FB, RPL, 8>(L, phase, kBucketLo[3], st);
-    default: return bucket_phase<F, FB, RPL, 16>(L, phase, kBucketLo[4], st);
+    case 0: return bucket_phase<F, FB, RPL, 1>(L, phase, kBucketLo[0], st, expand);
+    case 1: return bucket_phase<F, FB, RPL, 2>(L, phase, kBucketLo[1], st, expand);
+    case 2: return bucket_phase<F, FB, RPL, 4>(L, phase, kBucketLo[2], st, expand);
+    case 3: return bucket_phase<F, FB, RPL, 8>(L, phase, kBucketLo[3], st, expand);
+    default: return bucket_phase<F, FB, RPL, 16>(L, phase, kBucketLo[4], st, expand);
   }
 }
 
@@ -134,27 +154,57 @@ h2_status tc_launch(const TcCall& T, cudaStream_t st) {
   }
 }
 
-// the phase launches; the caller has written the product's fields into the
-// matrix table and recorded the first profiling mark
+// The phase launches; the caller has written the product's fields into the matrix table and
+// recorded the first profiling mark. x is first copied to FP32 (k_split_x4). On the CUDA cores
+// the dense phase streams the D blocks only and adds its row sums into y (zeroed by the split),
+// and the downsweep ends with the leaf expansion U_i yhat_i, added the same way; so passes of up
+// to four vectors run the dense phase on the caller's stream while the tree phases (upsweep,
+// coupling, downsweep) run on L.side. The tensor-core pass fuses the expansion into its dense
+// phase and runs after the tree phases, and so do wider passes and profiled products (events
+// between the phases).
 template <int F, int FB, int RPL>
 h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {
   cudaError_t me = cudaSuccess;
   auto mk = [&]() {
     if (L.prof && me == cudaSuccess) me = mark(L.prof, st);
   };
-  for (int phase = 0; phase < 3; phase++) {
-    for (int b = 0; b < kBuckets; b++)
-      if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, st);
-    mk();
-  }
+  const bool expand = !tc;  // the CUDA-core dense phase leaves the expansion to the downsweep
+  const long long swarps = std::min<long long>(L.nrjobs, (long long)L.grid * 64);
+  h2::k_split_x4<F><<<(unsigned)((swarps + 7) / 8), 256, 0, st>>>(static_cast<const h2::MatDesc*>(L.mats),
+                                                              static_cast<const h2::RowJob*>(L.rjobs), L.nrjobs,
+                                                              expand ? 1 : 0);
   const int top = 31 - __builtin_clz(buckets | 1u);
-  h2_status s = tc         ? tc_launch<F>(*tc, st)
-                : top == 0 ? dense_launch<F, 1>(L, st)
-                : top == 1 ? dense_launch<F, 2>(L, st)
-                : top == 2 ? dense_launch<F, 4>(L, st)
-                : top == 3 ? dense_launch<F, 8>(L, st)
-                           : dense_launch<F, 16>(L, st);
-  if (s != H2_OK) return s;
+  auto dense = [&](cudaStream_t ds) -> h2_status {
+    return tc         ? tc_launch<F>(*tc, ds)
+           : top == 0 ? dense_launch<F, 1>(L, ds)
+           : top == 1 ? dense_launch<F, 2>(L, ds)
+           : top == 2 ? dense_launch<F, 4>(L, ds)
+           : top == 3 ? dense_launch<F, 8>(L, ds)
+                      : dense_launch<F, 16>(L, ds);
+  };
+  // passes of more than four vectors keep the phases in order: their tree kernels' shared memory does
+  // not fit beside the dense stream's, and the dense phase is bound by arithmetic there (measured)
+  const bool overlap = !tc && top <= 2 && !(L.prof && L.prof->on) && L.side && L.ev_fork && L.ev_join;
+  h2_status s = H2_OK;
+  if (overlap) {
+    cudaError_t e = cudaEventRecord(L.ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(L.side, L.ev_fork, 0);
+    if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "fork to the side stream: %s", cudaGetErrorString(e));
+    if ((s = dense(st)) != H2_OK) return s;
+    for (int phase = 0; phase < 3; phase++)
+      for (int b = 0; b < kBuckets; b++)
+        if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, L.side, expand);
+    e = cudaEventRecord(L.ev_join, L.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, L.ev_join, 0);
+    if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "join from the side stream: %s", cudaGetErrorString(e));
+  } else {
+    for (int phase = 0; phase < 3; phase++) {
+      for (int b = 0; b < kBuckets; b++)
+        if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, st, expand);
+      mk();
+    }
+    if ((s = dense(st)) != H2_OK) return s;
+  }
   mk();
   if (me != cudaSuccess) return h2_fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
   cudaError_t e = cudaGetLastError();

@@ -56,6 +56,36 @@ __device__ __forceinline__ float2 codes_to_f2(uint32_t w) {
                      __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7432)) - 8421376.0f);
 }
 
+// Per leaf row of a matrix: where U_i is and its block record (the leaf
+// expansion at the end of the downsweep and the split of x use them)
+struct __align__(16) RowJob {
+  long long uoff;  // byte offset of U_i in the matrix's dmat
+  int mat;         // matrix index in the table
+  int leaf;        // leaf index j (heap node 2^q - 1 + j)
+  int ublk;        // block record of U_i (scale, layout)
+  int has_dense;   // the dense phase adds a part of this row (it has dense blocks)
+  int pad[2];
+};
+struct __align__(16) MixedBlock {
+  long long voff;       // vector chunk offset, in floats per vector slot
+  float scale;
+  unsigned short cols;  // C
+  unsigned char vs;     // vector stride (>= C, multiple of 4)
+  unsigned char src;    // bit 0: vector from the second source (yhat); bit 1: FP32 entries (not codes);
+                        // bit 2: panel layout (below)
+};
+
+// Panel layout of a block of codes (64 rows, C columns): eight panels of 8 rows,
+// panel p holding column c's rows 8p .. 8p + 7 as 16 contiguous bytes at c * 16,
+// the panels kPanelPad bytes apart beyond their 16 * Cp bytes (Cp = C rounded up
+// to 16, padding columns zero). It is the MN-major operand layout of tcgen05.mma
+// (8 x 8 core matrices: K stride 128 bytes, M stride the panel stride), and the
+// pad staggers the panels over the shared-memory banks for the CUDA-core reader.
+constexpr int kPanelPad = 16;
+__host__ __device__ constexpr int panel_cols(int C) { return (C + 15) & ~15; }
+__host__ __device__ constexpr int panel_stride(int C) { return 16 * panel_cols(C) + kPanelPad; }  // bytes
+__host__ __device__ constexpr int panel_block_bytes(int C) { return 8 * panel_stride(C); }
+
 // ---------------------------------------------------------------- per-matrix descriptor
 // One entry per matrix of a batch (a single product is a batch of one); the
 // kernels of every phase find their matrix through it. The last group of
@@ -88,6 +118,9 @@ struct MatDesc {
   const float4* kf_off;
   float kf_inv_ell;
   int kf_kind;
+  // the leaf expansion done by the downsweep: the matrix's row jobs and the block records they index
+  const RowJob* rjobs;
+  const MixedBlock* blk;
   // per product
   const double* x;
   long long ldx;
@@ -230,28 +263,8 @@ __device__ __forceinline__ void project_leaf_m(const TreeParamsM& P, int64_t j, 
   const int64_t off = P.leaf_off[j];
   const int sj = (int)(P.leaf_off[j + 1] - off);
   const int spad = (sj + 3) & ~3;
-  float* xj = P.x4 + P.xp4_off[j] * P.nv;
-  const double* __restrict__ xs = P.x + off;
-  // every load of the chunk is issued before any store (the stores could alias x for the compiler)
-  float xr[NVB][2];
-#pragma unroll
-  for (int v = 0; v < NVB; v++)
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int a = lane + 32 * h;
-      xr[v][h] = (v < P.nv && a < sj) ? __double2float_rn(__ldg(xs + v * P.ldx + a)) : 0.f;  // padding is zero
-    }
-#pragma unroll
-  for (int v = 0; v < NVB; v++)
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int a = lane + 32 * h;
-      if (v < P.nv && a < spad) {
-        xj[v * spad + a] = xr[v][h];
-        wbuf[v * spad + a] = xr[v][h];
-      }
-    }
-  __syncwarp();
+  // the FP32 copy of x(j) (k_split_x4, padding zero) into the warp's buffer
+  stage_vectors<false>(wbuf, P.x4 + P.xp4_off[j] * P.nv, P.nv * spad, lane);
   float acc[RPL][NVB];
 #pragma unroll
   for (int r = 0; r < RPL; r++)
@@ -336,10 +349,67 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_upsweep_tree_m(const MatDe
 }
 
 // the whole downsweep in one launch (see k_downsweep_tree)
+// y(j) += scale * U_j yhat_j for leaf j (Eq. 4) with FP64 atomic adds: the dense phase adds its
+// part of the row the same way (both into a y zeroed before the product), so the two may run at
+// the same time. U_j is size_j x k, FP32 entries or 16-bit codes of format FB (column-major or
+// panel layout); its place and scale come from the matrix's row job and block record.
+template <int FB, int NVB>
+__device__ __forceinline__ void expand_leaf_m(const MatDesc& D, int64_t j, int lane, float* wbuf) {
+  const RowJob J = D.rjobs[j];
+  const MixedBlock mb = D.blk[J.ublk];
+  const int nv = D.nv, k = D.k, kp = D.kp;
+  const int64_t off = D.leaf_off[j];
+  const int R = (int)(D.leaf_off[j + 1] - off);
+  stage_vectors<false>(wbuf, D.yhat + ((((int64_t)1 << D.q) - 1 + j) * nv) * kp, nv * kp, lane);
+  const bool f32 = (mb.src & 2) != 0, panel = (mb.src & 4) != 0;
+  const unsigned char* U = reinterpret_cast<const unsigned char*>(D.dmat) + J.uoff;
+  const int ps2 = panel_stride(k) / 2;
+  float acc[2][NVB];
+#pragma unroll
+  for (int r = 0; r < 2; r++)
+#pragma unroll
+    for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
+  for (int nu0 = 0; nu0 < k; nu0 += 8) {  // eight columns' loads before their use
+    float u[8][2];
+#pragma unroll
+    for (int c = 0; c < 8; c++)
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        const int row = lane + 32 * r, nu = nu0 + c;
+        u[c][r] = 0.f;
+        if (row < R && nu < k) {
+          if (f32) u[c][r] = __ldg(reinterpret_cast<const float*>(U) + row + R * nu);
+          else
+            u[c][r] = code_to_f<FB>(__ldg(reinterpret_cast<const uint16_t*>(U) +
+                                          (panel ? (row >> 3) * ps2 + 8 * nu + (row & 7) : row + R * nu)));
+        }
+      }
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      if (nu0 + c >= k) break;
+#pragma unroll
+      for (int v = 0; v < NVB; v++) {
+        const float yv = v < nv ? wbuf[v * kp + nu0 + c] : 0.f;
+        acc[0][v] = fmaf(u[c][0], yv, acc[0][v]);
+        acc[1][v] = fmaf(u[c][1], yv, acc[1][v]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 2; r++) {
+    const int row = lane + 32 * r;
+    if (row >= R) continue;
+#pragma unroll
+    for (int v = 0; v < NVB; v++)
+      if (v < nv) atomicAdd(D.y + v * D.ldy + off + row, (double)(mb.scale * acc[r][v]));
+  }
+  __syncwarp();  // wbuf is reused by the warp's next leaf
+}
+
 template <int F, int RPL, int NVB>
 __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(const MatDesc* __restrict__ mats,
                                                                       const int2* __restrict__ jobs, int nvlo,
-                                                                      int nvhi) {
+                                                                      int nvhi, int expand) {
   __shared__ float path[2][NVB][64];
   __shared__ __align__(16) float wstage[kTreeWarpsM][NVB * 64];
   const int2 job = jobs[blockIdx.x];
@@ -405,6 +475,13 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(const Mat
       store_node_m<RPL, NVB, true>(P.yhat + ch * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, acc, lane);
     }
     __syncthreads();
+  }
+  // leaf expansion (Eq. 4) of the subtree's leaves: their yhat is final (written by this CTA
+  // above, or by the coupling phase when the subtree root is the root and a leaf)
+  if (expand) {
+    const MatDesc& D = mats[job.x];
+    const int T = P.q - P.L;
+    for (int64_t t = warp; t < ((int64_t)1 << T); t += kTreeWarpsM) expand_leaf_m<F, NVB>(D, (sub << T) + t, lane, wbuf);
   }
 }
 
@@ -762,33 +839,22 @@ __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const Mat
 
 // ---------------------------------------------------------------- dense near field + expansion (TMA stream)
 // Per-block side information of the dense stream, 16 bytes.
-struct __align__(16) MixedBlock {
-  long long voff;       // vector chunk offset, in floats per vector slot
-  float scale;
-  unsigned short cols;  // C
-  unsigned char vs;     // vector stride (>= C, multiple of 4)
-  unsigned char src;    // bit 0: vector from the second source (yhat); bit 1: FP32 entries (not codes);
-                        // bit 2: panel layout (below)
-};
 
-// Panel layout of a block of codes (64 rows, C columns): eight panels of 8 rows,
-// panel p holding column c's rows 8p .. 8p + 7 as 16 contiguous bytes at c * 16,
-// the panels kPanelPad bytes apart beyond their 16 * Cp bytes (Cp = C rounded up
-// to 16, padding columns zero). It is the MN-major operand layout of tcgen05.mma
-// (8 x 8 core matrices: K stride 128 bytes, M stride the panel stride), and the
-// pad staggers the panels over the shared-memory banks for the CUDA-core reader.
-constexpr int kPanelPad = 16;
-__host__ __device__ constexpr int panel_cols(int C) { return (C + 15) & ~15; }
-__host__ __device__ constexpr int panel_stride(int C) { return 16 * panel_cols(C) + kPanelPad; }  // bytes
-__host__ __device__ constexpr int panel_block_bytes(int C) { return 8 * panel_stride(C); }
+
+
 
 constexpr int kMixedMaxBlocks = 8;   // blocks of one row per work item
 constexpr int kMixedVecCols = 256;   // vector columns of one work item (sum of its blocks' vs)
 constexpr int kMixedHeader = 256;
 __host__ __device__ constexpr int mixed_vec_area(int nvb) { return kMixedVecCols * nvb * 4; }
 __host__ __device__ constexpr int mixed_stage_bytes(int nvb) { return kMixedHeader + kStageMat + mixed_vec_area(nvb); }
-__host__ __device__ constexpr int mixed_red_bytes(int nvb, int cw) { return cw * nvb * 64 * 4; }
-constexpr int kMixedBlkBuf = 32 * kMixedMaxBlocks * 16;  // block records of one producer batch (32 items)
+// row partials [warp][vector][64 rows]; passes of at most four vectors double-buffer them by row
+// parity (rows end without a CTA-wide barrier, see k_dense_stream_m)
+__host__ __device__ constexpr int mixed_red_bytes(int nvb, int cw) { return (nvb <= 4 ? 2 : 1) * cw * nvb * 64 * 4; }
+// block records of one producer batch of 32 items: their blocks, plus one record per row between
+// them (U_i, not streamed) -- at most 32 (kMixedMaxBlocks + 1) records
+constexpr int kMixedBatchBlocks = 32 * (kMixedMaxBlocks + 1);
+constexpr int kMixedBlkBuf = kMixedBatchBlocks * 16;
 __host__ __device__ constexpr int mixed_stages(int nvb, int cw) {
   return (kSmemLimit - 256 - kMixedBlkBuf - mixed_red_bytes(nvb, cw)) / mixed_stage_bytes(nvb) < 6
              ? (kSmemLimit - 256 - kMixedBlkBuf - mixed_red_bytes(nvb, cw)) / mixed_stage_bytes(nvb)
@@ -810,7 +876,9 @@ struct MixedStreamParams {
   long long budget;
 };
 
-// Stage header (ints): [0] R, [1] nb, [2] row, [3] flags; block t at 8 + 4 t:
+// Stage header (ints): [0] R, [1] nb, [2] row, [3] flags, [4] uniform (1: every block a full 64 x 64
+// column-major block of 16-bit codes with 64 vector columns, 2: the same in the panel layout; the
+// blocks' codes and vector chunks then follow each other at fixed strides); block t at 8 + 4 t:
 // cols | FP32-entries flag << 16, vs, matrix offset in bytes, scale (bits);
 // [40 + t] block t's vector offset in bytes; [48] nv; [50..51] y; [52..53] ldy.
 constexpr int kHdVoff = 40, kHdNv = 48, kHdY = 50, kHdLdy = 52;
@@ -840,7 +908,7 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
     const long long blast = (long long)(((unsigned long long)(unsigned)__shfl_sync(0xFFFFFFFFu, d1.y, cnt - 1) << 32) |
                                         (unsigned)__shfl_sync(0xFFFFFFFFu, d1.x, cnt - 1)) +
                             min((int)((lshape >> 8) & 0xFF), kMixedMaxBlocks);
-    const int nbatch = (int)min(blast - bfirst, (long long)(32 * kMixedMaxBlocks));
+    const int nbatch = (int)min(blast - bfirst, (long long)kMixedBatchBlocks);
     for (int u = lane; u < nbatch; u += 32) blkbuf[u] = P.blk[bfirst + u];
     // each lane fetches the matrix fields of its own item
     const char* l_dmat = nullptr;
@@ -911,6 +979,10 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
       }
       const unsigned vtot = __shfl_sync(0xFFFFFFFFu, voff, kMixedMaxBlocks - 1);
       voff -= vbytes;
+      // uniform item: every block full 64 x 64 16-bit codes in one layout, 64 vector columns each
+      const int panel0 = __shfl_sync(0xFFFFFFFFu, (int)((mb.src >> 2) & 1), 0);
+      const bool full = lane >= nb || (!(mb.src & 2) && mb.cols == 64 && mb.vs == 64 && (int)((mb.src >> 2) & 1) == panel0);
+      const int uniform = (__all_sync(0xFFFFFFFFu, full) && R == 64) ? 1 + panel0 : 0;
       if (lane < nb) {
         hd[8 + 4 * lane] = mb.cols | ((mb.src & 2) << 15) | ((mb.src & 4) << 15);
         hd[9 + 4 * lane] = mb.vs;
@@ -923,6 +995,7 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
         hd[1] = nb;
         hd[2] = row;
         hd[3] = flags;
+        hd[4] = uniform;
         hd[kHdNv] = nv;
         *reinterpret_cast<unsigned long long*>(hd + kHdY) = ydst;
         *reinterpret_cast<long long*>(hd + kHdLdy) = ldy;
@@ -1116,6 +1189,123 @@ __device__ __forceinline__ void consume_item(const unsigned char* stage, const i
   }
 }
 
+// Rows of more than 32 points with at most four vectors per product (the
+// byte-bound case): lane (g, j) = (lane % 8, lane / 8) owns the eight rows
+// 8g .. 8g + 7 and takes columns j, j + 4, ... of its warp's range, so that a
+// full 64 x 64 block of codes costs a lane one 16-byte load per column
+// (rows 8g .. 8g + 7 of a column are 16 contiguous bytes in both layouts),
+// the block scale multiplies the lane's vector entries, and the codes feed
+// the accumulators directly. Lanes sharing g meet at the row's end.
+template <int F, int NV2, int NVB, int CW>
+__device__ __forceinline__ void consume_item8(const unsigned char* stage, const int* hd, int nb, int R, int warp, int lane,
+                                              float (&acc)[8][NVB]) {
+  constexpr int VAREA = mixed_vec_area(NVB);
+  constexpr int CPW = 64 / CW, CPL = CPW / 4;  // columns per warp and per lane of a full block
+  static_assert(CPW % 4 == 0, "full blocks need a multiple of four columns per warp");
+  const int g = lane & 7, j = lane >> 3;
+  for (int t = 0; t < nb; t++) {
+    const int4 bh = *reinterpret_cast<const int4*>(hd + 8 + 4 * t);  // cols | flags, vs, matrix offset, scale
+    const bool f32 = (bh.x >> 16) & 1, panel = (bh.x >> 17) & 1;
+    const int C = min(bh.x & 0xFFFF, 64), vs = min(bh.y, 64);
+    const int moff = min(bh.z, kStageMat - 16) & ~15;
+    const float scale = __int_as_float(bh.w);
+    const int voff = min(hd[kHdVoff + t], VAREA - 16) & ~15;
+    const unsigned char* A = stage + kMixedHeader + moff;
+    const float* X = reinterpret_cast<const float*>(stage + kMixedHeader + kStageMat + voff);
+    if (!f32 && R == 64 && C == 64 && vs == 64) {
+      const int gb = panel ? g * panel_stride(64) : 16 * g;  // bytes: rows 8g .. 8g + 7
+      const int cb = panel ? 16 : 128;                        // bytes per column
+#pragma unroll
+      for (int u = 0; u < CPL; u++) {
+        const int c = CPW * warp + CPL * j + u;
+        const uint4 w = *reinterpret_cast<const uint4*>(A + gb + cb * c);
+        const float2 q0 = codes_to_f2<F>(w.x), q1 = codes_to_f2<F>(w.y), q2 = codes_to_f2<F>(w.z),
+                     q3 = codes_to_f2<F>(w.w);
+#pragma unroll
+        for (int v = 0; v < NV2; v++) {
+          const float xs = scale * X[v * 64 + c];
+          acc[0][v] = fmaf(q0.x, xs, acc[0][v]);
+          acc[1][v] = fmaf(q0.y, xs, acc[1][v]);
+          acc[2][v] = fmaf(q1.x, xs, acc[2][v]);
+          acc[3][v] = fmaf(q1.y, xs, acc[3][v]);
+          acc[4][v] = fmaf(q2.x, xs, acc[4][v]);
+          acc[5][v] = fmaf(q2.y, xs, acc[5][v]);
+          acc[6][v] = fmaf(q3.x, xs, acc[6][v]);
+          acc[7][v] = fmaf(q3.y, xs, acc[7][v]);
+        }
+      }
+    } else {
+      // any other block: element (row, col) at 16-bit unit row + R col (column-major) or
+      // (row / 8) (panel stride / 2) + 8 col + row % 8 (panel layout); FP32 entries column-major
+      const uint16_t* A16 = reinterpret_cast<const uint16_t*>(A);
+      const float* A32 = reinterpret_cast<const float*>(A);
+      const int c0 = (C * warp) / CW, c1 = (C * (warp + 1)) / CW;
+      const int ps2 = panel_stride(C) / 2;
+      for (int col = c0 + j; col < c1; col += 4) {
+        float q[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const int row = 8 * g + i;
+          q[i] = 0.f;
+          if (row < R)
+            q[i] = f32 ? A32[row + R * col] : code_to_f<F>(A16[panel ? g * ps2 + 8 * col + i : row + R * col]);
+        }
+#pragma unroll
+        for (int v = 0; v < NV2; v++) {
+          const float xs = scale * X[v * vs + col];
+#pragma unroll
+          for (int i = 0; i < 8; i++) acc[i][v] = fmaf(q[i], xs, acc[i][v]);
+        }
+      }
+    }
+  }
+}
+
+// A uniform item (header word 4) in the eight-rows-per-lane layout: block t's
+// codes at t * block bytes, its vector chunk at t * 64 nv floats, so a block
+// costs a lane its 16-byte code loads (issued one block ahead), one scale and
+// its vector entries.
+template <int F, int NV2, int NVB, int CW>
+__device__ __forceinline__ void consume_uniform8(const unsigned char* stage, const int* hd, int nb, int nv, bool panel,
+                                                 int warp, int lane, float (&acc)[8][NVB]) {
+  constexpr int CPW = 64 / CW, CPL = CPW / 4;
+  const int g = lane & 7, j = lane >> 3, c0 = CPW * warp + CPL * j;
+  const int bbytes = panel ? panel_block_bytes(64) : 64 * 64 * 2;
+  const unsigned char* A = stage + kMixedHeader + (panel ? g * panel_stride(64) + 16 * c0 : 16 * g + 128 * c0);
+  const int cb = panel ? 16 : 128;  // bytes per column
+  const float* X = reinterpret_cast<const float*>(stage + kMixedHeader + kStageMat) + c0;
+  uint4 w[CPL];
+#pragma unroll
+  for (int u = 0; u < CPL; u++) w[u] = *reinterpret_cast<const uint4*>(A + cb * u);
+  for (int t = 0; t < nb; t++) {
+    uint4 wn[CPL];
+    const int tn = t + 1 < nb ? t + 1 : t;
+#pragma unroll
+    for (int u = 0; u < CPL; u++) wn[u] = *reinterpret_cast<const uint4*>(A + bbytes * tn + cb * u);
+    const float scale = __int_as_float(hd[11 + 4 * t]);
+    const float* Xt = X + t * 64 * nv;
+#pragma unroll
+    for (int u = 0; u < CPL; u++) {
+      const float2 q0 = codes_to_f2<F>(w[u].x), q1 = codes_to_f2<F>(w[u].y), q2 = codes_to_f2<F>(w[u].z),
+                   q3 = codes_to_f2<F>(w[u].w);
+#pragma unroll
+      for (int v = 0; v < NV2; v++) {
+        const float xs = scale * Xt[v * 64 + u];
+        acc[0][v] = fmaf(q0.x, xs, acc[0][v]);
+        acc[1][v] = fmaf(q0.y, xs, acc[1][v]);
+        acc[2][v] = fmaf(q1.x, xs, acc[2][v]);
+        acc[3][v] = fmaf(q1.y, xs, acc[3][v]);
+        acc[4][v] = fmaf(q2.x, xs, acc[4][v]);
+        acc[5][v] = fmaf(q2.y, xs, acc[5][v]);
+        acc[6][v] = fmaf(q3.x, xs, acc[6][v]);
+        acc[7][v] = fmaf(q3.y, xs, acc[7][v]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CPL; u++) w[u] = wn[u];
+  }
+}
+
 template <int F, int NVB, int CW>
 __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStreamParams P) {
   constexpr int NST = mixed_stages(NVB, CW);
@@ -1124,7 +1314,27 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
   static_assert(NST >= 2, "at least two stages");
   extern __shared__ __align__(1024) unsigned char smem[];
   const StreamShared S = stream_shared<NST, SB>(smem);
-  stream_init<NST, CW>(S);
+  // kAsyncRows (passes of at most four vectors): rows end without a CTA-wide barrier. Every warp
+  // writes its partial sums into the row's half of the double-buffered red area and counts
+  // itself in (cnt[row parity]); the warp that completes the count sums the partials, writes y,
+  // resets the count and arrives on rowfree2[parity] (count 1), which a warp waits for before
+  // it writes that half again. Wider passes share the row's sum among all warps between the
+  // rowfull and rowfree barriers (count CW each).
+  constexpr bool kAsyncRows = NVB <= 4;
+  uint64_t* rowfree2 = S.rowfull;  // kAsyncRows: rowfree2[0], rowfree2[1] (the stream's two row barriers)
+  int* cnt = const_cast<int*>(S.abort_flag) + 1;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; s++) {
+      mbar_init(S.full + s, 1);
+      mbar_init(S.empty + s, CW);
+    }
+    mbar_init(S.rowfull, kAsyncRows ? 1 : CW);
+    mbar_init(S.rowfree, kAsyncRows ? 1 : CW);
+    *S.abort_flag = 0;
+    cnt[0] = cnt[1] = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
   const int ib = P.cta_begin[blockIdx.x], ie = P.cta_begin[blockIdx.x + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == CW) {
@@ -1137,11 +1347,16 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
   W.err = P.err;
   W.budget = P.budget;
   float* red = reinterpret_cast<float*>(S.red);
-  float acc[2][NVB];
+  // kEight: rows of more than 32 points use the eight-rows-per-lane layout (consume_item8); the
+  // other layouts keep their sums in the first two rows of acc
+  constexpr bool kEight = NVB <= 4;
+  constexpr int AR = kEight ? 8 : 2;
+  float acc[AR][NVB];
 #pragma unroll
-  for (int r = 0; r < 2; r++)
+  for (int r = 0; r < AR; r++)
 #pragma unroll
     for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
+  float(&acc2)[2][NVB] = *reinterpret_cast<float(*)[2][NVB]>(&acc[0][0]);
   int rows_done = 0;
   for (int it = 0; it < ie - ib; it++) {
     const int st = it % NST, use = it / NST;
@@ -1153,45 +1368,153 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
     double* const ydst = reinterpret_cast<double*>(*reinterpret_cast<const unsigned long long*>(hd + kHdY));
     const long long ldy = *reinterpret_cast<const long long*>(hd + kHdLdy);
     // the variant for the item's vector count (a matrix of a batch may take fewer than NVB)
-    if (NVB >= 16 && nv > 8) consume_item<F, (NVB >= 16 ? 16 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
-    else if (NVB >= 8 && nv > 4) consume_item<F, (NVB >= 8 ? 8 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
-    else if (NVB >= 4 && nv > 2) consume_item<F, (NVB >= 4 ? 4 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
-    else if (NVB >= 2 && nv > 1) consume_item<F, (NVB >= 2 ? 2 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
-    else consume_item<F, 1, NVB, CW>(stage, hd, nb, R, warp, lane, acc);
+    const bool eight = kEight && R > 32;
+    if constexpr (kEight) {
+      const int uni = hd[4];
+      if (eight && (uni == 1 || uni == 2) && nb * 64 * nv <= kMixedVecCols * NVB) {
+        const bool pnl = uni == 2;
+        if (NVB >= 4 && nv > 2) consume_uniform8<F, (NVB >= 4 ? 4 : 1), NVB, CW>(stage, hd, nb, nv, pnl, warp, lane, acc);
+        else if (NVB >= 2 && nv > 1) consume_uniform8<F, (NVB >= 2 ? 2 : 1), NVB, CW>(stage, hd, nb, nv, pnl, warp, lane, acc);
+        else consume_uniform8<F, 1, NVB, CW>(stage, hd, nb, nv, pnl, warp, lane, acc);
+      } else if (eight) {
+        if (NVB >= 4 && nv > 2) consume_item8<F, (NVB >= 4 ? 4 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
+        else if (NVB >= 2 && nv > 1) consume_item8<F, (NVB >= 2 ? 2 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc);
+        else consume_item8<F, 1, NVB, CW>(stage, hd, nb, R, warp, lane, acc);
+      }
+    }
+    if (!eight) {
+      if (NVB >= 16 && nv > 8) consume_item<F, (NVB >= 16 ? 16 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc2);
+      else if (NVB >= 8 && nv > 4) consume_item<F, (NVB >= 8 ? 8 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc2);
+      else if (NVB >= 4 && nv > 2) consume_item<F, (NVB >= 4 ? 4 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc2);
+      else if (NVB >= 2 && nv > 1) consume_item<F, (NVB >= 2 ? 2 : 1), NVB, CW>(stage, hd, nb, R, warp, lane, acc2);
+      else consume_item<F, 1, NVB, CW>(stage, hd, nb, R, warp, lane, acc2);
+    }
     __syncwarp();
     if (lane == 0) mbar_arrive(S.empty + st);
     if (flags & kItemFlagLast) {
       const bool half = R <= 32;
       const int r0 = half ? 2 * (lane & 15) : 2 * lane;
-      if (half)  // add the other half-warp's columns
+      if (eight) {  // add the columns of the lanes that share the rows (lanes g, g + 8, g + 16, g + 24)
+#pragma unroll
+        for (int r = 0; r < AR; r++)
+#pragma unroll
+          for (int v = 0; v < NVB; v++) {
+            acc[r][v] += __shfl_xor_sync(0xFFFFFFFFu, acc[r][v], 8);
+            acc[r][v] += __shfl_xor_sync(0xFFFFFFFFu, acc[r][v], 16);
+          }
+      } else if (half) {  // add the other half-warp's columns
 #pragma unroll
         for (int r = 0; r < 2; r++)
 #pragma unroll
           for (int v = 0; v < NVB; v++) acc[r][v] += __shfl_xor_sync(0xFFFFFFFFu, acc[r][v], 16);
-      if (rows_done > 0 && !warp_wait(S.rowfree, (rows_done - 1) & 1, W, S.abort_flag)) break;
-      if (!half || lane < 16)
+      }
+      const int par = kAsyncRows ? rows_done & 1 : 0;
+      if (kAsyncRows) {
+        // the half of red this row uses was last summed for row rows_done - 2
+        if (rows_done >= 2 && !warp_wait(rowfree2 + par, ((rows_done >> 1) - 1) & 1, W, S.abort_flag)) break;
+      } else if (rows_done > 0 && !warp_wait(S.rowfree, (rows_done - 1) & 1, W, S.abort_flag)) {
+        break;
+      }
+      float* redp = red + par * (CW * NVB * 64);
+      if (eight) {
+        if (lane < 8)
+#pragma unroll
+          for (int v = 0; v < NVB; v++)
+            if (v < nv) {
+              float4* dst = reinterpret_cast<float4*>(redp + (warp * NVB + v) * 64 + 8 * lane);
+              dst[0] = make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+              dst[1] = make_float4(acc[4][v], acc[5][v], acc[6][v], acc[7][v]);
+            }
+      } else if (!half || lane < 16) {
 #pragma unroll
         for (int r = 0; r < 2; r++)
 #pragma unroll
           for (int v = 0; v < NVB; v++)
-            if (v < nv) red[(warp * NVB + v) * 64 + r0 + r] = acc[r][v];
+            if (v < nv) redp[(warp * NVB + v) * 64 + r0 + r] = acc[r][v];
+      }
 #pragma unroll
-      for (int r = 0; r < 2; r++)
+      for (int r = 0; r < AR; r++)
 #pragma unroll
         for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
       __syncwarp();
-      if (lane == 0) mbar_arrive(S.rowfull);
-      if (!warp_wait(S.rowfull, rows_done & 1, W, S.abort_flag)) break;
-      for (int idx = threadIdx.x; idx < R * nv; idx += CW * 32) {
-        const int r = idx % R, v = idx / R;
-        float sum = 0.f;
+      if (!kAsyncRows) {
+        if (lane == 0) mbar_arrive(S.rowfull);
+        if (!warp_wait(S.rowfull, rows_done & 1, W, S.abort_flag)) break;
+        for (int idx = threadIdx.x; idx < R * nv; idx += CW * 32) {
+          const int r = idx % R, v = idx / R;
+          float sum = 0.f;
 #pragma unroll
-        for (int w = 0; w < CW; w++) sum += red[(w * NVB + v) * 64 + r];
-        ydst[v * ldy + row + r] = (double)sum;
+          for (int w = 0; w < CW; w++) sum += red[(w * NVB + v) * 64 + r];
+          atomicAdd(ydst + v * ldy + row + r, (double)sum);  // y was zeroed; the leaf expansion adds too
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(S.rowfree);
+        rows_done++;
+        continue;
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(S.rowfree);
+      int last = 0;
+      if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(cnt + par, 1) == CW - 1;
+      }
+      last = __shfl_sync(0xFFFFFFFFu, last, 0);
+      if (last) {  // every warp's partials of this row are in: sum them and write y
+        __threadfence_block();
+        for (int idx = lane; idx < R * nv; idx += 32) {
+          const int r = idx % R, v = idx / R;
+          float sum = 0.f;
+#pragma unroll
+          for (int w = 0; w < CW; w++) sum += redp[(w * NVB + v) * 64 + r];
+          atomicAdd(ydst + v * ldy + row + r, (double)sum);  // y was zeroed; the leaf expansion adds too
+        }
+        __syncwarp();
+        if (lane == 0) {
+          cnt[par] = 0;
+          mbar_arrive(rowfree2 + par);
+        }
+      }
       rows_done++;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- split x and leaf expansion
+// Per leaf row of every matrix of the launch: its matrix, leaf, the block
+// record of U_i and where U_i's codes are, and whether the dense phase writes
+// the row. The two kernels below run over this list; a product then runs its
+// tree phases (which need x4 first) concurrently with the dense phase (which
+// needs x4 too, and no tree result), and adds U_i yhat_i (Eq. 4) at the end.
+
+
+// x4(j) = FP32 copy of x(j), padded with zeros to a multiple of 4 per vector, and (zero_y) y(j) = 0
+// for the products whose dense phase and leaf expansion add their parts into y; one warp per row
+// job (one instance per storage format: each format's launch unit has its own)
+template <int F>
+__global__ void __launch_bounds__(256) k_split_x4(const MatDesc* __restrict__ mats, const RowJob* __restrict__ jobs,
+                                                  int64_t njobs, int zero_y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < njobs; w += nw) {
+    const RowJob J = jobs[w];
+    const MatDesc& D = mats[J.mat];
+    const int nv = D.nv;
+    if (nv <= 0) continue;
+    const int64_t off = D.leaf_off[J.leaf];
+    const int sj = (int)(D.leaf_off[J.leaf + 1] - off), spad = (sj + 3) & ~3;
+    float* xj = D.x4 + D.xp4_off[J.leaf] * nv;
+    const double* __restrict__ xs = D.x + off;
+    double* __restrict__ yz = D.y + off;
+#pragma unroll 4
+    for (int v = 0; v < nv; v++) {
+      // leaf sizes <= 64: two entries per lane
+      const double x0 = lane < sj ? __ldg(xs + v * D.ldx + lane) : 0.0;
+      const double x1 = lane + 32 < sj ? __ldg(xs + v * D.ldx + lane + 32) : 0.0;
+      if (lane < spad) xj[v * spad + lane] = __double2float_rn(x0);
+      if (lane + 32 < spad) xj[v * spad + lane + 32] = __double2float_rn(x1);
+      if (zero_y) {
+        if (lane < sj) yz[v * D.ldy + lane] = 0.0;
+        if (lane + 32 < sj) yz[v * D.ldy + lane + 32] = 0.0;
+      }
     }
   }
 }
