@@ -172,13 +172,15 @@ class H2Matrix:
 
 def generate(dim: int = 2, n: int = 4096, m: int = 32, p: int = 4, eta: float = 0.9, kernel: str = "exp",
              ell: float = 0.1, seed: int = 0, points: np.ndarray | None = None, values: bool = True,
-             coupling_values: bool = True) -> H2Matrix:
+             coupling_values: bool = True, dense_values: bool = True) -> H2Matrix:
     """Build a synthetic H^2 covariance matrix.
 
     points: optional n x dim array (original order) replacing the seeded uniform points.
     values: fill U, E, S and D (False gives only the structure).
     coupling_values: with values, also fill S (False leaves S_val None: for a handle that
     evaluates its coupling blocks from the kernel).
+    dense_values: with values, also fill D (False leaves D_val None: for a handle whose dense
+    blocks are generated on the device from the points).
     """
     lib = _load()
     h = ctypes.c_void_p()
@@ -205,8 +207,9 @@ def generate(dim: int = 2, n: int = 4096, m: int = 32, p: int = 4, eta: float = 
         A.U = np.empty(n * k)
         A.E = np.empty(max(n_nodes - 1, 0) * k * k)
         A.S_val = np.empty(nS * k * k) if coupling_values else None
-        A.D_val = np.empty(nDval)
-        lib.h2gen_fill_values(h, _p(A.U), _p(A.E), _p(A.S_val) if coupling_values else None, _p(A.D_val))
+        A.D_val = np.empty(nDval) if dense_values else None
+        lib.h2gen_fill_values(h, _p(A.U), _p(A.E), _p(A.S_val) if coupling_values else None,
+                              _p(A.D_val) if dense_values else None)
     return A
 
 
