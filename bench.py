@@ -138,17 +138,45 @@ class ClockSampler:
 # of the 2D n=2^18 workload (FP64, and int16 codes with FP32 bases); the traffic grows with the leaf
 # count, so the ratio carries over to the n=2^20 launch
 TRAFFIC_RATIO = {("fp64", False): 3184277648 / 3178496000, ("int16", True): 809942016 / 805640544}
+TRAFFIC_KERNEL = {("fp64", False): "k_dense_stream", ("int16", True): "k_dense_stream_m"}  # the kernel those counters belong to
+
+# FP32 instructions per double-float product a * x (split entry times split vector entry): the exact
+# product p, e (2), the two cross terms (2), TwoSum of the running sum (6), the small-part sum (2)
+DF_FP32_OPS = 12
+FP32_LANES_PER_SM = 128
 
 
 def dense_kernel_bytes(info: dict, A, nv: int, storage: str = "fp64", bases_fp32: bool = False) -> int:
-    """Algorithmic bytes of one dense + expansion launch: D and U once (plus one 4-byte scale per block
-    in the scaled forms), x read once, y written once (8 bytes), the leaf yhat read once."""
+    """Algorithmic bytes of one launch of the dense phase's kernel. FP64 form (D blocks and the fused
+    leaf expansion): D and U once, x read once, y written once (8 bytes), the leaf yhat read once.
+    Precision form on the CUDA cores (D blocks only; the expansion runs in the downsweep): D codes
+    and one 4-byte scale per block, x once (FP32), y written once (8 bytes). Tensor-core pass (D
+    blocks with the fused expansion): D codes and U codes with their scales, x once, y once, yhat."""
     nDval = int(A.D_valoff[-1])
     if storage == "fp64":
         return 8 * (nDval + A.n * A.k) + 8 * A.n * nv * 2 + 8 * A.leaves * A.k * nv
+    if dense_kernel_name(A, nv, storage, bases_fp32) == "k_dense_stream_m":
+        return 2 * nDval + 4 * A.nD + 4 * A.n * nv + 8 * A.n * nv
     u_bytes = 4 if bases_fp32 else 2
     return (2 * nDval + u_bytes * A.n * A.k + 4 * (A.nD + A.leaves) + 4 * A.n * nv + 8 * A.n * nv
             + 4 * A.leaves * A.k * nv)
+
+
+def sm_count(dev) -> int:
+    import torch
+
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def df_peak_products(dev) -> float:
+    """Peak double-float products per second on the FP32 pipes: 128 FP32 lanes per SM x SMs x the
+    measured maximum SM clock / 12 FP32 instructions per product."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mhz = 2070.0
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return FP32_LANES_PER_SM * sm_count(dev) * mhz * 1e6 / DF_FP32_OPS
 
 
 def dense_kernel_name(A, nv: int, storage: str, bases_fp32: bool) -> str:
@@ -248,7 +276,11 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    M.profile(True)
+    # The FP64 form runs its phases in order: per-phase events inside the timed region give the dense
+    # kernel's duration live. A scaled form runs its dense phase beside the tree phases (events
+    # between phases would serialize them), so it is timed plain and its phases are timed after.
+    live_phases = args.storage == "fp64"
+    M.profile(live_phases)
     M.profile_read()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev.index) as clk:
@@ -258,8 +290,16 @@ def main():
             step()
         e1.record(stream)
         barrier()
-    phase_ms, launches = M.profile_read()
-    M.profile(False)
+    if live_phases:
+        phase_ms, launches = M.profile_read()
+        M.profile(False)
+    else:
+        M.profile(True)
+        M.profile_read()
+        for _ in range(args.steps):
+            step()
+        phase_ms, launches = M.profile_read()
+        M.profile(False)
     ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_step = ms / args.steps
     gbs = job_rate(info["paper_bytes"], world, ms_step * 1e-3) / 1e9
@@ -273,7 +313,10 @@ def main():
     roofline = {"kernel": kname + " (dense blocks + leaf expansion)", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                 "traffic": (round(TRAFFIC_RATIO[(args.storage, args.bases_fp32)] * dbytes)
-                            if (args.storage, args.bases_fp32) in TRAFFIC_RATIO and nv == 1 else None),
+                            if (args.storage, args.bases_fp32) in TRAFFIC_RATIO and nv == 1
+                            and TRAFFIC_KERNEL[(args.storage, args.bases_fp32)] == kname else None),
+                "duration_source": ("CUDA events between phases inside the timed region" if live_phases else
+                                    "CUDA events between phases, separate run of the same steps"),
                 "bytes_per_launch": dbytes,
                 "phase_share": {k: round(v / max(sum(phase_ms.values()), 1e-9), 4) for k, v in phase_ms.items()}}
 
@@ -331,6 +374,27 @@ def main():
         out["nv16"] = {"ms_per_step": round(ms16, 4), "vectors_per_s": round(16 * world / (ms16 * 1e-3), 1),
                        "GBs": round(info["paper_bytes"] * world / (ms16 * 1e-3) / 1e9, 1),
                        "rel_err_vs_oracle": oracle.rel_l2(y16.cpu().numpy(), oracle.matvec(A, x16_np))}
+        if args.storage == "fp64":
+            # at 16 vectors the FP64 form's dense phase is bound by double-float arithmetic on the FP32
+            # pipes, not by HBM: products per second of its kernel against that peak
+            M.profile(True)
+            M.profile_read()
+            for _ in range(steps16):
+                M.matvec(x16, y16, stream=stream)
+            ph16, _ = M.profile_read()
+            M.profile(False)
+            d16_ms = ph16["dense_expand"] / steps16
+            prods = 16 * (int(A.D_valoff[-1]) + A.n * A.k)
+            peak = df_peak_products(dev)
+            ach = prods / (d16_ms * 1e-3)
+            hbm_frac = dense_kernel_bytes(info, A, 16) / (d16_ms * 1e-3) / 1e9 / hbm
+            out["nv16"]["roofline"] = {
+                "kernel": "k_dense_stream (dense blocks + leaf expansion, 16 vectors)", "bound": "alu",
+                "achieved": round(ach / 1e12, 4), "peak": round(peak / 1e12, 4), "unit": "T double-float products/s",
+                "frac": round(ach / peak, 4), "hbm_frac": round(hbm_frac, 4),
+                "peak_derivation": f"{FP32_LANES_PER_SM} FP32 lanes x {sm_count(dev)} SMs x max SM clock / "
+                                   f"{DF_FP32_OPS} FP32 instructions per product",
+                "products_per_launch": prods, "kernel_ms": round(d16_ms, 4)}
 
         # precision form (per-block scaled 16-bit S and D; U, V, E, F in FP32 or 16-bit) at several vector counts
         out["mixed"] = mixed_lines(h2, A, info, dev, stream, y_ref, x_np, args.steps, world, rank)
@@ -421,8 +485,6 @@ def kernel_coupling_lines(h2, A, dev, stream, y_ref, x_np, steps, world, form="i
                 M.matvec(X, Y, stream=stream)
             M.check(stream)
             k = max(3, steps // (1 + nv // 8))
-            M.profile(True)
-            M.profile_read()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
@@ -430,9 +492,13 @@ def kernel_coupling_lines(h2, A, dev, stream, y_ref, x_np, steps, world, form="i
                 M.matvec(X, Y, stream=stream)
             e1.record(stream)
             torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            M.profile(True)  # the coupling phase alone (profiled products keep the phases in order)
+            M.profile_read()
+            for _ in range(k):
+                M.matvec(X, Y, stream=stream)
             phase, _ = M.profile_read()
             M.profile(False)
-            ms = e0.elapsed_time(e1) / k
             lines.append({"coupling": coupling, "storage": form, "bases_fp32": bases, "nv": nv,
                           "ms_per_step": round(ms, 4), "coupling_ms": round(phase["coupling"] / k, 4),
                           "vectors_per_s": round(nv * world / (ms * 1e-3), 1), "stored_bytes": info["paper_bytes"],
@@ -594,8 +660,6 @@ def kernel_coupling_main(h2, args, cfg, dev, dist, world, rank):
                 M.matvec(X, Y)
             M.check()
             k = max(3, args.steps // (1 + nv // 4))
-            M.profile(True)
-            M.profile_read()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             if dist is not None:
                 dist.barrier()
@@ -605,9 +669,13 @@ def kernel_coupling_main(h2, args, cfg, dev, dist, world, rank):
                 M.matvec(X, Y)
             e1.record()
             torch.cuda.synchronize()
+            ms = max_over_ranks(e0.elapsed_time(e1) / k, dist, dev)
+            M.profile(True)  # per-phase times from a separate run (profiled products keep the phases in order)
+            M.profile_read()
+            for _ in range(k):
+                M.matvec(X, Y)
             phase, launches = M.profile_read()
             M.profile(False)
-            ms = max_over_ranks(e0.elapsed_time(e1) / k, dist, dev)
             yr = Y[:, 0].cpu().numpy()[rows]
             err = float(np.linalg.norm(yr - exact[:, 0]) / np.linalg.norm(exact[:, 0]))
             lines.append({"nv": nv, "tuned": tuned, "ms_per_step": round(ms, 4),

@@ -683,10 +683,12 @@ h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, doubl
     T.nv = nv;
     T.err = h->err;
     T.budget = h->budget;
-    h->prof.launches += h->storage == H2_FP16_SCALED ? 8 : 7;  // set_calls, split, 3 tree, (vmax,) vscale, tc
+    h->prof.launches += h->storage == H2_FP16_SCALED ? 7 : 6;  // set_calls, 3 tree, (vmax,) vscale, tc
     return mixed_launch(h->storage, L, 1u << bucket_of(nv), st, &T);
   }
-  h->prof.launches += 6;  // set_calls, split, upsweep, coupling, downsweep (+ expansion), dense
+  // set_calls, upsweep, coupling, downsweep (+ expansion), dense; the split of x when the dense phase
+  // runs beside the tree phases (passes of up to four vectors, not profiled)
+  h->prof.launches += 5 + (bucket_of(nv) <= 2 && !h->prof.on ? 1 : 0);
   return mixed_launch(h->storage, L, 1u << bucket_of(nv), st);
 }
 
@@ -956,7 +958,8 @@ h2_status h2_batch_matvec(h2_batch b, const int32_t* nv, const double* const* x,
     h2_status s = set_calls(static_cast<h2::MatDesc*>(L.mats), count, pnv.data(), px.data(), pldx.data(), py.data(),
                             pldy.data(), st);
     if (s != H2_OK) return s;
-    b->prof.launches += (count + kCallChunk - 1) / kCallChunk + 3 * bucket_count(buckets) + 2;
+    b->prof.launches += (count + kCallChunk - 1) / kCallChunk + 3 * bucket_count(buckets) + 1 +
+                        (31 - __builtin_clz(buckets | 1u) <= 2 && !b->prof.on ? 1 : 0);
     s = mixed_launch(b->storage, L, buckets, st);
     if (s != H2_OK) return s;
   }

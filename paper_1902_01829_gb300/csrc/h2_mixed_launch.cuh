@@ -27,9 +27,11 @@ void prefer_max_shared(K kernel) {
 }
 
 // the tree and coupling launches of one vector-count bucket (phase 0: upsweep, 1: coupling, 2: downsweep)
-// expand: the downsweep ends with the leaf expansion (y was zeroed and the dense phase adds its part)
+// convert: the upsweep's leaf projection writes the FP32 copy of x (no split kernel ran);
+// expand: the downsweep ends with the leaf expansion: 0 none (the tensor-core pass fuses it),
+// 1 added to y (zeroed; the dense phase adds beside it), 2 assigned (the dense phase adds after)
 template <int F, int FB, int RPL, int NVB>
-void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st, bool expand) {
+void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st, bool convert, int expand) {
   using namespace h2;
   static const bool carveout = [] {
     constexpr int NVW = NVB < 4 ? NVB : 4, VG = NVB / NVW;
@@ -46,7 +48,7 @@ void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st, bo
   const MatDesc* mats = static_cast<const MatDesc*>(L.mats);
   const unsigned tree_threads = kTreeWarpsM * 32;
   if (phase == 0 && L.njobs > 0) {
-    k_upsweep_tree_m<FB, RPL, NVB><<<(unsigned)L.njobs, tree_threads, 0, st>>>(mats, L.jobs, nvlo, NVB);
+    k_upsweep_tree_m<FB, RPL, NVB><<<(unsigned)L.njobs, tree_threads, 0, st>>>(mats, L.jobs, nvlo, NVB, convert ? 1 : 0);
   } else if (phase == 1 && L.nchunks > 0) {
     const unsigned cgrid = (unsigned)((L.nchunks + 3) / 4);
     const int k = L.k;
@@ -70,18 +72,18 @@ void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st, bo
       k_coupling_m_generic<F, RPL, NVB><<<cgrid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
     }
   } else if (phase == 2 && L.njobs > 0) {
-    k_downsweep_tree_m<FB, RPL, NVB><<<(unsigned)L.njobs, tree_threads, 0, st>>>(mats, L.jobs, nvlo, NVB, expand ? 1 : 0);
+    k_downsweep_tree_m<FB, RPL, NVB><<<(unsigned)L.njobs, tree_threads, 0, st>>>(mats, L.jobs, nvlo, NVB, expand);
   }
 }
 
 template <int F, int FB, int RPL>
-void bucket_dispatch(const MixedLaunch& L, int phase, int b, cudaStream_t st, bool expand) {
+void bucket_dispatch(const MixedLaunch& L, int phase, int b, cudaStream_t st, bool convert, int expand) {
   switch (b) {
-    case 0: return bucket_phase<F, FB, RPL, 1>(L, phase, kBucketLo[0], st, expand);
-    case 1: return bucket_phase<F, FB, RPL, 2>(L, phase, kBucketLo[1], st, expand);
-    case 2: return bucket_phase<F, FB, RPL, 4>(L, phase, kBucketLo[2], st, expand);
-    case 3: return bucket_phase<F, FB, RPL, 8>(L, phase, kBucketLo[3], st, expand);
-    default: return bucket_phase<F, FB, RPL, 16>(L, phase, kBucketLo[4], st, expand);
+    case 0: return bucket_phase<F, FB, RPL, 1>(L, phase, kBucketLo[0], st, convert, expand);
+    case 1: return bucket_phase<F, FB, RPL, 2>(L, phase, kBucketLo[1], st, convert, expand);
+    case 2: return bucket_phase<F, FB, RPL, 4>(L, phase, kBucketLo[2], st, convert, expand);
+    case 3: return bucket_phase<F, FB, RPL, 8>(L, phase, kBucketLo[3], st, convert, expand);
+    default: return bucket_phase<F, FB, RPL, 16>(L, phase, kBucketLo[4], st, convert, expand);
   }
 }
 
@@ -155,24 +157,19 @@ h2_status tc_launch(const TcCall& T, cudaStream_t st) {
 }
 
 // The phase launches; the caller has written the product's fields into the matrix table and
-// recorded the first profiling mark. x is first copied to FP32 (k_split_x4). On the CUDA cores
-// the dense phase streams the D blocks only and adds its row sums into y (zeroed by the split),
-// and the downsweep ends with the leaf expansion U_i yhat_i, added the same way; so passes of up
-// to four vectors run the dense phase on the caller's stream while the tree phases (upsweep,
-// coupling, downsweep) run on L.side. The tensor-core pass fuses the expansion into its dense
-// phase and runs after the tree phases, and so do wider passes and profiled products (events
-// between the phases).
+// recorded the first profiling mark. On the CUDA cores the dense phase streams the D blocks only
+// and adds its row sums into y; the downsweep ends with the leaf expansion U_i yhat_i. Passes of
+// up to four vectors (not profiled) run the dense phase on the caller's stream while the tree
+// phases (upsweep, coupling, downsweep) run on L.side: k_split_x4 first copies x to FP32 and
+// zeroes y, and both sides add into y. Other passes run the phases in order: the leaf projection
+// copies x itself, the expansion assigns y and the dense phase adds after it. The tensor-core
+// pass fuses the expansion into its dense phase.
 template <int F, int FB, int RPL>
 h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {
   cudaError_t me = cudaSuccess;
   auto mk = [&]() {
     if (L.prof && me == cudaSuccess) me = mark(L.prof, st);
   };
-  const bool expand = !tc;  // the CUDA-core dense phase leaves the expansion to the downsweep
-  const long long swarps = std::min<long long>(L.nrjobs, (long long)L.grid * 64);
-  h2::k_split_x4<F><<<(unsigned)((swarps + 7) / 8), 256, 0, st>>>(static_cast<const h2::MatDesc*>(L.mats),
-                                                              static_cast<const h2::RowJob*>(L.rjobs), L.nrjobs,
-                                                              expand ? 1 : 0);
   const int top = 31 - __builtin_clz(buckets | 1u);
   auto dense = [&](cudaStream_t ds) -> h2_status {
     return tc         ? tc_launch<F>(*tc, ds)
@@ -187,20 +184,23 @@ h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st, 
   const bool overlap = !tc && top <= 2 && !(L.prof && L.prof->on) && L.side && L.ev_fork && L.ev_join;
   h2_status s = H2_OK;
   if (overlap) {
+    const long long swarps = std::min<long long>(L.nrjobs, (long long)L.grid * 64);
+    h2::k_split_x4<F><<<(unsigned)((swarps + 7) / 8), 256, 0, st>>>(static_cast<const h2::MatDesc*>(L.mats),
+                                                                static_cast<const h2::RowJob*>(L.rjobs), L.nrjobs, 1);
     cudaError_t e = cudaEventRecord(L.ev_fork, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(L.side, L.ev_fork, 0);
     if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "fork to the side stream: %s", cudaGetErrorString(e));
     if ((s = dense(st)) != H2_OK) return s;
     for (int phase = 0; phase < 3; phase++)
       for (int b = 0; b < kBuckets; b++)
-        if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, L.side, expand);
+        if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, L.side, false, 1);
     e = cudaEventRecord(L.ev_join, L.side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, L.ev_join, 0);
     if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "join from the side stream: %s", cudaGetErrorString(e));
   } else {
     for (int phase = 0; phase < 3; phase++) {
       for (int b = 0; b < kBuckets; b++)
-        if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, st, expand);
+        if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, st, true, tc ? 0 : 2);
       mk();
     }
     if ((s = dense(st)) != H2_OK) return s;

@@ -257,14 +257,40 @@ __device__ __forceinline__ void stage_vectors(float* __restrict__ dst, const flo
 // Each warp stages the vector block it multiplies (a leaf's x chunk, a child's xhat, a
 // parent's yhat: nv x up to 64 floats) in its own shared-memory buffer wbuf, so that
 // warp_mv_m's many reads of it are shared-memory reads.
+// convert: x(j) is read in FP64 and its FP32 copy written to x4 here (products whose phases run
+// in order); else k_split_x4 wrote x4 before the launch
 template <int F, int RPL, int NVB>
-__device__ __forceinline__ void project_leaf_m(const TreeParamsM& P, int64_t j, int lane, float* wbuf) {
+__device__ __forceinline__ void project_leaf_m(const TreeParamsM& P, int64_t j, int lane, float* wbuf, bool convert) {
   const int64_t leaf0 = ((int64_t)1 << P.q) - 1;
   const int64_t off = P.leaf_off[j];
   const int sj = (int)(P.leaf_off[j + 1] - off);
   const int spad = (sj + 3) & ~3;
-  // the FP32 copy of x(j) (k_split_x4, padding zero) into the warp's buffer
-  stage_vectors<false>(wbuf, P.x4 + P.xp4_off[j] * P.nv, P.nv * spad, lane);
+  float* xj = P.x4 + P.xp4_off[j] * P.nv;
+  if (convert) {
+    const double* __restrict__ xs = P.x + off;
+    // every load of the chunk is issued before any store (the stores could alias x for the compiler)
+    float xr[NVB][2];
+#pragma unroll
+    for (int v = 0; v < NVB; v++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int a = lane + 32 * h;
+        xr[v][h] = (v < P.nv && a < sj) ? __double2float_rn(__ldg(xs + v * P.ldx + a)) : 0.f;  // padding is zero
+      }
+#pragma unroll
+    for (int v = 0; v < NVB; v++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int a = lane + 32 * h;
+        if (v < P.nv && a < spad) {
+          xj[v * spad + a] = xr[v][h];
+          wbuf[v * spad + a] = xr[v][h];
+        }
+      }
+    __syncwarp();
+  } else {
+    stage_vectors<false>(wbuf, xj, P.nv * spad, lane);  // the FP32 copy of x(j), padding zero
+  }
   float acc[RPL][NVB];
 #pragma unroll
   for (int r = 0; r < RPL; r++)
@@ -306,7 +332,8 @@ __host__ __device__ constexpr int slice_vectors() { return NVB >= kTreeWarpsM ? 
 template <int F, int RPL, int NVB>
 // (the matrices whose vector count lies outside [nvlo, nvhi] are left to another launch: all their CTAs return)
 __global__ void __launch_bounds__(kTreeWarpsM * 32) k_upsweep_tree_m(const MatDesc* __restrict__ mats,
-                                                                    const int2* __restrict__ jobs, int nvlo, int nvhi) {
+                                                                    const int2* __restrict__ jobs, int nvlo, int nvhi,
+                                                                    int convert) {
   __shared__ __align__(16) float wstage[kTreeWarpsM][NVB * 64];
   const int2 job = jobs[blockIdx.x];
   const TreeParamsM P = tree_params(mats[job.x]);
@@ -316,7 +343,7 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_upsweep_tree_m(const MatDe
   const int T = P.q - P.L;
   const int64_t sub = job.y;
   for (int64_t t = warp; t < ((int64_t)1 << T); t += kTreeWarpsM)
-    project_leaf_m<F, RPL, NVB>(P, (sub << T) + t, lane, wbuf);
+    project_leaf_m<F, RPL, NVB>(P, (sub << T) + t, lane, wbuf, convert != 0);
   __syncthreads();
   for (int lvl = P.q - 1; lvl >= P.L; lvl--) {
     const int64_t node0 = ((int64_t)1 << lvl) - 1 + (sub << (lvl - P.L));
@@ -349,12 +376,13 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_upsweep_tree_m(const MatDe
 }
 
 // the whole downsweep in one launch (see k_downsweep_tree)
-// y(j) += scale * U_j yhat_j for leaf j (Eq. 4) with FP64 atomic adds: the dense phase adds its
-// part of the row the same way (both into a y zeroed before the product), so the two may run at
-// the same time. U_j is size_j x k, FP32 entries or 16-bit codes of format FB (column-major or
-// panel layout); its place and scale come from the matrix's row job and block record.
+// Leaf expansion of leaf j (Eq. 4): y(j) = scale * U_j yhat_j (assign: the dense phase runs
+// afterwards and adds its part), or y(j) += scale * U_j yhat_j with FP64 atomic adds (the dense
+// phase adds its part the same way at the same time, both into a y zeroed before the product).
+// U_j is size_j x k, FP32 entries or 16-bit codes of format FB (column-major or panel layout);
+// its place and scale come from the matrix's row job and block record.
 template <int FB, int NVB>
-__device__ __forceinline__ void expand_leaf_m(const MatDesc& D, int64_t j, int lane, float* wbuf) {
+__device__ __forceinline__ void expand_leaf_m(const MatDesc& D, int64_t j, int lane, float* wbuf, bool assign) {
   const RowJob J = D.rjobs[j];
   const MixedBlock mb = D.blk[J.ublk];
   const int nv = D.nv, k = D.k, kp = D.kp;
@@ -401,7 +429,12 @@ __device__ __forceinline__ void expand_leaf_m(const MatDesc& D, int64_t j, int l
     if (row >= R) continue;
 #pragma unroll
     for (int v = 0; v < NVB; v++)
-      if (v < nv) atomicAdd(D.y + v * D.ldy + off + row, (double)(mb.scale * acc[r][v]));
+      if (v < nv) {
+        double* yp = D.y + v * D.ldy + off + row;
+        const double val = (double)(mb.scale * acc[r][v]);
+        if (assign) *yp = val;
+        else atomicAdd(yp, val);
+      }
   }
   __syncwarp();  // wbuf is reused by the warp's next leaf
 }
@@ -409,7 +442,7 @@ __device__ __forceinline__ void expand_leaf_m(const MatDesc& D, int64_t j, int l
 template <int F, int RPL, int NVB>
 __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(const MatDesc* __restrict__ mats,
                                                                       const int2* __restrict__ jobs, int nvlo,
-                                                                      int nvhi, int expand) {
+                                                                      int nvhi, int expand) {  // 0 none, 1 add, 2 assign
   __shared__ float path[2][NVB][64];
   __shared__ __align__(16) float wstage[kTreeWarpsM][NVB * 64];
   const int2 job = jobs[blockIdx.x];
@@ -481,7 +514,8 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(const Mat
   if (expand) {
     const MatDesc& D = mats[job.x];
     const int T = P.q - P.L;
-    for (int64_t t = warp; t < ((int64_t)1 << T); t += kTreeWarpsM) expand_leaf_m<F, NVB>(D, (sub << T) + t, lane, wbuf);
+    for (int64_t t = warp; t < ((int64_t)1 << T); t += kTreeWarpsM)
+      expand_leaf_m<F, NVB>(D, (sub << T) + t, lane, wbuf, expand == 2);
   }
 }
 
