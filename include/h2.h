@@ -175,6 +175,24 @@ typedef struct {
 h2_status h2_create_kernel_coupling(const h2_desc* d, const h2_coupling_kernel* kc, h2_handle* out);
 
 /*
+ * As h2_create_kernel_coupling, and the dense blocks are generated on the
+ * device instead of copied from the host: D_ij[a][b] = K(x_a, x_b) for the
+ * points x of the two leaves (Sec. 2.2, Sec. 4.6), evaluated in FP64 and
+ * quantized block by block with the rule of the storage form (h2_storage), so
+ * that no host array of dense values is needed. d->D_val is ignored (it may
+ * be NULL); d->D_rowptr and d->D_colidx give the block structure; U and E
+ * come from d as in h2_create.
+ *   kc       the kernel and the Chebyshev nodes, as for h2_create_kernel_coupling
+ *   points   host FP64, n * kc->dim finite values: point a of the cluster order
+ *            at points + a * dim. Copied; the caller keeps ownership.
+ * Kernel values on the device may differ from a host evaluation in the last
+ * bit, so a code may differ by one unit where a value lies at a rounding
+ * boundary. Errors: those of h2_create_kernel_coupling; H2_ERR_INVALID
+ * (points NULL or not finite).
+ */
+h2_status h2_create_generated(const h2_desc* d, const h2_coupling_kernel* kc, const double* points, h2_handle* out);
+
+/*
  * y = A^H x for nv right-hand sides (Sec. 4, all phases), asynchronously on
  * `stream` (a cudaStream_t; NULL = legacy default stream).
  *   x   device FP64, n x nv, column-major, leading dimension ldx >= n

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
 
 # every symbol include/h2.h declares
 EXPORTS = ["h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
-           "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
+           "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_create_generated", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
            "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_tune", "h2_batch_destroy",
            "h2_last_error"]
 PHASES = ["upsweep", "coupling", "downsweep", "dense_expand"]
@@ -59,6 +59,7 @@ def _load():
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.h2_create.argtypes = [ctypes.POINTER(h2_desc), ctypes.POINTER(vp)]
     lib.h2_create_kernel_coupling.argtypes = [ctypes.POINTER(h2_desc), ctypes.POINTER(h2_coupling_kernel), ctypes.POINTER(vp)]
+    lib.h2_create_generated.argtypes = [ctypes.POINTER(h2_desc), ctypes.POINTER(h2_coupling_kernel), vp, ctypes.POINTER(vp)]
     lib.h2_matvec.argtypes = [vp, i32, vp, i64, vp, i64, vp]
     lib.h2_matvec_host.argtypes = [vp, i32, vp, i64, vp, i64, vp]
     lib.h2_info.argtypes = [vp, vp]
@@ -79,7 +80,7 @@ def _load():
     lib.h2_tune.argtypes = [vp, i32, vp, i64, vp, i64, vp, vp]
     lib.h2_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.h2_last_error.restype = ctypes.c_char_p
-    for name in ("h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
+    for name in ("h2_create", "h2_create_kernel_coupling", "h2_create_generated", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
                  "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
                  "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy",
                  "h2_tune", "h2_batch_tune"):
@@ -119,10 +120,13 @@ class H2Matrix:
     """An H^2 matrix resident on the current CUDA device (h2_create / h2_destroy)."""
 
     def __init__(self, *, n, depth, rank, leaf_offset, U, E, S_rowptr, S_colidx, S_val, D_rowptr, D_colidx, D_val,
-                 V=None, F=None, storage="fp64", check_cover=False, bases_fp32=False, coupling_kernel=None):
+                 V=None, F=None, storage="fp64", check_cover=False, bases_fp32=False, coupling_kernel=None,
+                 points=None):
         """coupling_kernel: None (S_val stored), or dict(kernel="exp"|"matern32", ell, cheb) with cheb the
         (n_nodes, dim, p) Chebyshev nodes of every node: the coupling blocks are then evaluated from the
-        kernel at the interpolation points in every product (h2_create_kernel_coupling), S_val unused."""
+        kernel at the interpolation points in every product (h2_create_kernel_coupling), S_val unused.
+        points: with coupling_kernel, the (n, dim) points in cluster order: the dense blocks are then
+        generated on the device from the kernel (h2_create_generated), D_val unused."""
         sym = V is None and F is None
         keep = dict(leaf_offset=np.ascontiguousarray(leaf_offset, dtype=np.int64),
                     U=np.ascontiguousarray(U, dtype=np.float64), E=np.ascontiguousarray(E, dtype=np.float64),
@@ -133,7 +137,7 @@ class H2Matrix:
                     S_val=None if coupling_kernel is not None else np.ascontiguousarray(S_val, dtype=np.float64),
                     D_rowptr=np.ascontiguousarray(D_rowptr, dtype=np.int32),
                     D_colidx=np.ascontiguousarray(D_colidx, dtype=np.int32),
-                    D_val=np.ascontiguousarray(D_val, dtype=np.float64))
+                    D_val=None if points is not None else np.ascontiguousarray(D_val, dtype=np.float64))
         d = h2_desc(n=int(n), depth=int(depth), rank=int(rank), symmetric=1 if sym else 0, storage=STORAGE[storage],
                     check_cover=1 if check_cover else 0, bases_fp32=1 if bases_fp32 else 0,
                     **{key: _ptr(val) for key, val in keep.items()})
@@ -144,21 +148,31 @@ class H2Matrix:
             cheb = np.ascontiguousarray(coupling_kernel["cheb"], dtype=np.float64)
             kc = h2_coupling_kernel(kernel=KERNELS[coupling_kernel["kernel"]], dim=int(cheb.shape[1]),
                                     p=int(cheb.shape[2]), reserved=0, ell=float(coupling_kernel["ell"]), cheb=_ptr(cheb))
-            _check(_lib.h2_create_kernel_coupling(ctypes.byref(d), ctypes.byref(kc), ctypes.byref(self._h)))
+            if points is None:
+                _check(_lib.h2_create_kernel_coupling(ctypes.byref(d), ctypes.byref(kc), ctypes.byref(self._h)))
+            else:
+                pts = np.ascontiguousarray(points, dtype=np.float64)
+                _check(_lib.h2_create_generated(ctypes.byref(d), ctypes.byref(kc), _ptr(pts), ctypes.byref(self._h)))
         self.n = int(n)
 
     @classmethod
-    def from_generator(cls, A, storage="fp64", check_cover=False, bases_fp32=False, coupling="stored") -> "H2Matrix":
+    def from_generator(cls, A, storage="fp64", check_cover=False, bases_fp32=False, coupling="stored",
+                       dense="stored") -> "H2Matrix":
         """From an object with the generator's arrays (h2gen.H2Matrix). coupling="kernel" evaluates the
-        coupling blocks from the generator's kernel at its interpolation points in every product."""
+        coupling blocks from the generator's kernel at its interpolation points in every product;
+        dense="generated" (with coupling="kernel") generates the dense blocks on the device from the
+        generator's points."""
         ck = None
         if coupling == "kernel":
             ck = dict(kernel=A.kernel, ell=A.ell, cheb=A.chebyshev_nodes())
         elif coupling != "stored":
             raise ValueError(f"coupling={coupling!r}: 'stored' or 'kernel'")
+        if dense not in ("stored", "generated") or (dense == "generated" and ck is None):
+            raise ValueError(f"dense={dense!r}: 'stored', or 'generated' with coupling='kernel'")
         return cls(n=A.n, depth=A.q, rank=A.k, leaf_offset=A.leaf_offset, U=A.U, E=A.E, S_rowptr=A.S_rowptr,
                    S_colidx=A.S_colidx, S_val=A.S_val, D_rowptr=A.D_rowptr, D_colidx=A.D_colidx, D_val=A.D_val,
-                   storage=storage, check_cover=check_cover, bases_fp32=bases_fp32, coupling_kernel=ck)
+                   storage=storage, check_cover=check_cover, bases_fp32=bases_fp32, coupling_kernel=ck,
+                   points=A.points if dense == "generated" else None)
 
     def matvec(self, x, y=None, stream=None):
         """y = A^H x on the device. x, y: torch float64 CUDA tensors, shape (n,) or (n, nv) column-major."""

@@ -256,8 +256,10 @@ h2_status check_cover(const h2_desc* d, int64_t leaves) {
   return H2_OK;
 }
 
-// s_values: the coupling values are part of the description (not evaluated from a kernel)
-h2_status validate(const h2_desc* d, bool s_values, int64_t* nS, int64_t* nD, int64_t* nDval, int* m_max) {
+// s_values / d_values: the coupling / dense values are part of the description (not evaluated
+// from a kernel)
+h2_status validate(const h2_desc* d, bool s_values, bool d_values, int64_t* nS, int64_t* nD, int64_t* nDval,
+                   int* m_max) {
   if (!d) return fail(H2_ERR_INVALID, "desc is NULL");
   if (d->n < 1) return fail(H2_ERR_INVALID, "n = %lld < 1", (long long)d->n);
   if (d->n >= ((int64_t)1 << 31)) return fail(H2_ERR_UNSUPPORTED, "n = %lld >= 2^31", (long long)d->n);
@@ -297,7 +299,8 @@ h2_status validate(const h2_desc* d, bool s_values, int64_t* nS, int64_t* nD, in
   for (int64_t r = 0; r < leaves; r++)
     if (d->D_rowptr[r + 1] < d->D_rowptr[r]) return fail(H2_ERR_INVALID, "D_rowptr decreases at row %lld", (long long)r);
   *nD = d->D_rowptr[leaves];
-  if (*nD > 0 && (!d->D_colidx || !d->D_val)) return fail(H2_ERR_INVALID, "D_colidx/D_val NULL with %lld blocks", (long long)*nD);
+  if (*nD > 0 && (!d->D_colidx || (d_values && !d->D_val)))
+    return fail(H2_ERR_INVALID, "D_colidx/D_val NULL with %lld blocks", (long long)*nD);
   int64_t dv = 0;
   for (int64_t r = 0; r < leaves; r++)
     for (int32_t b = d->D_rowptr[r]; b < d->D_rowptr[r + 1]; b++) {
@@ -318,7 +321,7 @@ h2_status validate(const h2_desc* d, bool s_values, int64_t* nS, int64_t* nD, in
   }
   if (s_values && *nS && !values_ok(d->S_val, *nS * k * k, &bad, f32))
     return fail(H2_ERR_INVALID, "S_val[%lld] is not finite or too large", (long long)bad);
-  if (*nD && !values_ok(d->D_val, dv, &bad, f32))
+  if (d_values && *nD && !values_ok(d->D_val, dv, &bad, f32))
     return fail(H2_ERR_INVALID, "D_val[%lld] is not finite or too large", (long long)bad);
   if (d->check_cover) return check_cover(d, leaves);
   return H2_OK;
@@ -707,14 +710,16 @@ h2_status build_device(h2_matrix_s* h, const h2_desc* d) {
 }  // namespace
 
 // h2_create, or h2_create_kernel_coupling with kc (already checked): the coupling phase then
-// evaluates the blocks from the kernel and stores none
-h2_status create_handle(const h2_desc* d, const h2_coupling_kernel* kc, h2_handle* out) {
+// evaluates the blocks from the kernel and stores none; with gen_points (h2_create_generated,
+// already checked) the dense blocks are generated on the device from the points
+h2_status create_handle(const h2_desc* d, const h2_coupling_kernel* kc, h2_handle* out,
+                        const double* gen_points = nullptr) {
   if (!kc) g_err.clear();
   if (!out) return fail(H2_ERR_INVALID, "out is NULL");
   *out = nullptr;
   int64_t nS = 0, nD = 0, nDval = 0;
   int m_max = 0;
-  h2_status st = validate(d, kc == nullptr, &nS, &nD, &nDval, &m_max);
+  h2_status st = validate(d, kc == nullptr, gen_points == nullptr, &nS, &nD, &nDval, &m_max);
   if (st != H2_OK) return st;
   h2_matrix_s* h = new (std::nothrow) h2_matrix_s();
   if (!h) return fail(H2_ERR_OOM, "host allocation failed");
@@ -732,6 +737,7 @@ h2_status create_handle(const h2_desc* d, const h2_coupling_kernel* kc, h2_handl
   h->lr = h->k > 32 ? 32 : pow2ceil(h->k);
   h->storage = d->storage;
   h->kc = kc;
+  h->gen_points = gen_points;
   h->kf = kc != nullptr;
   if (kc) {
     h->kf_kind = kc->kernel;
@@ -743,6 +749,7 @@ h2_status create_handle(const h2_desc* d, const h2_coupling_kernel* kc, h2_handl
     st = fail(H2_ERR_OOM, "host allocation failed");
   }
   h->kc = nullptr;  // the caller's description is not kept
+  h->gen_points = nullptr;
   if (st != H2_OK) {
     free_all(h);
     delete h;
@@ -765,10 +772,8 @@ const char* h2_last_error(void) { return g_err.c_str(); }
 
 h2_status h2_create(const h2_desc* d, h2_handle* out) { return create_handle(d, nullptr, out); }
 
-h2_status h2_create_kernel_coupling(const h2_desc* d, const h2_coupling_kernel* kc, h2_handle* out) {
-  g_err.clear();
-  if (!out) return fail(H2_ERR_INVALID, "out is NULL");
-  *out = nullptr;
+// checks of h2_create_kernel_coupling's kernel description; H2_OK or the failure
+static h2_status check_kernel_desc(const h2_desc* d, const h2_coupling_kernel* kc) {
   if (!d || !kc || !kc->cheb) return fail(H2_ERR_INVALID, "desc, kernel description or cheb is NULL");
   if (kc->kernel != H2_KERNEL_EXP && kc->kernel != H2_KERNEL_MATERN32)
     return fail(H2_ERR_INVALID, "kernel = %d is not an h2_kernel_kind", kc->kernel);
@@ -786,7 +791,28 @@ h2_status h2_create_kernel_coupling(const h2_desc* d, const h2_coupling_kernel* 
   int64_t bad = 0;
   if (!values_ok(kc->cheb, n_nodes * kc->dim * kc->p, &bad))
     return fail(H2_ERR_INVALID, "cheb[%lld] is not finite or too large", (long long)bad);
+  return H2_OK;
+}
+
+h2_status h2_create_kernel_coupling(const h2_desc* d, const h2_coupling_kernel* kc, h2_handle* out) {
+  g_err.clear();
+  if (!out) return fail(H2_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  const h2_status st = check_kernel_desc(d, kc);
+  if (st != H2_OK) return st;
   return create_handle(d, kc, out);
+}
+
+h2_status h2_create_generated(const h2_desc* d, const h2_coupling_kernel* kc, const double* points, h2_handle* out) {
+  g_err.clear();
+  if (!out) return fail(H2_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  h2_status st = check_kernel_desc(d, kc);
+  if (st != H2_OK) return st;
+  int64_t bad = 0;
+  if (!points) return fail(H2_ERR_INVALID, "points is NULL");
+  if (!values_ok(points, d->n * kc->dim, &bad, false)) return fail(H2_ERR_INVALID, "points[%lld] is not finite", (long long)bad);
+  return create_handle(d, kc, out, points);
 }
 
 h2_status h2_matvec(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream) {

@@ -162,6 +162,7 @@ struct h2_matrix_s {
   int q = 0, k = 0, kp = 0, m_max = 0, lr = 32, grid = 0;
   int storage = H2_FP64;
   const h2_coupling_kernel* kc = nullptr;  // while h2_create_kernel_coupling builds the handle
+  const double* gen_points = nullptr;      // while h2_create_generated builds the handle (host, n x dim)
   bool kf = false;                         // coupling blocks evaluated from the kernel
   int kf_kind = 0;
   float kf_inv_ell = 0.f;

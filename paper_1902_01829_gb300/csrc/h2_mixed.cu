@@ -177,6 +177,124 @@ h2_status set_calls(h2::MatDesc* mats, int64_t count, const int* nv, const doubl
 
 }  // namespace
 
+// ---------------------------------------------------------------- dense blocks generated on the device
+// D_ij[a][b] = K(x_a, x_b) for the points of leaves i and j (Sec. 2.2, Sec. 4.6), evaluated in FP64
+// exactly as the host generator evaluates it, then quantized with the host quantizer's rule
+// (quantize() above): sigma = fl32(max |a|) (int16: fl32(max |a| / 32767)), codes of a / sigma
+// rounded to nearest even (int16: rint, clamped to +-32767, offset by 32768). One CTA per block.
+struct GenDense {
+  const double* pts;        // n x dim, cluster order
+  const int64_t* leaf_off;  // [leaves + 1]
+  const int32_t* brow;      // per dense block: row leaf, column leaf
+  const int32_t* bcol;
+  const int64_t* bbyte;     // byte offset of the block's codes in dmat
+  const int64_t* bglob;     // index of the block's record
+  int64_t nblocks;
+  unsigned char* dmat;
+  h2::MixedBlock* blk;
+  double ell;
+  int dim, kind, panel;
+};
+
+template <int F>
+__device__ __forceinline__ uint16_t gen_code(double v, float sigma) {
+  if (sigma == 0.0f) return F == h2::kFormInt16 ? 32768u : 0u;
+  const double r = v / (double)sigma;
+  if constexpr (F == h2::kFormFp16) return __half_as_ushort(__double2half(r));
+  else if constexpr (F == h2::kFormBf16) return __bfloat16_as_ushort(__double2bfloat16(r));
+  else return (uint16_t)((int)fmin(32767.0, fmax(-32767.0, rint(r))) + 32768);
+}
+
+template <int F>
+__global__ void __launch_bounds__(256) k_gen_dense(GenDense a) {
+  __shared__ double xs[2][64 * 3];
+  __shared__ double wmax[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < a.nblocks; t += gridDim.x) {
+    const int i = a.brow[t], j = a.bcol[t];
+    const int64_t oi = a.leaf_off[i], oj = a.leaf_off[j];
+    const int si = (int)(a.leaf_off[i + 1] - oi < 64 ? a.leaf_off[i + 1] - oi : 64);
+    const int sj = (int)(a.leaf_off[j + 1] - oj < 64 ? a.leaf_off[j + 1] - oj : 64);
+    for (int e = threadIdx.x; e < si * a.dim; e += 256) xs[0][e] = a.pts[oi * a.dim + e];
+    for (int e = threadIdx.x; e < sj * a.dim; e += 256) xs[1][e] = a.pts[oj * a.dim + e];
+    __syncthreads();
+    double v[16];
+    double m = 0.0;
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int e = threadIdx.x + 256 * u;
+      v[u] = 0.0;
+      if (e < si * sj) {
+        const int r = e % si, c = e / si;
+        double r2 = 0.0;
+        for (int d = 0; d < a.dim; d++) {
+          const double df = xs[0][r * a.dim + d] - xs[1][c * a.dim + d];
+          r2 += df * df;
+        }
+        const double rr = sqrt(r2);
+        double kv;
+        if (a.kind == H2_KERNEL_EXP) {
+          kv = exp(-rr / a.ell);
+        } else {
+          const double s = 1.7320508075688772 * rr / a.ell;
+          kv = (1.0 + s) * exp(-s);
+        }
+        v[u] = kv;
+        m = fmax(m, fabs(kv));
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
+    if (lane == 0) wmax[warp] = m;
+    __syncthreads();
+    m = wmax[0];
+#pragma unroll
+    for (int w = 1; w < 8; w++) m = fmax(m, wmax[w]);
+    const float sigma = F == h2::kFormInt16 ? (float)(m / 32767.0) : (float)m;
+    uint16_t* dst = reinterpret_cast<uint16_t*>(a.dmat + a.bbyte[t]);
+    const int ps2 = h2::panel_stride(sj) / 2;
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int e = threadIdx.x + 256 * u;
+      if (e < si * sj) {
+        const int r = e % si, c = e / si;
+        dst[a.panel ? (r >> 3) * ps2 + 8 * c + (r & 7) : r + si * c] = gen_code<F>(v[u], sigma);
+      }
+    }
+    if (threadIdx.x == 0) a.blk[a.bglob[t]].scale = sigma;
+    __syncthreads();  // xs and wmax are reused by the next block
+  }
+}
+
+// copy blocks of whole 16-byte words: block t from src + soff[t] to dst + doff[t] (bytes[t] bytes)
+__global__ void k_scatter_blocks(const unsigned char* __restrict__ src, const int64_t* __restrict__ soff,
+                                 unsigned char* __restrict__ dst, const int64_t* __restrict__ doff,
+                                 const int64_t* __restrict__ bytes, int64_t nblocks) {
+  for (int64_t t = blockIdx.x; t < nblocks; t += gridDim.x) {
+    const int4* s = reinterpret_cast<const int4*>(src + soff[t]);
+    int4* d = reinterpret_cast<int4*>(dst + doff[t]);
+    for (int64_t w = threadIdx.x; w < bytes[t] / 16; w += blockDim.x) d[w] = s[w];
+  }
+}
+
+// device buffer freed when it goes out of scope (temporaries of a handle's creation)
+template <class T>
+struct DevTemp {
+  T* p = nullptr;
+  ~DevTemp() {
+    if (p) cudaFree(p);
+  }
+  h2_status put(const T* src, int64_t count) {
+    cudaError_t e = cudaMalloc(&p, (size_t)std::max<int64_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess && count > 0) e = cudaMemcpy(p, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return h2_fail(e == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA, "temporary device buffer: %s",
+                     cudaGetErrorString(e));
+    }
+    return H2_OK;
+  }
+};
+
 static_assert(h2i::kDenseCW == h2::kMixedCW, "dense-stream consumer warps");
 
 // The dense stream's producer stages the block records of 32 consecutive items of a CTA at a
@@ -396,7 +514,14 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
     }
     row_blk0[leaves] = h->nD + leaves;
     const int64_t nblk = h->nD + leaves, total = boff[nblk];  // bytes
-    std::vector<unsigned char> bytes_host((size_t)total, 0);
+    // dense blocks generated on the device: the host assembles only the U blocks, compactly
+    const bool gen = h->gen_points != nullptr;
+    std::vector<int64_t> uoffc(gen ? (size_t)leaves + 1 : 0, 0);
+    for (int64_t i = 0; gen && i < leaves; i++) {
+      const int64_t g1 = row_blk0[i + 1] - 1;
+      uoffc[i + 1] = uoffc[i] + (boff[g1 + 1] - boff[g1]);
+    }
+    std::vector<unsigned char> bytes_host((size_t)(gen ? uoffc[leaves] : total), 0);
     unsigned char* base = bytes_host.data();
     std::vector<h2::MixedBlock> blk((size_t)nblk);
 #pragma omp parallel
@@ -416,7 +541,9 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
           const int32_t j = d->D_colidx[b];
           const int64_t sj = lo[j + 1] - lo[j];
           h2::MixedBlock& m = blk[g];
-          if (panel) {
+          if (gen) {
+            m.scale = 0.f;  // the device writes the codes and the scale
+          } else if (panel) {
             tmp.resize((size_t)(si * sj));
             m.scale = quantize(d->D_val + doff[b], si * sj, form, tmp.data());
             to_panels(sj, reinterpret_cast<uint16_t*>(base + boff[g]));
@@ -429,18 +556,19 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
           m.src = panel ? 4 : 0;
         }
         h2::MixedBlock& m = blk[g];  // U_i, multiplied with yhat of leaf i
+        unsigned char* ub = gen ? base + uoffc[i] : base + boff[g];
         if (M.bases_fp32) {
-          float* u = reinterpret_cast<float*>(base + boff[g]);
+          float* u = reinterpret_cast<float*>(ub);
           for (int64_t e = 0; e < si * k; e++) u[e] = (float)d->U[lo[i] * k + e];
           m.scale = 1.0f;
           m.src = 1 | 2;
         } else if (panel) {
           tmp.resize((size_t)(si * k));
           m.scale = quantize(d->U + lo[i] * k, si * k, form, tmp.data());
-          to_panels(k, reinterpret_cast<uint16_t*>(base + boff[g]));
+          to_panels(k, reinterpret_cast<uint16_t*>(ub));
           m.src = 1 | 4;
         } else {
-          m.scale = quantize(d->U + lo[i] * k, si * k, form, reinterpret_cast<uint16_t*>(base + boff[g]));
+          m.scale = quantize(d->U + lo[i] * k, si * k, form, reinterpret_cast<uint16_t*>(ub));
           m.src = 1;
         }
         m.voff = (h->leaf0 + i) * M.kp4;
@@ -448,21 +576,87 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
         m.vs = (unsigned char)M.kp4;
       }
     }
+    unsigned char* dm = nullptr;
+    h2::MixedBlock* dblk = nullptr;
+    if (!gen) {
+      if ((st = upload(h, &dm, base, total)) != H2_OK) return st;
+      if ((st = upload(h, &dblk, blk.data(), nblk)) != H2_OK) return st;
+    } else {
+      // the U blocks go to their places; every dense block is evaluated and quantized on the device
+      if ((st = dalloc(h, &dm, total)) != H2_OK) return st;
+      CUDA_TRY(cudaMemset(dm, 0, (size_t)total));
+      if ((st = upload(h, &dblk, blk.data(), nblk)) != H2_OK) return st;
+      {
+        std::vector<int64_t> soff((size_t)leaves), doffu((size_t)leaves), ubytes((size_t)leaves);
+        for (int64_t i = 0; i < leaves; i++) {
+          const int64_t g1 = row_blk0[i + 1] - 1;
+          soff[i] = uoffc[i];
+          doffu[i] = boff[g1];
+          ubytes[i] = boff[g1 + 1] - boff[g1];
+        }
+        DevTemp<unsigned char> tu;
+        DevTemp<int64_t> ts, td, tb;
+        if ((st = tu.put(base, uoffc[leaves])) != H2_OK || (st = ts.put(soff.data(), leaves)) != H2_OK ||
+            (st = td.put(doffu.data(), leaves)) != H2_OK || (st = tb.put(ubytes.data(), leaves)) != H2_OK)
+          return st;
+        k_scatter_blocks<<<(unsigned)std::min<int64_t>(leaves, 8 * h->grid), 128>>>(tu.p, ts.p, dm, td.p, tb.p, leaves);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaDeviceSynchronize());
+      }
+      {
+        std::vector<int32_t> brow((size_t)h->nD), bcol((size_t)h->nD);
+        std::vector<int64_t> bbyte((size_t)h->nD), bglob((size_t)h->nD);
+        for (int64_t i = 0; i < leaves; i++) {
+          int64_t g = row_blk0[i];
+          for (int32_t b = d->D_rowptr[i]; b < d->D_rowptr[i + 1]; b++, g++) {
+            brow[b] = (int32_t)i;
+            bcol[b] = d->D_colidx[b];
+            bbyte[b] = boff[g];
+            bglob[b] = g;
+          }
+        }
+        const int dim = h->kc->dim;
+        DevTemp<double> tp;
+        DevTemp<int32_t> tr, tc;
+        DevTemp<int64_t> tby, tgl;
+        if ((st = tp.put(h->gen_points, h->n * dim)) != H2_OK || (st = tr.put(brow.data(), h->nD)) != H2_OK ||
+            (st = tc.put(bcol.data(), h->nD)) != H2_OK || (st = tby.put(bbyte.data(), h->nD)) != H2_OK ||
+            (st = tgl.put(bglob.data(), h->nD)) != H2_OK)
+          return st;
+        GenDense ga{};
+        ga.pts = tp.p;
+        ga.leaf_off = h->leaf_off;
+        ga.brow = tr.p;
+        ga.bcol = tc.p;
+        ga.bbyte = tby.p;
+        ga.bglob = tgl.p;
+        ga.nblocks = h->nD;
+        ga.dmat = dm;
+        ga.blk = dblk;
+        ga.ell = h->kc->ell;
+        ga.dim = dim;
+        ga.kind = h->kc->kernel;
+        ga.panel = panel ? 1 : 0;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(h->nD, 16 * h->grid));
+        if (form == h2::kFormFp16) k_gen_dense<h2::kFormFp16><<<grid, 256>>>(ga);
+        else if (form == h2::kFormBf16) k_gen_dense<h2::kFormBf16><<<grid, 256>>>(ga);
+        else k_gen_dense<h2::kFormInt16><<<grid, 256>>>(ga);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaDeviceSynchronize());
+      }
+      CUDA_TRY(cudaMemcpy(blk.data(), dblk, (size_t)nblk * sizeof(h2::MixedBlock), cudaMemcpyDeviceToHost));
+    }
+    M.dmat = dm;
+    M.dblk = dblk;
     for (int64_t g = 0; g < nblk; g++) {
       float& mx = (blk[g].src & 1) ? M.umax : M.dmax;
       mx = std::max(mx, blk[g].scale);
     }
-    unsigned char* dm = nullptr;
-    if ((st = upload(h, &dm, base, total)) != H2_OK) return st;
-    M.dmat = dm;
-    h2::MixedBlock* dblk = nullptr;
-    if ((st = upload(h, &dblk, blk.data(), nblk)) != H2_OK) return st;
-    M.dblk = dblk;
 
     // work items: consecutive dense blocks of one row, at most kMixedMaxBlocks blocks, 32 KB of
     // entries and kMixedVecCols vector columns per item. U_i (the row's last block) is not
-    // streamed: the leaf expansion multiplies it after the downsweep (k_expand_m), so that the
-    // dense phase does not wait for the tree phases.
+    // streamed: the leaf expansion at the end of the downsweep multiplies it, so that the dense
+    // phase does not wait for the tree phases.
     std::vector<h2::StreamItem> items;
     std::vector<int64_t> row_bytes((size_t)leaves), row_item0((size_t)leaves + 1);
     std::vector<h2::RowJob> rj((size_t)leaves);

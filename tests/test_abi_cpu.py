@@ -180,3 +180,30 @@ def test_kernel_coupling_rejects_bad_descriptions(h2, small):
     assert lib.h2_create_kernel_coupling(ctypes.byref(d), ctypes.byref(kc), ctypes.byref(out)) == h2.H2_ERR_INVALID
     assert "kernel" in lib.h2_last_error().decode()
     assert out.value is None
+
+
+def test_generated_dense_rejects_bad_points(h2, small):
+    """h2_create_generated checks the kernel description and the points before touching the device."""
+    kw = _kw(small)
+    kw["D_val"] = None
+    ck = dict(kernel="exp", ell=0.1, cheb=small.chebyshev_nodes())
+
+    def expect(status, storage="fp16", points=small.points):
+        with pytest.raises(h2.H2Error) as ei:
+            h2.H2Matrix(storage=storage, coupling_kernel=ck, points=points, **kw)
+        assert ei.value.status == status, str(ei.value)
+        return str(ei.value)
+
+    assert "scaled storage" in expect(h2.H2_ERR_UNSUPPORTED, storage="fp64")
+    bad = small.points.copy()
+    bad[7, 1] = np.nan
+    assert "points[15]" in expect(h2.H2_ERR_INVALID, points=bad)
+    bad[7, 1] = -np.inf
+    assert "not finite" in expect(h2.H2_ERR_INVALID, points=bad)
+    lib = h2._lib
+    out = ctypes.c_void_p()
+    d = h2.h2_desc(n=small.n, depth=small.q, rank=small.k, storage=2)
+    kc = h2.h2_coupling_kernel(kernel=0, dim=2, p=3, reserved=0, ell=0.1,
+                               cheb=ck["cheb"].ctypes.data_as(ctypes.c_void_p))
+    assert lib.h2_create_generated(ctypes.byref(d), ctypes.byref(kc), None, ctypes.byref(out)) == h2.H2_ERR_INVALID
+    assert out.value is None
