@@ -39,6 +39,9 @@ WORKLOADS = {
                 "eta=0.9, FP64",
     "3d_n1M_kc": "3D exp(-r/0.2) covariance H^2 matvec, n=2^20 uniform points in the unit cube, m=64, k=64 (4x4x4 "
                  "Chebyshev), eta=0.9, int16 + per-block f32 scale (S none: evaluated from the kernel), f32 bases",
+    "3d_n4M_gen": "3D Matern-3/2 (length 0.1) covariance H^2 matvec, n=2^22 uniform points in the unit cube, m=64, "
+                  "k=64 (4x4x4 Chebyshev), eta=0.7, fp16 + per-block f32 scale (S none: evaluated from the kernel; "
+                  "D generated and quantized on the device from the points)",
     "batch256": "256 independent 2D exp(-r/0.1) covariance H^2 matvecs, n log-uniform in [2^12, 2^17], m=32, k=16, "
                 "eta=0.9, nv in {1, 4, 16}, fp16 storage + f32 arithmetic, one graph-captured batched product",
 }
@@ -46,7 +49,7 @@ WORKLOADS = {
 
 def replica_config(workload: str, rank: int) -> dict:
     """Weak scaling: every rank multiplies its own independent matrix of the same workload (seed per rank)."""
-    workload = {"3d_n1M_kc": "3d_n1M"}.get(workload, workload)
+    workload = {"3d_n1M_kc": "3d_n1M", "3d_n4M_gen": "3d_n4M"}.get(workload, workload)
     if workload not in h2gen.CONFIGS:
         return {}
     cfg = dict(h2gen.CONFIGS[workload])
@@ -247,8 +250,8 @@ def main():
 
     if args.workload == "batch256":
         return batch_main(h2, args, dev, dist, world, rank, hbm, peak_kind)
-    if args.workload == "3d_n1M_kc":
-        return kernel_coupling_main(h2, args, cfg, dev, dist, world, rank)
+    if args.workload in LARGE:
+        return large_main(h2, args, cfg, dev, dist, world, rank, LARGE[args.workload])
     A = h2gen.generate(**cfg)
     M = h2.H2Matrix.from_generator(A, storage=args.storage, bases_fp32=args.bases_fp32, coupling=args.coupling)
     info = M.info()
@@ -631,28 +634,46 @@ def batch_main(h2, args, dev, dist, world, rank, hbm, peak_kind):
         dist.destroy_process_group()
 
 
-def kernel_coupling_main(h2, args, cfg, dev, dist, world, rank):
-    """--workload 3d_n1M_kc: the 3D k = 64 workload at its full size, n = 2^20, which one GPU holds
-    with the coupling blocks evaluated from the kernel (their 126 GB of FP64 values are never made):
-    int16 codes + FP32 bases, nv in {1, 8, 32, 64}. The error is taken on sampled rows against the
-    exact kernel matrix, as the paper measures its large problems (Sec. 4.6)."""
+# Workloads that one GPU holds only with the coupling blocks evaluated from the kernel in every product
+# (and, for the largest, the dense blocks generated on the device): their FP64 values are never made.
+LARGE = {
+    "3d_n1M_kc": dict(storage="int16", bases_fp32=True, dense="stored", nvs=(1, 8, 32, 64), leaves=16,
+                      dtype="int16 + per-block f32 scale (stored), f32 bases / f32 (computed)"),
+    "3d_n4M_gen": dict(storage="fp16", bases_fp32=False, dense="generated", nvs=(1, 32), leaves=8,
+                       dtype="fp16 + per-block f32 scale (stored) / f32 (computed)"),
+}
+
+
+def large_main(h2, args, cfg, dev, dist, world, rank, spec):
+    """--workload 3d_n1M_kc: the 3D k = 64 workload at n = 2^20 (int16 codes + FP32 bases, nv in
+    {1, 8, 32, 64}); --workload 3d_n4M_gen: the 3D Matern-3/2 workload at n = 2^22, eta = 0.7 (fp16
+    codes, nv in {1, 32}), its dense blocks generated on the device. Both evaluate the coupling blocks
+    from the kernel. The error is taken on sampled rows against the exact kernel matrix, as the paper
+    measures its large problems (Sec. 4.6)."""
     import torch
 
     t0 = time.perf_counter()
-    A = h2gen.generate(**cfg, coupling_values=False)
-    M = h2.H2Matrix.from_generator(A, storage="int16", bases_fp32=True, coupling="kernel")
+    gen = spec["dense"] == "generated"
+    A = h2gen.generate(**cfg, coupling_values=False, dense_values=not gen)
+    t_host = time.perf_counter() - t0
+    M = h2.H2Matrix.from_generator(A, storage=spec["storage"], bases_fp32=spec["bases_fp32"], coupling="kernel",
+                                   dense=spec["dense"])
     build_s = time.perf_counter() - t0
     A.D_val = None  # the device holds the codes; free the host copy
     info = M.info()
     rng = np.random.default_rng(7 + rank)
-    leaves = rng.choice(A.leaves, size=16, replace=False)
+    leaves = rng.choice(A.leaves, size=spec["leaves"], replace=False)
     rows = np.concatenate([np.arange(A.leaf_offset[i], A.leaf_offset[i + 1]) for i in sorted(leaves)])
-    x_np = h2gen.vectors(51 + rank, A.n, 64)
+    nv_max = max(spec["nvs"])
+    x_np = h2gen.vectors(51 + rank, A.n, nv_max)
     xw = torch.from_numpy(np.ascontiguousarray(x_np.T)).to(dev).t()
     exact = A.exact_matvec_rows(rows, x_np[:, :1])
+    from oracle import rows as oracle_rows  # the checks below run outside the timed regions
+
+    ref64 = oracle_rows.sampled_rows(A, x_np[:, :1], sorted(leaves))
     lines = []
     with ClockSampler(dev.index) as clk:
-        for nv in (1, 8, 32, 64):
+        for nv in spec["nvs"]:
             X = xw[:, :nv]
             Y = torch.empty((nv, A.n), dtype=torch.float64, device=dev).t()
             tuned = M.tune(X, Y)
@@ -678,24 +699,28 @@ def kernel_coupling_main(h2, args, cfg, dev, dist, world, rank):
             M.profile(False)
             yr = Y[:, 0].cpu().numpy()[rows]
             err = float(np.linalg.norm(yr - exact[:, 0]) / np.linalg.norm(exact[:, 0]))
+            err64 = float(np.linalg.norm(yr - ref64[:, 0]) / np.linalg.norm(ref64[:, 0]))
             lines.append({"nv": nv, "tuned": tuned, "ms_per_step": round(ms, 4),
                           "GBs": round(info["paper_bytes"] * world / (ms * 1e-3) / 1e9, 1),
                           "vectors_per_s": round(nv * world / (ms * 1e-3), 1),
                           "phase_ms": {key: round(v / k, 4) for key, v in phase.items()},
                           "launches_per_step": int(launches) // k,
+                          "rel_err_vs_fp64_oracle_sampled_rows": err64,
                           "rel_err_vs_exact_kernel_sampled_rows": err})
     head = lines[0]
     out = {"metric": METRIC, "value": head["GBs"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
            "warmup": 3, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "int16 + per-block f32 scale (stored), f32 bases / f32 (computed)",
-           "data": "synthetic",
-           "config": {"workload": WORKLOADS["3d_n1M_kc"], "n": A.n, "q": A.q, "k": A.k, "nS": A.nS, "nD": A.nD,
+           "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.workload], "n": A.n, "q": A.q, "k": A.k, "nS": A.nS, "nD": A.nD,
                       "paper_bytes": info["paper_bytes"], "device_bytes": info["device_bytes"],
                       "l2": "matrix (%.1f GB) >> 129 MB L2: no flush needed" % (info["paper_bytes"] / 1e9),
-                      "error_sample": f"{rows.size} rows of 16 random leaves, first vector",
+                      "error_sample": f"{rows.size} rows of {spec['leaves']} random leaves, first vector: against "
+                                      "the FP64 H^2 oracle (the same matrix in FP64) and against the exact kernel "
+                                      "matrix (adds the H^2 approximation error)",
                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
            "vectors_per_s": max(l["vectors_per_s"] for l in lines), "gpu_launches": head["launches_per_step"] * args.steps,
-           "lines": lines, "build_s": round(build_s, 1), "clocks": clk.summary()}
+           "rel_err_vs_fp64_oracle": max(l["rel_err_vs_fp64_oracle_sampled_rows"] for l in lines),
+           "lines": lines, "build_s": round(build_s, 1), "host_structure_s": round(t_host, 1), "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(out), flush=True)
     M.close()
@@ -709,9 +734,10 @@ def reference_arm(args, cfg, world):
 
     if args.workload == "batch256":
         return reference_batch(args, world)
-    if args.workload == "3d_n1M_kc":
-        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle needs the 126 GB of stored coupling "
-                          "values that this workload never makes (it evaluates them from the kernel)"}), flush=True)
+    if args.workload in LARGE:
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle needs the stored coupling values "
+                          "(126 GB at n=2^20, 960 GB at n=2^22) that this workload never makes (it evaluates them "
+                          "from the kernel)"}), flush=True)
         return
     A = h2gen.generate(**dict(h2gen.CONFIGS[args.workload]))
     x = h2gen.vectors(77, A.n, args.nv)

@@ -88,3 +88,35 @@ def test_generated_equals_handle_from_host_values(h2):
     check(oracle.rel_l2(yg, yh), 1e-6, "generated vs host dense blocks")
     Mh.close()
     Mg.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("workload", ["3d_n1M", "3d_n4M"])
+def test_full_size_sampled_rows(h2, workload):
+    """The two large 3D workloads at their full sizes, in the launch configuration the benchmark
+    times: n = 2^20 (exp, eta = 0.9) in int16 codes with FP32 bases and stored dense blocks, and
+    n = 2^22 (Matern-3/2, eta = 0.7) in fp16 codes with its dense blocks generated on the device;
+    both evaluate the coupling blocks. The rows of 8 random leaves are compared with the oracle of
+    the stored precision form restricted to those rows (oracle/rows.py)."""
+    from oracle import rows
+
+    cfg = dict(h2gen.CONFIGS[workload])
+    gen = workload == "3d_n4M"
+    form, bases, nvs = ("fp16", False, (1, 32)) if gen else ("int16", True, (1, 64))
+    A = h2gen.generate(**cfg, coupling_values=False, dense_values=not gen)
+    M = h2.H2Matrix.from_generator(A, storage=form, bases_fp32=bases, coupling="kernel",
+                                   dense="generated" if gen else "stored")
+    A.D_val = None
+    leaves = sorted(np.random.default_rng(95).choice(A.leaves, size=8, replace=False).tolist())
+    r = np.concatenate([np.arange(A.leaf_offset[i], A.leaf_offset[i + 1]) for i in leaves])
+    for nv in nvs:
+        x = h2gen.vectors(1200 + nv, A.n, nv)
+        y = M.matvec(to_dev(x))
+        M.check()
+        got = y.cpu().numpy()[r]
+        assert np.isfinite(got).all()
+        ref = rows.sampled_rows(A, x, leaves, form=form, bases_fp32=bases)
+        tol = acc_tol(A) + KERNEL_EVAL + (tc_split_tol(form) if nv >= 8 and form != "int16" else 0.0)
+        check(oracle.rel_l2(got, ref), tol, ("full size, sampled rows", workload, form, nv))
+        del y
+    M.close()
