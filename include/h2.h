@@ -409,6 +409,92 @@ h2_status h2_batch_profile_read(h2_batch b, double ms[H2_NPHASES], int64_t* laun
 /* Free the batch's own tables (not the member handles). NULL is a no-op. */
 h2_status h2_batch_destroy(h2_batch b);
 
+/*
+ * Algebraic compression (Sec. 5): a new, orthogonal and (with eps >= 0)
+ * smaller representation of the same matrix.
+ *
+ *   orthogonalization (Sec. 5.2, Alg. 6)  U_i = Q_i T_i at the leaves (QR);
+ *       Z_p = [T_c1 E_c1; T_c2 E_c2] = Q_Z T_p at inner nodes; the halves of
+ *       Q_Z are the new transfers. Every explicit basis becomes orthonormal.
+ *   projection (Alg. 7)                   S_ij <- T^U_i S_ij (T^V_j)^T
+ *   basis generation (Sec. 5.3, Alg. 9)   R_i = triangular factor of
+ *       [R_parent E_i^T; S_ij1^T; ...; S_ijb^T] (row tree; the column tree
+ *       stacks [R_parent F_j^T; S_i1j; ...]), from R_root = 0 down
+ *   truncation (Sec. 5.4, Alg. 10)        leading left singular vectors of
+ *       W_i = U_i R_i^T (leaves) and W_p = Z_p R_p^T (inner nodes, Z_p from
+ *       the children's new T), as many per node as the level's rank: the
+ *       largest, over the level's nodes, count of singular values >= eps
+ *       times that node's largest; T = Q^T U (leaves) or Q^T Z (inner nodes)
+ *   projection again with the truncation's T
+ * QR factors are taken with a non-negative diagonal in R. Where a node's
+ * matrix has fewer singular vectors than the level rank, the missing ones
+ * are zero. FP64 throughout (Householder QR, one-sided Jacobi SVD).
+ *
+ * The result has one uniform rank k_out, the largest level rank of either
+ * tree (at least 1); levels of smaller rank are zero-padded, which leaves
+ * the matrix unchanged. It is in the h2_desc layout at rank k_out, with the
+ * input's structure and dense blocks, so it can be passed to h2_create.
+ */
+typedef struct h2_compressor_s* h2_compressor;
+
+/*
+ * Copy the matrix's bases, transfers and coupling blocks (FP64 storage form;
+ * dense values are not needed and may be NULL) to the current device and
+ * allocate the working arrays (about 4 x the coupling bytes in all).
+ * Synchronous. Errors: as h2_create, H2_ERR_UNSUPPORTED for a scaled storage
+ * form or 2^31 or more coupling blocks.
+ */
+h2_status h2_compress_create(const h2_desc* d, h2_compressor* out);
+
+/*
+ * Run on `stream` (asynchronous; nothing is allocated). eps < 0: only the
+ * orthogonalization and projection (the result has rank k); 0 <= eps < 1:
+ * the whole compression with relative threshold eps. Every run starts from
+ * the matrix given to h2_compress_create and overwrites the previous
+ * result. H2_ERR_INVALID for eps >= 1 or NaN, or another current device.
+ */
+h2_status h2_compress_run(h2_compressor c, double eps, void* stream);
+
+/*
+ * Wait for `stream`, then report the uniform rank of the result (k_out) and
+ * the rank of every level l = 0..q of the row and column trees (ranks_u,
+ * ranks_v: q + 1 entries each, may be NULL). After an eps < 0 run all are k.
+ */
+h2_status h2_compress_result(h2_compressor c, int32_t* k_out, int32_t* ranks_u, int32_t* ranks_v, void* stream);
+
+/*
+ * Copy one result array to host memory `dst` (count must be its exact size;
+ * waits for `stream`). With K = k_out and k the input rank:
+ *   H2C_U, H2C_V   leaf bases, n * K (layout of h2_desc.U at rank K)
+ *   H2C_E, H2C_F   transfers, (2^(q+1) - 2) * K * K
+ *   H2C_S          coupling blocks, nS * K * K
+ *   H2C_T_ORTHO_U, H2C_T_ORTHO_V   the orthogonalization's T of every node,
+ *                  (2^(q+1) - 1) * k * k, upper triangular (old = new * T)
+ *   H2C_R_U, H2C_R_V               the basis generation's R of every node,
+ *                  (2^(q+1) - 1) * k * k (after an eps >= 0 run)
+ *   H2C_SIGMA_U, H2C_SIGMA_V       singular values of every node's W in
+ *                  descending order, (2^(q+1) - 1) * k (after an eps >= 0 run)
+ * V, F, T_ORTHO_V, R_V and SIGMA_V equal their U counterparts for a
+ * symmetric matrix. H2_ERR_INVALID for an unknown array, a wrong count, or
+ * before the first run.
+ */
+enum {
+  H2C_U = 0, H2C_V = 1, H2C_E = 2, H2C_F = 3, H2C_S = 4, H2C_T_ORTHO_U = 5, H2C_T_ORTHO_V = 6,
+  H2C_R_U = 7, H2C_R_V = 8, H2C_SIGMA_U = 9, H2C_SIGMA_V = 10
+};
+h2_status h2_compress_read(h2_compressor c, int32_t what, double* dst, int64_t count, void* stream);
+
+/* Per-phase timing of h2_compress_run (CUDA events on its stream, recorded
+ * while enabled): 0 orthogonalization, 1 projection, 2 basis generation,
+ * 3 truncation, 4 second projection and repacking. h2_compress_profile_read
+ * waits for the last run and gives its phase times and kernel launches. */
+#define H2C_NPHASES 5
+h2_status h2_compress_profile(h2_compressor c, int32_t enable);
+h2_status h2_compress_profile_read(h2_compressor c, double ms[H2C_NPHASES], int64_t* launches);
+
+/* Free the compressor's device arrays. NULL is a no-op. */
+h2_status h2_compress_destroy(h2_compressor c);
+
 /* Message of the calling thread's last failed call ("" if none). Valid until the next call. */
 const char* h2_last_error(void);
 

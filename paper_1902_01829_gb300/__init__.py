@@ -24,8 +24,12 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
 EXPORTS = ["h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
            "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_create_generated", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
            "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_tune", "h2_batch_destroy",
-           "h2_last_error"]
+           "h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read", "h2_compress_profile",
+           "h2_compress_profile_read", "h2_compress_destroy", "h2_last_error"]
 PHASES = ["upsweep", "coupling", "downsweep", "dense_expand"]
+COMPRESS_PHASES = ["orthogonalize", "project", "basis_generation", "truncate", "project_truncated"]
+COMPRESS_ARRAYS = {"U": 0, "V": 1, "E": 2, "F": 3, "S": 4, "T_ortho_U": 5, "T_ortho_V": 6, "R_U": 7, "R_V": 8,
+                   "sigma_U": 9, "sigma_V": 10}
 
 
 class H2Error(RuntimeError):
@@ -79,8 +83,16 @@ def _load():
     lib.h2_batch_profile_read.argtypes = [vp, vp, vp]
     lib.h2_tune.argtypes = [vp, i32, vp, i64, vp, i64, vp, vp]
     lib.h2_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.h2_compress_create.argtypes = [ctypes.POINTER(h2_desc), ctypes.POINTER(vp)]
+    lib.h2_compress_run.argtypes = [vp, ctypes.c_double, vp]
+    lib.h2_compress_result.argtypes = [vp, vp, vp, vp, vp]
+    lib.h2_compress_read.argtypes = [vp, i32, vp, i64, vp]
+    lib.h2_compress_profile.argtypes = [vp, i32]
+    lib.h2_compress_profile_read.argtypes = [vp, vp, vp]
+    lib.h2_compress_destroy.argtypes = [vp]
     lib.h2_last_error.restype = ctypes.c_char_p
-    for name in ("h2_create", "h2_create_kernel_coupling", "h2_create_generated", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
+    for name in ("h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read",
+                 "h2_compress_profile", "h2_compress_profile_read", "h2_compress_destroy", "h2_create", "h2_create_kernel_coupling", "h2_create_generated", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
                  "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
                  "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy",
                  "h2_tune", "h2_batch_tune"):
@@ -334,6 +346,79 @@ class H2Batch:
         if getattr(self, "_b", None) is not None and self._b.value:
             _lib.h2_batch_destroy(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Compressor:
+    """Algebraic compression of an FP64 H^2 matrix on the current CUDA device
+    (h2_compress_create / h2_compress_run / h2_compress_read / h2_compress_destroy)."""
+
+    def __init__(self, *, n, depth, rank, leaf_offset, U, E, S_rowptr, S_colidx, S_val, D_rowptr, D_colidx,
+                 V=None, F=None):
+        sym = V is None and F is None
+        keep = dict(leaf_offset=np.ascontiguousarray(leaf_offset, dtype=np.int64),
+                    U=np.ascontiguousarray(U, dtype=np.float64), E=np.ascontiguousarray(E, dtype=np.float64),
+                    V=None if sym else np.ascontiguousarray(V, dtype=np.float64),
+                    F=None if sym else np.ascontiguousarray(F, dtype=np.float64),
+                    S_rowptr=np.ascontiguousarray(S_rowptr, dtype=np.int32),
+                    S_colidx=np.ascontiguousarray(S_colidx, dtype=np.int32),
+                    S_val=np.ascontiguousarray(S_val, dtype=np.float64),
+                    D_rowptr=np.ascontiguousarray(D_rowptr, dtype=np.int32),
+                    D_colidx=np.ascontiguousarray(D_colidx, dtype=np.int32))
+        d = h2_desc(n=int(n), depth=int(depth), rank=int(rank), symmetric=1 if sym else 0, storage=STORAGE["fp64"],
+                    check_cover=0, bases_fp32=0, D_val=None, **{key: _ptr(val) for key, val in keep.items()})
+        self._c = ctypes.c_void_p()
+        _check(_lib.h2_compress_create(ctypes.byref(d), ctypes.byref(self._c)))
+        self.n, self.q, self.k, self.sym = int(n), int(depth), int(rank), sym
+        self.nS = int(keep["S_colidx"].size)
+
+    @classmethod
+    def from_generator(cls, A, V=None, F=None) -> "Compressor":
+        return cls(n=A.n, depth=A.q, rank=A.k, leaf_offset=A.leaf_offset, U=A.U, E=A.E, S_rowptr=A.S_rowptr,
+                   S_colidx=A.S_colidx, S_val=A.S_val, D_rowptr=A.D_rowptr, D_colidx=A.D_colidx, V=V, F=F)
+
+    def run(self, eps: float, stream=None):
+        """eps < 0: orthogonalize and project only; 0 <= eps < 1: the whole compression (asynchronous)."""
+        _check(_lib.h2_compress_run(self._c, float(eps), _stream_ptr(stream)))
+
+    def result(self, stream=None) -> tuple[int, list, list]:
+        """(uniform rank, row-tree level ranks, column-tree level ranks); waits for the stream."""
+        k = np.zeros(1, dtype=np.int32)
+        ru = np.zeros(self.q + 1, dtype=np.int32)
+        rv = np.zeros(self.q + 1, dtype=np.int32)
+        _check(_lib.h2_compress_result(self._c, _ptr(k), _ptr(ru), _ptr(rv), _stream_ptr(stream)))
+        return int(k[0]), ru.tolist(), rv.tolist()
+
+    def read(self, what: str, stream=None) -> np.ndarray:
+        """One result array (see COMPRESS_ARRAYS) as a flat numpy array."""
+        K = self.result(stream)[0]
+        nodes = (2 << self.q) - 1
+        size = {"U": self.n * K, "V": self.n * K, "E": (nodes - 1) * K * K, "F": (nodes - 1) * K * K,
+                "S": self.nS * K * K, "T_ortho_U": nodes * self.k ** 2, "T_ortho_V": nodes * self.k ** 2,
+                "R_U": nodes * self.k ** 2, "R_V": nodes * self.k ** 2, "sigma_U": nodes * self.k,
+                "sigma_V": nodes * self.k}[what]
+        out = np.empty(size, dtype=np.float64)
+        _check(_lib.h2_compress_read(self._c, COMPRESS_ARRAYS[what], _ptr(out), size, _stream_ptr(stream)))
+        return out
+
+    def profile(self, enable: bool = True):
+        _check(_lib.h2_compress_profile(self._c, 1 if enable else 0))
+
+    def profile_read(self) -> tuple[dict, int]:
+        ms = np.zeros(len(COMPRESS_PHASES), dtype=np.float64)
+        n = np.zeros(1, dtype=np.int64)
+        _check(_lib.h2_compress_profile_read(self._c, _ptr(ms), _ptr(n)))
+        return dict(zip(COMPRESS_PHASES, ms.tolist())), int(n[0])
+
+    def close(self):
+        if getattr(self, "_c", None) is not None and self._c.value:
+            _lib.h2_compress_destroy(self._c)
+            self._c = ctypes.c_void_p()
 
     def __del__(self):
         try:

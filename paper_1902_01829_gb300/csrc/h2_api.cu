@@ -343,6 +343,11 @@ void transpose_block(const double* src, double* dst, int64_t rows, int64_t cols)
 
 namespace h2i {
 
+h2_status validate_desc(const h2_desc* d, bool s_values, bool d_values, int64_t* nS, int64_t* nD, int64_t* nDval,
+                        int* m_max) {
+  return validate(d, s_values, d_values, nS, nD, nDval, m_max);
+}
+
 // Split rows (row r weighs row_bytes[r] and starts at item row_item0[r]) into
 // `grid` contiguous ranges of about equal weight; returns each range's first item.
 std::vector<int> balance(const std::vector<int64_t>& row_bytes, const std::vector<int64_t>& row_item0, int grid) {

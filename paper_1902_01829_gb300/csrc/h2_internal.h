@@ -244,6 +244,10 @@ h2_status profile_read(Profiler* p, double ms[H2_NPHASES], int64_t* launches);
 void profile_free(Profiler* p);
 // precision form: device layout (h2_create) and one product pass of up to kPassVectors vectors
 h2_status mixed_build(h2_matrix_s* h, const h2_desc* d);
+// structural and value checks of a description (h2_create's); s_values / d_values: the
+// coupling / dense values are part of it
+h2_status validate_desc(const h2_desc* d, bool s_values, bool d_values, int64_t* nS, int64_t* nD, int64_t* nDval,
+                        int* m_max);
 // one product pass; buckets: bit b set when some matrix has a vector count in bucket b
 h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc = nullptr);
 // precision form: use coupling chunk target option `chunk_opt`, `cw` dense consumer warps and

@@ -207,3 +207,33 @@ def test_generated_dense_rejects_bad_points(h2, small):
                                cheb=ck["cheb"].ctypes.data_as(ctypes.c_void_p))
     assert lib.h2_create_generated(ctypes.byref(d), ctypes.byref(kc), None, ctypes.byref(out)) == h2.H2_ERR_INVALID
     assert out.value is None
+
+
+def test_compressor_rejects_bad_input(h2, small):
+    """h2_compress_create validates like h2_create and takes only the FP64 form; the other
+    compression entry points reject a NULL compressor."""
+    kw = _kw(small)
+    kw.pop("D_val")
+    bad = dict(kw, S_rowptr=kw["S_rowptr"].copy())
+    bad["S_rowptr"][3] = bad["S_rowptr"][4] + 1
+    with pytest.raises(h2.H2Error) as ei:
+        h2.Compressor(**bad)
+    assert ei.value.status == h2.H2_ERR_INVALID and "decreases" in str(ei.value)
+    lib = h2._lib
+    out = ctypes.c_void_p()
+    d = h2.h2_desc(n=small.n, depth=small.q, rank=small.k, symmetric=1, storage=h2.STORAGE["fp16"],
+                   leaf_offset=kw["leaf_offset"].ctypes.data_as(ctypes.c_void_p),
+                   U=small.U.ctypes.data_as(ctypes.c_void_p), E=small.E.ctypes.data_as(ctypes.c_void_p),
+                   S_rowptr=kw["S_rowptr"].ctypes.data_as(ctypes.c_void_p),
+                   S_colidx=kw["S_colidx"].ctypes.data_as(ctypes.c_void_p),
+                   S_val=small.S_val.ctypes.data_as(ctypes.c_void_p),
+                   D_rowptr=kw["D_rowptr"].ctypes.data_as(ctypes.c_void_p),
+                   D_colidx=kw["D_colidx"].ctypes.data_as(ctypes.c_void_p))
+    assert lib.h2_compress_create(ctypes.byref(d), ctypes.byref(out)) == h2.H2_ERR_UNSUPPORTED
+    assert out.value is None
+    assert lib.h2_compress_create(None, ctypes.byref(out)) == h2.H2_ERR_INVALID
+    assert lib.h2_compress_run(None, 1e-7, None) == h2.H2_ERR_INVALID
+    assert lib.h2_compress_result(None, None, None, None, None) == h2.H2_ERR_INVALID
+    assert lib.h2_compress_read(None, 0, None, 0, None) == h2.H2_ERR_INVALID
+    assert lib.h2_compress_profile_read(None, None, None) == h2.H2_ERR_INVALID
+    assert lib.h2_compress_destroy(None) == h2.H2_OK
