@@ -42,6 +42,11 @@ WORKLOADS = {
     "3d_n4M_gen": "3D Matern-3/2 (length 0.1) covariance H^2 matvec, n=2^22 uniform points in the unit cube, m=64, "
                   "k=64 (4x4x4 Chebyshev), eta=0.7, fp16 + per-block f32 scale (S none: evaluated from the kernel; "
                   "D generated and quantized on the device from the points)",
+    "compress_2d": "algebraic compression (Sec. 5: orthogonalization, basis generation, truncation, projection) of the "
+                   "2D exp(-r/0.1) covariance H^2 matrix, n=2^20 uniform points, m=64, k=64 (8x8 Chebyshev), eta=0.9, "
+                   "FP64, relative threshold 1e-7",
+    "compress_3d": "algebraic compression (Sec. 5) of the 3D exp(-r/0.2) covariance H^2 matrix, n=2^18 uniform points "
+                   "in the unit cube, m=64, k=64 (4x4x4 Chebyshev), eta=0.9, FP64, relative threshold 1e-3",
     "batch256": "256 independent 2D exp(-r/0.1) covariance H^2 matvecs, n log-uniform in [2^12, 2^17], m=32, k=16, "
                 "eta=0.9, nv in {1, 4, 16}, fp16 storage + f32 arithmetic, one graph-captured batched product",
 }
@@ -182,6 +187,194 @@ def df_peak_products(dev) -> float:
     return FP32_LANES_PER_SM * sm_count(dev) * mhz * 1e6 / DF_FP32_OPS
 
 
+FP64_FMA_PER_SM_CYCLE = 2   # GB300: 152 SMs x 2 FP64 FMA per cycle x 2.07 GHz x 2 = 1.26 TFLOP/s (nominal 1.25)
+
+
+def fp64_peak_flops(dev) -> float:
+    """FP64 FLOP/s: 2 FP64 FMA per SM per cycle x SMs x the measured maximum SM clock x 2 flops."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mhz = 2070.0
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return 2.0 * FP64_FMA_PER_SM_CYCLE * sm_count(dev) * mhz * 1e6
+
+
+def compress_kernel_flops(A, K: int) -> dict:
+    """FP64 flops each compression kernel computes, counted from what it does per unit:
+    k_project: two K x K x K products per coupling block (4 K^3);
+    k_basis_gen: per coupling block the Householder reduction of K stacked rows against the
+    triangular factor (per column j, a dot product and an update of K rows for the K - j - 1
+    later columns: 4 K sum_j (K - j - 1) = 2 K^2 (K - 1)), per node R_parent E^T (K^2 (K + 1))
+    and the QR of that K x K product (4 K^3 / 3)."""
+    nodes = (2 << A.q) - 1
+    return {"k_project": 4 * K ** 3 * A.nS,
+            "k_basis_gen": 2 * K * K * (K - 1) * A.nS + (nodes - 1) * (K * K * (K + 1) + 4 * K ** 3 // 3)}
+
+
+COMPRESS = {
+    "compress_2d": dict(cfg=dict(dim=2, n=1 << 20, m=64, p=8, eta=0.9, kernel="exp", ell=0.1, seed=2), eps=1e-7,
+                        oracle_n=1 << 14),
+    "compress_3d": dict(cfg=dict(dim=3, n=1 << 18, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=3), eps=1e-3,
+                        oracle_n=1 << 13),
+    # the small line of the default run: the 2D problem at n = 2^16
+    "compress_2d_small": dict(cfg=dict(dim=2, n=1 << 16, m=64, p=8, eta=0.9, kernel="exp", ell=0.1, seed=2),
+                              eps=1e-7, oracle_n=1 << 13),
+}
+
+
+def compress_line(h2, dev, name: str, steps: int, warmup: int, cpu: bool = True) -> dict:
+    """Time h2_compress_run on one of COMPRESS's workloads (inputs resident on the device, CUDA
+    events on the stream), then: level ranks, memory of the low-rank part before and after, the
+    FP64 product before and after, the errors of the paper's compression tables (Sec. 5.6) on
+    sampled rows, the dominant kernel's roofline against the FP64 peak, and the compression
+    oracle on a smaller matrix of the same family (host cores)."""
+    import torch
+
+    spec = COMPRESS[name]
+    cfg, eps = spec["cfg"], spec["eps"]
+    t0 = time.perf_counter()
+    A = h2gen.generate(**cfg)
+    gen_s = time.perf_counter() - t0
+    cp = h2.Compressor.from_generator(A)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(1, warmup)):
+        cp.run(eps, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            cp.run(eps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    cp.profile(True)
+    cp.run(eps, stream=stream)
+    phases, launches = cp.profile_read()
+    cp.profile(False)
+    K, ru, rv = cp.result()
+    inf = cp.info()
+    U2, E2, S2 = cp.read("U"), cp.read("E"), cp.read("S")
+    cp.close()
+    nodes = (2 << A.q) - 1
+
+    def lr_bytes(k):
+        return 8 * (A.n * k + (nodes - 1) * k * k + A.nS * k * k)
+
+    # the FP64 product before and after compression (1 vector x ~ U[0, 1], as the paper's tables)
+    M1 = h2.H2Matrix.from_generator(A)
+    M2 = h2.H2Matrix(n=A.n, depth=A.q, rank=K, leaf_offset=A.leaf_offset, U=U2, E=E2, S_rowptr=A.S_rowptr,
+                     S_colidx=A.S_colidx, S_val=S2, D_rowptr=A.D_rowptr, D_colidx=A.D_colidx, D_val=A.D_val)
+    x_np = h2gen.vectors(61, A.n, 1, dist="uniform")
+    x = torch.from_numpy(np.ascontiguousarray(x_np.T)).to(dev).t()
+    hmv = {}
+    ys = {}
+    for tag, M in (("before", M1), ("after", M2)):
+        y = torch.empty((1, A.n), dtype=torch.float64, device=dev).t()
+        for _ in range(3):
+            M.matvec(x, y, stream=stream)
+        reps = 20
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            M.matvec(x, y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hmv[tag] = round(e0.elapsed_time(e1) / reps, 4)
+        ys[tag] = y[:, 0].cpu().numpy()
+    M1.close()
+    M2.close()
+    rng = np.random.default_rng(11)
+    rows = np.sort(rng.choice(A.n, size=min(A.n, 4096), replace=False))
+    ax = A.exact_matvec_rows(rows, x_np)[:, 0]
+    e_h1 = float(np.linalg.norm(ax - ys["before"][rows]) / np.linalg.norm(ax))
+    e_h2 = float(np.linalg.norm(ax - ys["after"][rows]) / np.linalg.norm(ax))
+    e_12 = float(np.linalg.norm(ys["after"] - ys["before"]) / np.linalg.norm(ys["before"]))
+    flops = compress_kernel_flops(A, A.k)
+    kern = {"k_project": phases["project"], "k_basis_gen": phases["basis_generation"]}
+    top = max(kern, key=kern.get)
+    peak = fp64_peak_flops(dev)
+    ach = flops[top] / (kern[top] * 1e-3)
+    out = {"workload": WORKLOADS.get(name, name), "n": A.n, "k": A.k, "q": A.q, "nS": A.nS, "eps": eps,
+           "ms_per_compression": round(ms, 3), "points_per_s": round(A.n / (ms * 1e-3), 1),
+           "phase_ms": {k: round(v, 3) for k, v in phases.items()}, "launches": launches,
+           "ranks_per_level": ru, "uniform_rank": K, "jacobi_sweeps": {"max": inf["max_sweeps"],
+                                                                     "mean": round(inf["total_sweeps"] / nodes, 2)},
+           "lowrank_bytes_before": lr_bytes(A.k), "lowrank_bytes_after": lr_bytes(K),
+           "hmv_ms_before": hmv["before"], "hmv_ms_after": hmv["after"],
+           "rel_err_compressed_vs_original": e_12,
+           "rel_err_vs_exact_before_sampled": e_h1, "rel_err_vs_exact_after_sampled": e_h2,
+           "error_sample": f"{rows.size} random rows, x ~ U[0,1]",
+           "roofline": {"kernel": top, "bound": "alu", "achieved": round(ach / 1e12, 4), "peak": round(peak / 1e12, 4),
+                        "unit": "TFLOP/s (FP64)", "frac": round(ach / peak, 4),
+                        "peak_derivation": f"{FP64_FMA_PER_SM_CYCLE} FP64 FMA per SM per cycle x {sm_count(dev)} SMs "
+                                           "x max SM clock x 2",
+                        "flops_per_launch_total": flops[top], "kernel_ms": round(kern[top], 3)},
+           "device_bytes": inf["device_bytes"], "generate_s": round(gen_s, 1), "clocks": clk.summary()}
+    if cpu:
+        import oracle
+        from oracle import compress as oc
+
+        B = h2gen.generate(**dict(cfg, n=spec["oracle_n"]))
+        t1 = time.perf_counter()
+        oc.compress(B, eps)
+        sec = time.perf_counter() - t1
+        out["cpu_baseline"] = {"value": round(B.n / sec, 1), "unit": "points/s", "cores": oracle.threads(),
+                               "kind": "oracle", "sample": f"the same family at n={B.n}, one compression "
+                                                           f"({sec:.2f} s; numpy, plain loops over nodes and blocks)"}
+    return out
+
+
+COMPRESS_METRIC = "H^2 algebraic compression throughput (points/s) and time, Sec. 5"
+
+
+def reference_compress(args):
+    """The compression oracle (numpy, FP64) on a bounded sample of the workload's family."""
+    import oracle
+    from oracle import compress as oc
+
+    spec = COMPRESS[args.workload]
+    B = h2gen.generate(**dict(spec["cfg"], n=spec["oracle_n"]))
+    oc.compress(B, spec["eps"])   # warm
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t = time.perf_counter()
+        oc.compress(B, spec["eps"])
+        times.append(time.perf_counter() - t)
+    sec = statistics.median(times)
+    val = round(B.n / sec, 1)
+    sample = f"the same family at n={B.n} (the workload has n={spec['cfg']['n']}), {len(times)} compressions"
+    print(json.dumps({"impl": "reference", "metric": COMPRESS_METRIC, "value": val, "unit": "points/s",
+                      "n_gpus": 1, "steps": len(times), "warmup": 1, "ms_per_step": round(sec * 1e3, 1),
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOADS[args.workload], "sample_n": B.n},
+                      "cpu_baseline": {"value": val, "unit": "points/s", "cores": oracle.threads(), "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+def compress_main(h2, args, dev, world, rank):
+    """--workload compress_2d / compress_3d: the compression as the main line (points per second)."""
+    steps, warm = max(1, min(args.steps, 5)), max(1, min(args.warmup, 3))
+    c = compress_line(h2, dev, args.workload, steps, warm)
+    out = {"metric": COMPRESS_METRIC, "value": c["points_per_s"],
+           "unit": "points/s", "n_gpus": world, "steps": steps, "warmup": warm,
+           "ms_per_step": c["ms_per_compression"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": c["workload"], "n": c["n"], "k": c["k"], "eps": c["eps"],
+                      "l2": "coupling blocks (%.1f GB) >> 129 MB L2: no flush needed" % (c["lowrank_bytes_before"] / 1e9),
+                      "parallelism": "1 GPU"},
+           "gpu_launches": c["launches"] * steps, "roofline": c["roofline"],
+           "clocks": c["clocks"], "compression": c}
+    if "cpu_baseline" in c:
+        out["cpu_baseline"] = c["cpu_baseline"]
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def dense_kernel_name(A, nv: int, storage: str, bases_fp32: bool) -> str:
     """The kernel of the dense phase: the FP64 stream, or in the precision form the tensor-core
     kernel (16-bit fp16 / bf16 codes and bases, k a multiple of 16, every leaf 64 points, 8 or
@@ -250,6 +443,8 @@ def main():
 
     if args.workload == "batch256":
         return batch_main(h2, args, dev, dist, world, rank, hbm, peak_kind)
+    if args.workload in COMPRESS:
+        return compress_main(h2, args, dev, world, rank)
     if args.workload in LARGE:
         return large_main(h2, args, cfg, dev, dist, world, rank, LARGE[args.workload])
     A = h2gen.generate(**cfg)
@@ -408,6 +603,9 @@ def main():
         # many independent matrices of uneven size in one batched, graph-captured product
         if not args.no_batch:
             out["batch"] = batch_line(h2, dev, args.steps, world, rank, hbm)
+
+        # algebraic compression (Sec. 5) of the 2D 8x8-Chebyshev problem at n = 2^16
+        out["compression"] = compress_line(h2, dev, "compress_2d_small", 3, 1, cpu=(rank == 0 and world == 1))
 
         if rank == 0 and world == 1:
             sec, reps, cores = run_oracle_baseline(A, x_np)
@@ -734,6 +932,8 @@ def reference_arm(args, cfg, world):
 
     if args.workload == "batch256":
         return reference_batch(args, world)
+    if args.workload in COMPRESS:
+        return reference_compress(args)
     if args.workload in LARGE:
         print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle needs the stored coupling values "
                           "(126 GB at n=2^20, 960 GB at n=2^22) that this workload never makes (it evaluates them "

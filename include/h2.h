@@ -492,6 +492,11 @@ h2_status h2_compress_read(h2_compressor c, int32_t what, double* dst, int64_t c
 h2_status h2_compress_profile(h2_compressor c, int32_t enable);
 h2_status h2_compress_profile_read(h2_compressor c, double ms[H2C_NPHASES], int64_t* launches);
 
+/* info[0] most one-sided Jacobi sweeps a node took in the last run, [1] their
+ * total over all nodes, [2] device bytes the compressor holds, [3] coupling
+ * blocks, [4] q, [5] input rank k. Waits for the device. */
+h2_status h2_compress_info(h2_compressor c, int64_t info[6]);
+
 /* Free the compressor's device arrays. NULL is a no-op. */
 h2_status h2_compress_destroy(h2_compressor c);
 

@@ -25,7 +25,7 @@ EXPORTS = ["h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_hos
            "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_create_generated", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
            "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_tune", "h2_batch_destroy",
            "h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read", "h2_compress_profile",
-           "h2_compress_profile_read", "h2_compress_destroy", "h2_last_error"]
+           "h2_compress_profile_read", "h2_compress_info", "h2_compress_destroy", "h2_last_error"]
 PHASES = ["upsweep", "coupling", "downsweep", "dense_expand"]
 COMPRESS_PHASES = ["orthogonalize", "project", "basis_generation", "truncate", "project_truncated"]
 COMPRESS_ARRAYS = {"U": 0, "V": 1, "E": 2, "F": 3, "S": 4, "T_ortho_U": 5, "T_ortho_V": 6, "R_U": 7, "R_V": 8,
@@ -90,9 +90,10 @@ def _load():
     lib.h2_compress_profile.argtypes = [vp, i32]
     lib.h2_compress_profile_read.argtypes = [vp, vp, vp]
     lib.h2_compress_destroy.argtypes = [vp]
+    lib.h2_compress_info.argtypes = [vp, vp]
     lib.h2_last_error.restype = ctypes.c_char_p
     for name in ("h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read",
-                 "h2_compress_profile", "h2_compress_profile_read", "h2_compress_destroy", "h2_create", "h2_create_kernel_coupling", "h2_create_generated", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
+                 "h2_compress_profile", "h2_compress_profile_read", "h2_compress_info", "h2_compress_destroy", "h2_create", "h2_create_kernel_coupling", "h2_create_generated", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
                  "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
                  "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy",
                  "h2_tune", "h2_batch_tune"):
@@ -414,6 +415,12 @@ class Compressor:
         n = np.zeros(1, dtype=np.int64)
         _check(_lib.h2_compress_profile_read(self._c, _ptr(ms), _ptr(n)))
         return dict(zip(COMPRESS_PHASES, ms.tolist())), int(n[0])
+
+    def info(self) -> dict:
+        a = np.zeros(6, dtype=np.int64)
+        _check(_lib.h2_compress_info(self._c, _ptr(a)))
+        keys = ["max_sweeps", "total_sweeps", "device_bytes", "nS", "q", "k"]
+        return {key: int(v) for key, v in zip(keys, a)}
 
     def close(self):
         if getattr(self, "_c", None) is not None and self._c.value:

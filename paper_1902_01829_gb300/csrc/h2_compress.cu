@@ -14,6 +14,7 @@
 // calls; Householder QR and one-sided Jacobi SVD are written here and run in
 // shared memory, one node per CTA. A leaf's W = U R^T with an orthonormal U is
 // reduced to the K x K matrix R^T before its SVD.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
@@ -47,18 +48,21 @@ struct h2_compressor_s {
   double *RU = nullptr, *RV = nullptr, *Ut = nullptr, *Vt = nullptr, *Et = nullptr, *Ft = nullptr;
   double *TUt = nullptr, *TVt = nullptr, *sigU = nullptr, *sigV = nullptr, *workY = nullptr, *workZ = nullptr;
   int* ranks = nullptr;         // [2 (q+1) + 1]: row tree ranks, column tree ranks, uniform rank
+  int* stats = nullptr;         // [2]: most and total Jacobi sweeps of the last run
   // results at the uniform rank
   double *oU = nullptr, *oV = nullptr, *oE = nullptr, *oF = nullptr, *oS = nullptr;
   int mode = -1;                // -1 nothing run, 0 orthogonalized, 1 compressed
   bool prof = false;
   cudaEvent_t ev[6] = {};
   int64_t launches = 0;
+  int64_t dev_bytes = 0;
 };
 
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kSvdThreads = 128;
+constexpr int kMaxSweeps = 40;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -97,7 +101,7 @@ __device__ void cta_householder(double* A, int lda, int rows, int cols, double* 
     __syncthreads();
     const double t = tau[j];
     if (t != 0.0) {
-      for (int c = j + 1 + warp; c < cols; c += kWarps) {
+      for (int c = j + 1 + warp; c < cols; c += (int)(blockDim.x >> 5)) {
         double w = 0.0;
         for (int i = j + 1 + lane; i < rows; i += 32) w = fma(A[i + j * lda], A[i + c * lda], w);
         w = t * (warp_sum(w) + A[j + c * lda]);
@@ -121,7 +125,7 @@ __device__ void cta_form_q(const double* A, int lda, int rows, int cols, const d
   for (int j = min(rows, cols) - 1; j >= 0; j--) {
     const double t = tau[j];
     if (t != 0.0) {
-      for (int c = j + warp; c < cols; c += kWarps) {
+      for (int c = j + warp; c < cols; c += (int)(blockDim.x >> 5)) {
         double w = 0.0;
         for (int i = j + 1 + lane; i < rows; i += 32) w = fma(A[i + j * lda], Q[i + c * ldq], w);
         w = t * (warp_sum(w) + Q[j + c * ldq]);
@@ -253,19 +257,41 @@ __global__ void __launch_bounds__(kThreads) k_project(const double* __restrict__
 // ---------------------------------------------------------------------------------------------
 // Basis generation (Sec. 5.3, Alg. 9): R_i = triangular factor of
 // [R_parent E_i^T; S_ij1^T; ...] (row tree, blocks of row i) or [R_parent F_j^T; S_i1j; ...]
-// (column tree, blocks of column j). One CTA per node of level l. The stack is reduced one
-// K x K block at a time: QR of [R; B] with R upper triangular touches row j of R and all of B
-// for column j.
+// (column tree, blocks of column j). One CTA per node of level l. The stack is reduced a few
+// blocks at a time (up to 128 rows): QR of [R; B] with R upper triangular, where the reflector
+// of column j touches row j of R and all of B. The warp that updates column j + 1 also forms
+// the next reflector, so each column costs one CTA barrier.
+__device__ void warp_stack_reflector(double* Rs, int K, double* B, int ldb, int rows, int j, double* tau, int lane) {
+  double s = 0.0;
+  for (int r = lane; r < rows; r += 32) s = fma(B[r + j * ldb], B[r + j * ldb], s);
+  s = warp_sum(s);
+  const double alpha = Rs[j + j * K];
+  double t = 0.0, beta = alpha, scale = 1.0;
+  if (s > 0.0) {
+    beta = -copysign(sqrt(fma(alpha, alpha, s)), alpha);
+    t = (beta - alpha) / beta;
+    scale = 1.0 / (alpha - beta);
+  }
+  for (int r = lane; r < rows; r += 32) B[r + j * ldb] *= scale;
+  __syncwarp();
+  if (lane == 0) {
+    Rs[j + j * K] = beta;
+    tau[j] = t;
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(kThreads) k_basis_gen(const double* __restrict__ E, const double* __restrict__ S,
                                                         double* __restrict__ R, const int32_t* __restrict__ ptr,
                                                         const int32_t* __restrict__ blk, int columns, int K,
                                                         int64_t first) {
   extern __shared__ double sm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int64_t i = first + blockIdx.x;
+  const int nb_max = max(1, 128 / K), ldb = nb_max * K;
   double* Rs = sm;            // K x K
-  double* B = Rs + K * K;     // K x K
-  double* tau = B + K * K;    // K
+  double* B = Rs + K * K;     // up to nb_max stacked K x K blocks (ld ldb)
+  double* tau = B + ldb * K;  // K
   double* sgn = tau + 64;
   // M = R_parent E_i^T, then its QR
   const double* Rp = R + ((i - 1) / 2) * K * K;
@@ -283,42 +309,33 @@ __global__ void __launch_bounds__(kThreads) k_basis_gen(const double* __restrict
     if (a > c) Rs[idx] = 0.0;
   }
   __syncthreads();
-  for (int32_t e = ptr[i]; e < ptr[i + 1]; e++) {
-    const int64_t b = blk ? blk[e] : e;
-    const double* Sb = S + b * K * K;
-    for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
-      const int a = idx % K, c = idx / K;
-      B[idx] = columns ? Sb[idx] : Sb[c + a * K];   // S_ij or S_ij^T
+  const int32_t e0 = ptr[i], e1 = ptr[i + 1];
+  for (int32_t e = e0; e < e1; e += nb_max) {
+    const int nb = min(nb_max, (int)(e1 - e)), rows = nb * K;
+    for (int idx = threadIdx.x; idx < rows * K; idx += blockDim.x) {
+      const int r = idx % rows, c = idx / rows;
+      const int q = r / K, a = r % K;
+      const int64_t b = blk ? blk[e + q] : e + q;
+      const double* Sb = S + b * K * K;
+      B[r + c * ldb] = columns ? Sb[a + c * K] : Sb[c + a * K];   // S_ij or S_ij^T
     }
     __syncthreads();
+    if (warp == 0) warp_stack_reflector(Rs, K, B, ldb, rows, 0, tau, lane);
+    __syncthreads();
     for (int j = 0; j < K; j++) {
-      if (warp == 0) {
-        double s = 0.0;
-        for (int r = lane; r < K; r += 32) s = fma(B[r + j * K], B[r + j * K], s);
-        s = warp_sum(s);
-        const double alpha = Rs[j + j * K];
-        double t = 0.0, beta = alpha, scale = 1.0;
-        if (s > 0.0) {
-          beta = -copysign(sqrt(fma(alpha, alpha, s)), alpha);
-          t = (beta - alpha) / beta;
-          scale = 1.0 / (alpha - beta);
-        }
-        for (int r = lane; r < K; r += 32) B[r + j * K] *= scale;
-        __syncwarp();
-        if (lane == 0) {
-          Rs[j + j * K] = beta;
-          tau[j] = t;
-        }
-      }
-      __syncthreads();
       const double t = tau[j];
-      if (t != 0.0) {
-        for (int c = j + 1 + warp; c < K; c += kWarps) {
+      for (int c = j + 1 + warp; c < K; c += nw) {
+        if (t != 0.0) {
           double w = 0.0;
-          for (int r = lane; r < K; r += 32) w = fma(B[r + j * K], B[r + c * K], w);
+          for (int r = lane; r < rows; r += 32) w = fma(B[r + j * ldb], B[r + c * ldb], w);
           w = t * (warp_sum(w) + Rs[j + c * K]);
+          __syncwarp();
           if (lane == 0) Rs[j + c * K] -= w;
-          for (int r = lane; r < K; r += 32) B[r + c * K] = fma(-w, B[r + j * K], B[r + c * K]);
+          for (int r = lane; r < rows; r += 32) B[r + c * ldb] = fma(-w, B[r + j * ldb], B[r + c * ldb]);
+        }
+        if (c == j + 1) {
+          __syncwarp();
+          warp_stack_reflector(Rs, K, B, ldb, rows, j + 1, tau, lane);
         }
       }
       __syncthreads();
@@ -335,51 +352,66 @@ __global__ void __launch_bounds__(kThreads) k_basis_gen(const double* __restrict
 // dimension ld): rotates pairs of columns, in the round-robin order that makes each step's
 // pairs disjoint, until every pair is orthogonal to working precision. Afterwards the column
 // norms are the singular values of X and the normalized columns its left singular vectors.
-__device__ void cta_jacobi(double* X, int ld, int rows, int cols, int* flag) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int P = cols + (cols & 1);
-  const double tol = DBL_EPSILON * (double)max(rows, 8);
-  for (int sweep = 0; sweep < 60; sweep++) {
-    if (threadIdx.x == 0) *flag = 0;
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so the FP64 work per pair is
+// kept to the dot products and the rotation itself: each pair belongs to a group of g lanes
+// that split its rows (no CTA-wide reductions), and only the group computes its rotation.
+// Returns the number of sweeps.
+__device__ int cta_jacobi(double* X, int ld, int rows, int cols, int* flag) {
+  const int P = cols + (cols & 1), npairs = P / 2;
+  int g = 1;
+  while (g < 8 && npairs * g * 2 <= (int)blockDim.x) g <<= 1;
+  const int tid = threadIdx.x, grp = tid / g, sub = tid % g, lane = tid & 31;
+  const unsigned gmask = (g == 32 ? 0xffffffffu : ((1u << g) - 1u)) << (lane & ~(g - 1));
+  const double tol = DBL_EPSILON * (double)max(rows, 8), tol2 = tol * tol;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < kMaxSweeps; sweep++) {
+    if (tid == 0) *flag = 0;
     __syncthreads();
     for (int s = 0; s < P - 1; s++) {
-      for (int pr = warp; pr < P / 2; pr += kWarps) {
-        int a, b;
-        if (pr == 0) {
+      int a = cols, b = cols;
+      if (grp < npairs) {
+        if (grp == 0) {
           a = s;
           b = P - 1;
         } else {
-          a = (s + pr) % (P - 1);
-          b = (s - pr + P - 1) % (P - 1);
+          a = (s + grp) % (P - 1);
+          b = (s - grp + P - 1) % (P - 1);
         }
-        if (a >= cols || b >= cols) continue;
+      }
+      if (a < cols && b < cols) {   // the same for every lane of the group
         double* xa = X + a * ld;
         double* xb = X + b * ld;
         double al = 0.0, be = 0.0, ga = 0.0;
-        for (int r = lane; r < rows; r += 32) {
-          al = fma(xa[r], xa[r], al);
-          be = fma(xb[r], xb[r], be);
-          ga = fma(xa[r], xb[r], ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga == 0.0 || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-        const double c = 1.0 / sqrt(fma(t, t, 1.0)), sn = c * t;
-        for (int r = lane; r < rows; r += 32) {
+        for (int r = sub; r < rows; r += g) {
           const double u = xa[r], v = xb[r];
-          xa[r] = c * u - sn * v;
-          xb[r] = sn * u + c * v;
+          al = fma(u, u, al);
+          be = fma(v, v, be);
+          ga = fma(u, v, ga);
         }
-        if (lane == 0) *flag = 1;
+        for (int o = 1; o < g; o <<= 1) {
+          al += __shfl_xor_sync(gmask, al, o);
+          be += __shfl_xor_sync(gmask, be, o);
+          ga += __shfl_xor_sync(gmask, ga, o);
+        }
+        if (ga * ga > tol2 * al * be) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+          const double c = rsqrt(fma(t, t, 1.0)), sn = c * t;
+          for (int r = sub; r < rows; r += g) {
+            const double u = xa[r], v = xb[r];
+            xa[r] = fma(c, u, -sn * v);
+            xb[r] = fma(sn, u, c * v);
+          }
+          if (sub == 0) *flag = 1;
+        }
       }
       __syncthreads();
     }
+    sweeps++;
     if (*flag == 0) break;
     __syncthreads();
   }
+  return sweeps;
 }
 
 // After cta_jacobi: singular values (descending) to sig[0..cols), the left singular vectors
@@ -389,7 +421,7 @@ __device__ void cta_jacobi(double* X, int ld, int rows, int cols, int* flag) {
 __device__ void cta_sorted_vectors(const double* X, int ld, int rows, int cols, int nsv, double eps, double* nrm,
                                    int* order, double* sig, double* Y, int ldy, int* rank) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c = warp; c < cols; c += kWarps) {
+  for (int c = warp; c < cols; c += (int)(blockDim.x >> 5)) {
     double s = 0.0;
     for (int r = lane; r < rows; r += 32) s = fma(X[r + c * ld], X[r + c * ld], s);
     s = warp_sum(s);
@@ -421,9 +453,9 @@ __device__ void cta_sorted_vectors(const double* X, int ld, int rows, int cols, 
 // Leaves: W_i = U_i R_i^T with U_i orthonormal (zero columns beyond the leaf size), so the SVD
 // of W_i is U_i times that of M = R_i^T with the rows beyond the leaf size cleared. The left
 // singular vectors of M go to Y (K x K per leaf).
-__global__ void __launch_bounds__(kThreads) k_svd_leaf(const double* __restrict__ R, const int64_t* __restrict__ leaf_off,
-                                                       double* __restrict__ sig, double* __restrict__ Y, int* rank,
-                                                       double eps, int K, int64_t leaf0) {
+__global__ void __launch_bounds__(kSvdThreads) k_svd_leaf(const double* __restrict__ R, const int64_t* __restrict__ leaf_off,
+                                                          double* __restrict__ sig, double* __restrict__ Y, int* rank,
+                                                          int* stats, double eps, int K, int64_t leaf0) {
   extern __shared__ double sm[];
   const int64_t i = blockIdx.x, h = leaf0 + i;
   const int m = (int)(leaf_off[i + 1] - leaf_off[i]);
@@ -437,51 +469,61 @@ __global__ void __launch_bounds__(kThreads) k_svd_leaf(const double* __restrict_
     X[idx] = a < m ? Rh[c + a * K] : 0.0;   // (R^T)[a][c] = R[c][a]
   }
   __syncthreads();
-  cta_jacobi(X, K, K, K, &flag);
+  const int sw = cta_jacobi(X, K, K, K, &flag);
+  if (threadIdx.x == 0) {
+    atomicMax(stats, sw);
+    atomicAdd(stats + 1, sw);
+  }
   cta_sorted_vectors(X, K, K, K, min(m, K), eps, nrm, order, sig + h * K, Y + i * K * K, K, rank);
 }
 
 // Inner node p (level l - 1): Z_p = [T_c1 E_c1; T_c2 E_c2] (2 r x K, r the children's new
-// rank, E the orthogonal transfers) and W_p = Z_p R_p^T; Z_p is kept for T_p.
-__global__ void __launch_bounds__(kThreads) k_svd_inner(const double* __restrict__ R, const double* __restrict__ E,
-                                                        const double* __restrict__ T, double* __restrict__ sig,
-                                                        double* __restrict__ Y, double* __restrict__ Zw,
-                                                        const int* __restrict__ rank_child, int* rank, double eps, int K,
-                                                        int64_t first) {
+// rank, E the orthogonal transfers) and W_p = Z_p R_p^T. Z_p goes to global memory (for T_p);
+// a warp forms one row of Z_p at a time and from it the same row of W_p, so only W_p needs
+// shared memory.
+__global__ void __launch_bounds__(kSvdThreads) k_svd_inner(const double* __restrict__ R, const double* __restrict__ E,
+                                                           const double* __restrict__ T, double* __restrict__ sig,
+                                                           double* __restrict__ Y, double* __restrict__ Zw,
+                                                           const int* __restrict__ rank_child, int* rank, int* stats,
+                                                           double eps, int K, int64_t first) {
   extern __shared__ double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int64_t p = first + blockIdx.x;
   const int r = *rank_child, rows = 2 * r;
-  double* Z = sm;                 // 2r x K (ld 2K)
-  double* X = Z + 2 * K * K;      // 2r x K (ld 2K)
-  double* nrm = X + 2 * K * K;
-  int* order = (int*)(nrm + 64);
-  __shared__ int flag;
   const int ld = 2 * K;
-  for (int idx = threadIdx.x; idx < rows * K; idx += blockDim.x) {
-    const int a2 = idx % rows, c = idx / rows;
+  double* X = sm;                  // 2r x K (ld 2K)
+  double* nrm = X + 2 * K * K;     // 64
+  double* zrow = nrm + 64;         // one row of Z per warp (K each)
+  int* order = (int*)(zrow + nw * 64);
+  __shared__ int flag;
+  const double* Rp = R + p * K * K;
+  double* Zp = Zw + blockIdx.x * 2 * K * K;
+  for (int a2 = warp; a2 < rows; a2 += nw) {
     const int half = a2 / r, a = a2 % r;
     const int64_t ch = 2 * p + 1 + half;
     const double* Tc = T + ch * K * K;
     const double* Ec = E + (ch - 1) * K * K;
-    double s = 0.0;
-    for (int t = 0; t < K; t++) s = fma(Tc[a + t * K], Ec[t + c * K], s);
-    Z[a2 + c * ld] = s;
-  }
-  __syncthreads();
-  const double* Rp = R + p * K * K;
-  for (int idx = threadIdx.x; idx < rows * K; idx += blockDim.x) {
-    const int a2 = idx % rows, c = idx / rows;
-    double s = 0.0;
-    for (int t = c; t < K; t++) s = fma(Z[a2 + t * ld], Rp[c + t * K], s);   // (R^T)[t][c] = R[c][t], R upper
-    X[a2 + c * ld] = s;
-  }
-  for (int idx = threadIdx.x; idx < rows * K; idx += blockDim.x) {
-    const int a2 = idx % rows, c = idx / rows;
-    Zw[blockIdx.x * 2 * K * K + a2 + c * ld] = Z[a2 + c * ld];
+    for (int c = lane; c < K; c += 32) {
+      double z = 0.0;
+      for (int t = 0; t < K; t++) z = fma(Tc[a + t * K], Ec[t + c * K], z);
+      zrow[warp * 64 + c] = z;
+      Zp[a2 + c * ld] = z;
+    }
+    __syncwarp();
+    for (int c = lane; c < K; c += 32) {
+      double x = 0.0;
+      for (int t = c; t < K; t++) x = fma(zrow[warp * 64 + t], Rp[c + t * K], x);   // (R^T)[t][c] = R[c][t], R upper
+      X[a2 + c * ld] = x;
+    }
+    __syncwarp();
   }
   __syncthreads();
   if (rows > 0) {
-    cta_jacobi(X, ld, rows, K, &flag);
+    const int sw = cta_jacobi(X, ld, rows, K, &flag);
+    if (threadIdx.x == 0) {
+      atomicMax(stats, sw);
+      atomicAdd(stats + 1, sw);
+    }
     cta_sorted_vectors(X, ld, rows, K, min(rows, K), eps, nrm, order, sig + p * K, Y + blockIdx.x * 2 * K * K, ld,
                        rank);
   } else {
@@ -596,6 +638,7 @@ h2_status calloc_dev(h2_compressor_s* c, T** p, int64_t count) {
                 (long long)(count * (int64_t)sizeof(T)), cudaGetErrorString(e));
   }
   c->allocs.push_back(v);
+  c->dev_bytes += count * (int64_t)sizeof(T);
   CUDA_TRY(cudaMemset(v, 0, (size_t)count * sizeof(T)));
   *p = (T*)v;
   return H2_OK;
@@ -622,9 +665,11 @@ void release(h2_compressor_s* c) {
 size_t smem_qr_leaf(int K) { return (size_t)(2 * 64 * K + 128) * sizeof(double); }
 size_t smem_qr_inner(int K) { return (size_t)(4 * K * K + 128) * sizeof(double); }
 size_t smem_project(int K) { return (size_t)(3 * K * K) * sizeof(double); }
-size_t smem_basis(int K) { return (size_t)(2 * K * K + 128) * sizeof(double); }
+size_t smem_basis(int K) { return (size_t)(K * K + std::max(1, 128 / K) * K * K + 128) * sizeof(double); }
 size_t smem_svd_leaf(int K) { return (size_t)(K * K + 64) * sizeof(double) + 64 * sizeof(int); }
-size_t smem_svd_inner(int K) { return (size_t)(4 * K * K + 64) * sizeof(double) + 64 * sizeof(int); }
+size_t smem_svd_inner(int K) {
+  return (size_t)(2 * K * K + 64 + (kSvdThreads / 32) * 64) * sizeof(double) + 64 * sizeof(int);
+}
 size_t smem_trunc_leaf(int K) { return (size_t)(2 * 64 * K) * sizeof(double); }
 
 h2_status set_smem() {
@@ -677,15 +722,15 @@ h2_status basis_tree(h2_compressor_s* c, const double* Eo, double* R, bool colum
 h2_status trunc_tree(h2_compressor_s* c, const double* Uo, const double* Eo, const double* R, double* Ut, double* Et,
                      double* T, double* sig, int* ranks, double eps, cudaStream_t st) {
   const int K = c->K, q = c->q;
-  k_svd_leaf<<<(unsigned)c->leaves, kThreads, smem_svd_leaf(K), st>>>(R, c->leaf_off, sig, c->workY, ranks + q, eps, K,
-                                                                      c->leaves - 1);
+  k_svd_leaf<<<(unsigned)c->leaves, kSvdThreads, smem_svd_leaf(K), st>>>(R, c->leaf_off, sig, c->workY, ranks + q,
+                                                                         c->stats, eps, K, c->leaves - 1);
   k_trunc_leaf<<<(unsigned)c->leaves, kThreads, smem_trunc_leaf(K), st>>>(Uo, c->workY, Ut, T, c->leaf_off, ranks + q,
                                                                           K, c->leaves - 1);
   c->launches += 2;
   for (int l = q; l >= 1; l--) {
     const int64_t first = ((int64_t)1 << (l - 1)) - 1, cnt = (int64_t)1 << (l - 1);
-    k_svd_inner<<<(unsigned)cnt, kThreads, smem_svd_inner(K), st>>>(R, Eo, T, sig, c->workY, c->workZ, ranks + l,
-                                                                    ranks + l - 1, eps, K, first);
+    k_svd_inner<<<(unsigned)cnt, kSvdThreads, smem_svd_inner(K), st>>>(R, Eo, T, sig, c->workY, c->workZ, ranks + l,
+                                                                       ranks + l - 1, c->stats, eps, K, first);
     k_trunc_inner<<<(unsigned)cnt, kThreads, 0, st>>>(c->workY, c->workZ, Et, T, ranks + l, ranks + l - 1, K, first);
     c->launches += 2;
   }
@@ -759,6 +804,7 @@ h2_status h2_compress_create(const h2_desc* d, h2_compressor* out) {
     if ((s = calloc_dev(c, &c->workY, std::max(c->leaves * KK, inner_max * 2 * KK))) != H2_OK) return s;
     if ((s = calloc_dev(c, &c->workZ, inner_max * 2 * KK)) != H2_OK) return s;
     if ((s = calloc_dev(c, &c->ranks, 2 * (c->q + 1) + 1)) != H2_OK) return s;
+    if ((s = calloc_dev(c, &c->stats, 2)) != H2_OK) return s;
     if ((s = calloc_dev(c, &c->oU, c->n * K)) != H2_OK) return s;
     if ((s = calloc_dev(c, &c->oE, (nodes - 1) * KK)) != H2_OK) return s;
     if ((s = calloc_dev(c, &c->oS, nS * KK)) != H2_OK) return s;
@@ -825,6 +871,7 @@ h2_status h2_compress_run(h2_compressor c, double eps, void* stream) {
   mark(c, 3, st);
   // Sec. 5.4, Alg. 10: truncated bases, one rank per level
   CUDA_TRY(cudaMemsetAsync(c->ranks, 0, (size_t)(2 * (q + 1) + 1) * sizeof(int), st));
+  CUDA_TRY(cudaMemsetAsync(c->stats, 0, 2 * sizeof(int), st));
   if ((s = trunc_tree(c, c->Uo, c->Eo, c->RU, c->Ut, c->Et, c->TUt, c->sigU, c->ranks, eps, st)) != H2_OK) return s;
   if (sym) {
     CUDA_TRY(cudaMemcpyAsync(c->ranks + q + 1, c->ranks, (size_t)(q + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st));
@@ -922,6 +969,20 @@ h2_status h2_compress_profile_read(h2_compressor c, double ms[H2C_NPHASES], int6
     ms[p] = t;
   }
   if (launches) *launches = c->launches;
+  return H2_OK;
+}
+
+h2_status h2_compress_info(h2_compressor c, int64_t info[6]) {
+  if (!c || !info) return fail(H2_ERR_INVALID, "NULL argument");
+  int st[2] = {0, 0};
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(st, c->stats, sizeof st, cudaMemcpyDeviceToHost));
+  info[0] = st[0];
+  info[1] = st[1];
+  info[2] = c->dev_bytes;
+  info[3] = c->nS;
+  info[4] = c->q;
+  info[5] = c->K;
   return H2_OK;
 }
 
