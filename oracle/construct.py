@@ -116,3 +116,102 @@ def coupling_blocks(S_rowptr, S_colidx, cheb, kind, ell) -> np.ndarray:
         for b in range(S_rowptr[r], S_rowptr[r + 1]):
             S[b * k * k:(b + 1) * k * k] = kernel(kind, ell, cheb_points(cheb[r]), cheb_points(cheb[S_colidx[b]])).ravel(order="F")
     return S
+
+
+# ----------------------------------------------------------------------------- structure (Sec. 4.6)
+# The cluster tree, the boxes and the block structure, from their definitions:
+#   * KD bisection: q is the smallest level with m 2^q >= n; level by level, a node's points
+#     are ordered by (coordinate along the longest side of its tight box, the lowest dimension
+#     on a tie; original index) and the first ceil(s / 2) go to the left child.
+#   * tight axis-aligned boxes; Chebyshev nodes of the first kind on each side, a side shorter
+#     than 1e-10 widened to 1e-10 about its centre.
+#   * dual traversal from (root, root): a pair is a coupling block when eta > 0, the boxes'
+#     distance is > 0 and max(diam_i, diam_j) <= eta dist (diam the box diagonal, dist the
+#     Euclidean gap); otherwise a dense block at the leaf level, else the four child pairs.
+#   * blocks in block-sparse rows, each row's columns ascending.
+
+# A plausible mistake planted on purpose (tests only; None in every other use):
+# "floor_split" the left child gets floor(s / 2) points; "shortest_side" splits along the
+# shortest box side; "diam_sum" compares diam_i + diam_j instead of the larger one.
+MUTATION: str | None = None
+
+
+def cluster_tree(points: np.ndarray, m: int):
+    """(perm, leaf_offset, q): perm[a] = original index of cluster position a."""
+    n, dim = points.shape
+    q = 0
+    while (m << q) < n:
+        q += 1
+    perm = np.arange(n)
+    ranges = [(0, n)]
+    for _ in range(q):
+        nxt = []
+        for lo, hi in ranges:
+            P = points[perm[lo:hi]]
+            w = P.max(axis=0) - P.min(axis=0)
+            ds = int(np.argmin(w) if MUTATION == "shortest_side" else np.argmax(w))  # lowest dimension on a tie
+            order = np.lexsort((perm[lo:hi], P[:, ds]))
+            perm[lo:hi] = perm[lo:hi][order]
+            mid = lo + ((hi - lo) // 2 if MUTATION == "floor_split" else (hi - lo + 1) // 2)
+            nxt += [(lo, mid), (mid, hi)]
+        ranges = nxt
+    leaf_offset = np.array([lo for lo, _ in ranges] + [n], dtype=np.int64)
+    return perm, leaf_offset, q
+
+
+def node_boxes(points_cluster: np.ndarray, leaf_offset: np.ndarray, q: int):
+    """Tight boxes (bmin, bmax), (n_nodes, dim) each, of every heap node."""
+    n_nodes = (2 << q) - 1
+    dim = points_cluster.shape[1]
+    bmin, bmax = np.empty((n_nodes, dim)), np.empty((n_nodes, dim))
+    for h in range(n_nodes):
+        l = int(np.floor(np.log2(h + 1)))
+        span = 1 << (q - l)
+        t = h - ((1 << l) - 1)
+        lo, hi = int(leaf_offset[t * span]), int(leaf_offset[(t + 1) * span])
+        bmin[h] = points_cluster[lo:hi].min(axis=0)
+        bmax[h] = points_cluster[lo:hi].max(axis=0)
+    return bmin, bmax
+
+
+def chebyshev_nodes(bmin: np.ndarray, bmax: np.ndarray, p: int) -> np.ndarray:
+    """(n_nodes, dim, p) first-kind Chebyshev nodes on each box side."""
+    a, b = bmin.copy(), bmax.copy()
+    thin = (b - a) < 1e-10
+    c = 0.5 * (a + b)
+    a[thin], b[thin] = c[thin] - 0.5e-10, c[thin] + 0.5e-10
+    v = np.arange(p)
+    return 0.5 * (a + b)[:, :, None] + 0.5 * (b - a)[:, :, None] * np.cos((2.0 * v + 1.0) * np.pi / (2.0 * p))
+
+
+def dual_traversal(bmin: np.ndarray, bmax: np.ndarray, q: int, eta: float):
+    """(S_rowptr, S_colidx, D_rowptr, D_colidx): coupling blocks over all heap nodes, dense
+    blocks over the leaves, in block-sparse rows with ascending columns."""
+    diam = np.sqrt(((bmax - bmin) ** 2).sum(axis=1))
+    S, D = [], []
+    stack = [(0, 0, 0)]
+    while stack:
+        i, j, l = stack.pop()
+        gap = np.maximum(0.0, np.maximum(bmin[j] - bmax[i], bmin[i] - bmax[j]))
+        dist = float(np.sqrt((gap ** 2).sum()))
+        dm = diam[i] + diam[j] if MUTATION == "diam_sum" else max(diam[i], diam[j])
+        if eta > 0 and dist > 0 and dm <= eta * dist:
+            S.append((i, j))
+        elif l == q:
+            first = (1 << q) - 1
+            D.append((i - first, j - first))
+        else:
+            for a in (1, 2):
+                for b in (1, 2):
+                    stack.append((2 * i + a, 2 * j + b, l + 1))
+
+    def bsr(pairs, rows):
+        pairs = sorted(pairs)
+        ptr = np.zeros(rows + 1, dtype=np.int32)
+        for r, _ in pairs:
+            ptr[r + 1] += 1
+        return np.cumsum(ptr).astype(np.int32), np.array([c for _, c in pairs], dtype=np.int32)
+
+    S_rowptr, S_colidx = bsr(S, (2 << q) - 1)
+    D_rowptr, D_colidx = bsr(D, 1 << q)
+    return S_rowptr, S_colidx, D_rowptr, D_colidx
