@@ -202,13 +202,14 @@ def fp64_peak_flops(dev) -> float:
 
 def compress_kernel_flops(A, K: int) -> dict:
     """FP64 flops each compression kernel computes, counted from what it does per unit:
-    k_project: two K x K x K products per coupling block (4 K^3);
+    k_project (the orthogonalization's, with upper triangular T): two K x K x K products with one
+    triangular factor per coupling block (2 K^2 (K + 1));
     k_basis_gen: per coupling block the Householder reduction of K stacked rows against the
     triangular factor (per column j, a dot product and an update of K rows for the K - j - 1
     later columns: 4 K sum_j (K - j - 1) = 2 K^2 (K - 1)), per node R_parent E^T (K^2 (K + 1))
     and the QR of that K x K product (4 K^3 / 3)."""
     nodes = (2 << A.q) - 1
-    return {"k_project": 4 * K ** 3 * A.nS,
+    return {"k_project": 2 * K * K * (K + 1) * A.nS,
             "k_basis_gen": 2 * K * K * (K - 1) * A.nS + (nodes - 1) * (K * K * (K + 1) + 4 * K ** 3 // 3)}
 
 

@@ -213,16 +213,21 @@ __global__ void __launch_bounds__(kThreads) k_ortho_inner(const double* __restri
 // ---------------------------------------------------------------------------------------------
 // Projection (Alg. 7): S_out = T^U_i S T^V_j^T. T^U_i has ru rows, T^V_j rv rows (the ranks of
 // the block's level in the two trees, or K); S_out is ru x rv with leading dimension ldo, at
-// block * ldo * ldo (zero-padded to ldo x ldo). One CTA per block, grid-stride.
+// block * ldo * ldo (zero-padded to ldo x ldo). tri: both T are upper triangular (the
+// orthogonalization's), so each product skips the zero half. One CTA per block, grid-stride.
+// X = S T_j^T is kept row-major and the result tile goes through shared memory, so every
+// shared-memory access is a broadcast or unit-stride and the global store is coalesced.
 __global__ void __launch_bounds__(kThreads) k_project(const double* __restrict__ S, double* __restrict__ Sout,
                                                       const double* __restrict__ TU, const double* __restrict__ TV,
                                                       const int32_t* __restrict__ s_row, const int32_t* __restrict__ s_col,
                                                       int64_t nS, int K, const int* __restrict__ ranks_u,
-                                                      const int* __restrict__ ranks_v, const int* __restrict__ ld_out) {
+                                                      const int* __restrict__ ranks_v, const int* __restrict__ ld_out,
+                                                      int tri) {
   extern __shared__ double sm[];
-  double* Sb = sm;          // K x K, then T^U_i
-  double* Tj = Sb + K * K;  // K x K
-  double* X = Tj + K * K;   // K x rv: S T_j^T
+  const int K1 = K + 1;
+  double* Sb = sm;           // K x K (column-major), then T^U_i
+  double* Tj = Sb + K * K;   // K x K (column-major), then the result tile (ld K + 1)
+  double* Xt = Tj + K * K1;  // X = S T_j^T, row-major: X[a][c] at c + a (K + 1)
   const int ldo = ld_out ? *ld_out : K;
   for (int64_t b = blockIdx.x; b < nS; b += gridDim.x) {
     const int64_t i = s_row[b], j = s_col[b];
@@ -236,19 +241,24 @@ __global__ void __launch_bounds__(kThreads) k_project(const double* __restrict__
     for (int idx = threadIdx.x; idx < K * rv; idx += blockDim.x) {
       const int a = idx % K, c = idx / K;
       double s = 0.0;
-      for (int t = 0; t < K; t++) s = fma(Sb[a + t * K], Tj[c + t * K], s);
-      X[a + c * K] = s;
+      for (int t = tri ? c : 0; t < K; t++) s = fma(Sb[a + t * K], Tj[c + t * K], s);
+      Xt[c + a * K1] = s;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) Sb[idx] = TU[i * K * K + idx];
     __syncthreads();
+    if (rv > 0)
+      for (int idx = threadIdx.x; idx < ru * rv; idx += blockDim.x) {
+        const int c = idx % rv, a = idx / rv;
+        double s = 0.0;
+        for (int t = tri ? a : 0; t < K; t++) s = fma(Sb[a + t * K], Xt[c + t * K1], s);
+        Tj[a + c * K1] = s;
+      }
+    __syncthreads();
     double* out = Sout + b * ldo * ldo;
     for (int idx = threadIdx.x; idx < ldo * ldo; idx += blockDim.x) {
       const int a = idx % ldo, c = idx / ldo;
-      double s = 0.0;
-      if (a < ru && c < rv)
-        for (int t = 0; t < K; t++) s = fma(Sb[a + t * K], X[t + c * K], s);
-      out[idx] = s;
+      out[idx] = (a < ru && c < rv) ? Tj[a + c * K1] : 0.0;
     }
     __syncthreads();
   }
@@ -664,7 +674,7 @@ void release(h2_compressor_s* c) {
 
 size_t smem_qr_leaf(int K) { return (size_t)(2 * 64 * K + 128) * sizeof(double); }
 size_t smem_qr_inner(int K) { return (size_t)(4 * K * K + 128) * sizeof(double); }
-size_t smem_project(int K) { return (size_t)(3 * K * K) * sizeof(double); }
+size_t smem_project(int K) { return (size_t)(K * K + 2 * K * (K + 1)) * sizeof(double); }
 size_t smem_basis(int K) { return (size_t)(K * K + std::max(1, 128 / K) * K * K + 128) * sizeof(double); }
 size_t smem_svd_leaf(int K) { return (size_t)(K * K + 64) * sizeof(double) + 64 * sizeof(int); }
 size_t smem_svd_inner(int K) {
@@ -854,7 +864,7 @@ h2_status h2_compress_run(h2_compressor c, double eps, void* stream) {
   mark(c, 1, st);
   // Alg. 7: coupling blocks in the orthogonal bases
   k_project<<<proj_grid(c->nS), kThreads, smem_project(K), st>>>(c->S0, c->S1, c->TUo, sym ? c->TUo : c->TVo, c->s_row,
-                                                                  c->s_col, c->nS, K, nullptr, nullptr, nullptr);
+                                                                  c->s_col, c->nS, K, nullptr, nullptr, nullptr, 1);
   c->launches++;
   CUDA_TRY(cudaGetLastError());
   mark(c, 2, st);
@@ -884,7 +894,7 @@ h2_status h2_compress_run(h2_compressor c, double eps, void* stream) {
   // second projection, written at the uniform rank; bases and transfers repacked to it
   const int* kt = c->ranks + 2 * (q + 1);
   k_project<<<proj_grid(c->nS), kThreads, smem_project(K), st>>>(c->S1, c->oS, c->TUt, sym ? c->TUt : c->TVt, c->s_row,
-                                                                  c->s_col, c->nS, K, c->ranks, c->ranks + q + 1, kt);
+                                                                  c->s_col, c->nS, K, c->ranks, c->ranks + q + 1, kt, 0);
   k_pack_bases<<<1024, 128, 0, st>>>(c->Ut, c->oU, c->leaf_off, c->leaves, K, kt);
   k_pack_transfers<<<1024, 128, 0, st>>>(c->Et, c->oE, c->n_nodes - 1, K, kt);
   c->launches += 3;
