@@ -45,6 +45,8 @@ WORKLOADS = {
     "compress_2d": "algebraic compression (Sec. 5: orthogonalization, basis generation, truncation, projection) of the "
                    "2D exp(-r/0.1) covariance H^2 matrix, n=2^20 uniform points, m=64, k=64 (8x8 Chebyshev), eta=0.9, "
                    "FP64, relative threshold 1e-7",
+    "compress_2d_small": "algebraic compression (Sec. 5) of the 2D exp(-r/0.1) covariance H^2 matrix, n=2^16 uniform "
+                         "points, m=64, k=64 (8x8 Chebyshev), eta=0.9, FP64, relative threshold 1e-7",
     "compress_3d": "algebraic compression (Sec. 5) of the 3D exp(-r/0.2) covariance H^2 matrix, n=2^18 uniform points "
                    "in the unit cube, m=64, k=64 (4x4x4 Chebyshev), eta=0.9, FP64, relative threshold 1e-3",
     "batch256": "256 independent 2D exp(-r/0.1) covariance H^2 matvecs, n log-uniform in [2^12, 2^17], m=32, k=16, "
@@ -145,8 +147,8 @@ class ClockSampler:
 # DRAM bytes (read + write) of one dense-stream launch over its algorithmic bytes, from full ncu captures
 # of the 2D n=2^18 workload (FP64, and int16 codes with FP32 bases); the traffic grows with the leaf
 # count, so the ratio carries over to the n=2^20 launch
-TRAFFIC_RATIO = {("fp64", False): 3184277648 / 3178496000, ("int16", True): 809942016 / 805640544}
-TRAFFIC_KERNEL = {("fp64", False): "k_dense_stream", ("int16", True): "k_dense_stream_m"}  # the kernel those counters belong to
+TRAFFIC_RATIO = {("fp64", False): 3184266039 / 3178496000}
+TRAFFIC_KERNEL = {("fp64", False): "k_dense_stream"}  # the kernel those counters belong to
 
 # FP32 instructions per double-float product a * x (split entry times split vector entry): the exact
 # product p, e (2), the two cross terms (2), TwoSum of the running sum (6), the small-part sum (2)
