@@ -500,6 +500,93 @@ h2_status h2_compress_info(h2_compressor c, int64_t info[6]);
 /* Free the compressor's device arrays. NULL is a no-op. */
 h2_status h2_compress_destroy(h2_compressor c);
 
+/*
+ * Construction of a covariance H^2 matrix on the current device (Sec. 4.6):
+ *   cluster tree  KD bisection: q is the smallest level with m 2^q >= n; level
+ *                 by level a node's points are ordered by (coordinate along
+ *                 the longest side of its tight box, the lowest dimension on a
+ *                 tie; original index) and the first ceil(s/2) form the left
+ *                 child. A leaf keeps the order of its parent's split.
+ *   boxes, nodes  tight axis-aligned boxes; p first-kind Chebyshev nodes per
+ *                 box side, (a+b)/2 + (b-a)/2 cos((2v+1) pi / (2p)), a side
+ *                 shorter than 1e-10 widened to 1e-10 about its centre
+ *   blocks        dual traversal from (root, root): a pair is a coupling
+ *                 block when eta > 0, the boxes' Euclidean gap dist > 0 and
+ *                 max(diam_i, diam_j) <= eta dist (diam = box diagonal);
+ *                 else a dense block at the leaf level, else its four child
+ *                 pairs. Block-sparse rows with ascending columns.
+ *   values        (optional, FP64) U_i[a][nu] = L^i_nu(x_a) (tensor Lagrange
+ *                 polynomials, dimension 0 slowest), E_c[mu][nu] =
+ *                 L^parent_nu(xi^c_mu), S_ij[nu][mu] = K(xi_i^nu, xi_j^mu),
+ *                 D_ij[a][b] = K(x_a, x_b), laid out as in h2_desc.
+ * The structure is exact: boxes, diameters, distances and Chebyshev nodes use
+ * the same rounded operations in the same order as the definitions above.
+ * Kernel values (exp) may differ from a host evaluation in the last bit.
+ */
+typedef struct h2_built_s* h2_built;
+enum { H2B_VALUES_U = 1, H2B_VALUES_E = 2, H2B_VALUES_S = 4, H2B_VALUES_D = 8 };
+typedef struct {
+  int64_t n;        /* points, 1 .. 2^31 - 1 */
+  int32_t dim;      /* 1 .. 3 */
+  int32_t m;        /* leaf size bound, 2 .. 64 */
+  int32_t p;        /* Chebyshev nodes per dimension; rank k = p^dim <= 64 */
+  int32_t kernel;   /* h2_kernel_kind */
+  double eta;       /* admissibility parameter, >= 0 (0: dense blocks only) */
+  double ell;       /* correlation length, > 0 */
+  int32_t values;   /* mask of H2B_VALUES_*: which value arrays to build */
+  int32_t reserved; /* 0 */
+} h2_build_desc;
+
+/*
+ * Build from `points` (host FP64, n * dim, original order, point i at
+ * points + i * dim). Synchronous; the device arrays live until
+ * h2_built_destroy. Errors: H2_ERR_INVALID (NULL arguments, sizes or
+ * parameters out of range, non-finite points), H2_ERR_UNSUPPORTED (p^dim > 64,
+ * 2^31 or more blocks), H2_ERR_OOM, H2_ERR_CUDA.
+ */
+h2_status h2_build(const h2_build_desc* b, const double* points, h2_built* out);
+
+/* info[0] q, [1] k, [2] coupling blocks, [3] dense blocks, [4] dense values,
+ * [5] nodes, [6] leaves, [7] device bytes held */
+h2_status h2_built_info(h2_built b, int64_t info[8]);
+
+/* milliseconds of the build's device phases: [0] cluster tree, boxes and
+ * Chebyshev nodes, [1] dual traversal and block-sparse rows, [2] values */
+h2_status h2_built_times(h2_built b, double ms[3]);
+
+/*
+ * Copy one array to host memory (count must be its exact size):
+ *   H2B_PERM        int64 [n]: original index of each cluster position
+ *   H2B_LEAF_OFFSET int64 [2^q + 1]
+ *   H2B_POINTS      double [n * dim]: the points in cluster order
+ *   H2B_CHEB        double [nodes * dim * p]: node h, dimension d at (h dim + d) p
+ *   H2B_S_ROWPTR, H2B_S_COLIDX, H2B_D_ROWPTR, H2B_D_COLIDX   int32, as h2_desc
+ *   H2B_D_VALOFF    int64 [dense blocks + 1]: offset of each dense block's values
+ *   H2B_U, H2B_E, H2B_S, H2B_D   double, as h2_desc (only those built)
+ */
+enum {
+  H2B_PERM = 0, H2B_LEAF_OFFSET = 1, H2B_POINTS = 2, H2B_CHEB = 3, H2B_S_ROWPTR = 4, H2B_S_COLIDX = 5,
+  H2B_D_ROWPTR = 6, H2B_D_COLIDX = 7, H2B_D_VALOFF = 8, H2B_U = 9, H2B_E = 10, H2B_S = 11, H2B_D = 12
+};
+h2_status h2_built_read(h2_built b, int32_t what, void* dst, int64_t count);
+
+/*
+ * A product handle (as h2_create) from a built matrix: storage and bases_fp32
+ * as in h2_desc; flags: H2B_CREATE_KERNEL_COUPLING evaluates the coupling
+ * blocks from the kernel in every product (h2_create_kernel_coupling),
+ * adding H2B_CREATE_GENERATED_DENSE generates the dense blocks on the device
+ * (h2_create_generated). Needs the U and E values, and S and D where they are
+ * stored. The structure and the needed values pass through host memory once.
+ * Errors: those of the create call; H2_ERR_INVALID for missing values or
+ * flags outside the two above (generated dense blocks without kernel
+ * coupling included).
+ */
+enum { H2B_CREATE_KERNEL_COUPLING = 1, H2B_CREATE_GENERATED_DENSE = 2 };
+h2_status h2_create_built(h2_built b, int32_t storage, int32_t bases_fp32, int32_t flags, h2_handle* out);
+
+/* Free the built matrix's device arrays. NULL is a no-op. */
+h2_status h2_built_destroy(h2_built b);
+
 /* Message of the calling thread's last failed call ("" if none). Valid until the next call. */
 const char* h2_last_error(void);
 

@@ -25,7 +25,8 @@ EXPORTS = ["h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_hos
            "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_create_generated", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
            "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_tune", "h2_batch_destroy",
            "h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read", "h2_compress_profile",
-           "h2_compress_profile_read", "h2_compress_info", "h2_compress_destroy", "h2_last_error"]
+           "h2_compress_profile_read", "h2_compress_info", "h2_compress_destroy", "h2_build", "h2_built_info",
+           "h2_built_times", "h2_built_read", "h2_create_built", "h2_built_destroy", "h2_last_error"]
 PHASES = ["upsweep", "coupling", "downsweep", "dense_expand"]
 COMPRESS_PHASES = ["orthogonalize", "project", "basis_generation", "truncate", "project_truncated"]
 COMPRESS_ARRAYS = {"U": 0, "V": 1, "E": 2, "F": 3, "S": 4, "T_ortho_U": 5, "T_ortho_V": 6, "R_U": 7, "R_V": 8,
@@ -46,6 +47,12 @@ class h2_desc(ctypes.Structure):
                 ("S_rowptr", ctypes.c_void_p), ("S_colidx", ctypes.c_void_p), ("S_val", ctypes.c_void_p),
                 ("D_rowptr", ctypes.c_void_p), ("D_colidx", ctypes.c_void_p), ("D_val", ctypes.c_void_p),
                 ("check_cover", ctypes.c_int32), ("bases_fp32", ctypes.c_int32)]
+
+
+class h2_build_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("dim", ctypes.c_int32), ("m", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("eta", ctypes.c_double), ("ell", ctypes.c_double),
+                ("values", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class h2_coupling_kernel(ctypes.Structure):
@@ -91,8 +98,14 @@ def _load():
     lib.h2_compress_profile_read.argtypes = [vp, vp, vp]
     lib.h2_compress_destroy.argtypes = [vp]
     lib.h2_compress_info.argtypes = [vp, vp]
+    lib.h2_build.argtypes = [ctypes.POINTER(h2_build_desc), vp, ctypes.POINTER(vp)]
+    lib.h2_built_info.argtypes = [vp, vp]
+    lib.h2_built_times.argtypes = [vp, vp]
+    lib.h2_built_read.argtypes = [vp, i32, vp, i64]
+    lib.h2_built_destroy.argtypes = [vp]
+    lib.h2_create_built.argtypes = [vp, i32, i32, i32, ctypes.POINTER(vp)]
     lib.h2_last_error.restype = ctypes.c_char_p
-    for name in ("h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read",
+    for name in ("h2_create_built", "h2_build", "h2_built_info", "h2_built_times", "h2_built_read", "h2_built_destroy", "h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read",
                  "h2_compress_profile", "h2_compress_profile_read", "h2_compress_info", "h2_compress_destroy", "h2_create", "h2_create_kernel_coupling", "h2_create_generated", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
                  "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
                  "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy",
@@ -426,6 +439,67 @@ class Compressor:
         if getattr(self, "_c", None) is not None and self._c.value:
             _lib.h2_compress_destroy(self._c)
             self._c = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+BUILT_ARRAYS = {"perm": (0, np.int64), "leaf_offset": (1, np.int64), "points": (2, np.float64), "cheb": (3, np.float64),
+                "S_rowptr": (4, np.int32), "S_colidx": (5, np.int32), "D_rowptr": (6, np.int32),
+                "D_colidx": (7, np.int32), "D_valoff": (8, np.int64), "U": (9, np.float64), "E": (10, np.float64),
+                "S_val": (11, np.float64), "D_val": (12, np.float64)}
+BUILD_VALUES = {"U": 1, "E": 2, "S": 4, "D": 8}
+
+
+class Built:
+    """A covariance H^2 matrix constructed on the current CUDA device (h2_build): cluster tree, boxes,
+    Chebyshev nodes, block structure and, as asked, FP64 values (U, E, S, D)."""
+
+    def __init__(self, points, *, m, p, eta, kernel="exp", ell=0.1, values=("U", "E", "S", "D")):
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        n, dim = pts.shape
+        d = h2_build_desc(n=n, dim=dim, m=int(m), p=int(p), kernel=KERNELS[kernel], eta=float(eta), ell=float(ell),
+                          values=sum(BUILD_VALUES[v] for v in values), reserved=0)
+        self._b = ctypes.c_void_p()
+        _check(_lib.h2_build(ctypes.byref(d), _ptr(pts), ctypes.byref(self._b)))
+        self.n, self.dim, self.p = n, dim, int(p)
+        a = np.zeros(8, dtype=np.int64)
+        _check(_lib.h2_built_info(self._b, _ptr(a)))
+        self.q, self.k, self.nS, self.nD, self.nDval, self.n_nodes, self.leaves, self.device_bytes = (int(v) for v in a)
+
+    def times(self) -> dict:
+        ms = np.zeros(3, dtype=np.float64)
+        _check(_lib.h2_built_times(self._b, _ptr(ms)))
+        return {"tree_ms": float(ms[0]), "blocks_ms": float(ms[1]), "values_ms": float(ms[2])}
+
+    def read(self, what: str) -> np.ndarray:
+        code, dt = BUILT_ARRAYS[what]
+        kk = self.k * self.k
+        size = {"perm": self.n, "leaf_offset": self.leaves + 1, "points": self.n * self.dim,
+                "cheb": self.n_nodes * self.dim * self.p, "S_rowptr": self.n_nodes + 1, "S_colidx": self.nS,
+                "D_rowptr": self.leaves + 1, "D_colidx": self.nD, "D_valoff": self.nD + 1, "U": self.n * self.k,
+                "E": (self.n_nodes - 1) * kk, "S_val": self.nS * kk, "D_val": self.nDval}[what]
+        out = np.empty(size, dtype=dt)
+        _check(_lib.h2_built_read(self._b, code, _ptr(out), size))
+        return out
+
+    def matrix(self, storage="fp64", bases_fp32=False, coupling="stored", dense="stored") -> "H2Matrix":
+        """A product handle of this matrix (h2_create_built); coupling="kernel" evaluates the coupling
+        blocks in every product, dense="generated" (with it) generates the dense blocks on the device."""
+        flags = (1 if coupling == "kernel" else 0) | (2 if dense == "generated" else 0)
+        M = H2Matrix.__new__(H2Matrix)
+        M._h = ctypes.c_void_p()
+        _check(_lib.h2_create_built(self._b, STORAGE[storage], 1 if bases_fp32 else 0, flags, ctypes.byref(M._h)))
+        M.n = self.n
+        return M
+
+    def close(self):
+        if getattr(self, "_b", None) is not None and self._b.value:
+            _lib.h2_built_destroy(self._b)
+            self._b = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libh2gb300.so")
-SOURCES = ["h2_api.cu", "h2_static.cu", "h2_compress.cu", "h2_mixed.cu", "h2_mixed_fp16.cu", "h2_mixed_bf16.cu", "h2_mixed_int16.cu"]
+SOURCES = ["h2_api.cu", "h2_static.cu", "h2_compress.cu", "h2_build.cu", "h2_mixed.cu", "h2_mixed_fp16.cu", "h2_mixed_bf16.cu", "h2_mixed_int16.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

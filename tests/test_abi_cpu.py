@@ -237,3 +237,31 @@ def test_compressor_rejects_bad_input(h2, small):
     assert lib.h2_compress_read(None, 0, None, 0, None) == h2.H2_ERR_INVALID
     assert lib.h2_compress_profile_read(None, None, None) == h2.H2_ERR_INVALID
     assert lib.h2_compress_destroy(None) == h2.H2_OK
+
+
+def test_builder_rejects_bad_input(h2):
+    """h2_build checks its description and points before touching the device."""
+    pts = np.random.default_rng(1).random((100, 2))
+
+    def expect(status, points=pts, **kw):
+        args = dict(m=16, p=4, eta=0.9, kernel="exp", ell=0.1)
+        args.update(kw)
+        with pytest.raises(h2.H2Error) as ei:
+            h2.Built(points, **args)
+        assert ei.value.status == status, str(ei.value)
+        return str(ei.value)
+
+    assert "m = 1" in expect(h2.H2_ERR_INVALID, m=1)
+    assert "p = 0" in expect(h2.H2_ERR_INVALID, p=0)
+    assert "rank" in expect(h2.H2_ERR_UNSUPPORTED, p=9)
+    assert "ell" in expect(h2.H2_ERR_INVALID, ell=0.0)
+    assert "eta" in expect(h2.H2_ERR_INVALID, eta=float("nan"))
+    bad = pts.copy()
+    bad[3, 1] = np.inf
+    assert "points[7]" in expect(h2.H2_ERR_INVALID, points=bad)
+    assert "dim" in expect(h2.H2_ERR_INVALID, points=np.zeros((10, 4)))
+    lib = h2._lib
+    out = ctypes.c_void_p()
+    assert lib.h2_build(None, None, ctypes.byref(out)) == h2.H2_ERR_INVALID
+    assert lib.h2_built_read(None, 0, None, 0) == h2.H2_ERR_INVALID
+    assert lib.h2_built_destroy(None) == h2.H2_OK
