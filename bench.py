@@ -147,8 +147,8 @@ class ClockSampler:
 # DRAM bytes (read + write) of one dense-stream launch over its algorithmic bytes, from full ncu captures
 # of the 2D n=2^18 workload (FP64, and int16 codes with FP32 bases); the traffic grows with the leaf
 # count, so the ratio carries over to the n=2^20 launch
-TRAFFIC_RATIO = {("fp64", False): 3184266039 / 3178496000}
-TRAFFIC_KERNEL = {("fp64", False): "k_dense_stream"}  # the kernel those counters belong to
+TRAFFIC_RATIO = {("fp64", False): 3184266039 / 3178496000, ("int16", True): 794616064 / 788584800}
+TRAFFIC_KERNEL = {("fp64", False): "k_dense_stream", ("int16", True): "k_dense_stream_m"}  # the kernel those counters belong to
 
 # FP32 instructions per double-float product a * x (split entry times split vector entry): the exact
 # product p, e (2), the two cross terms (2), TwoSum of the running sum (6), the small-part sum (2)
@@ -376,6 +376,38 @@ def compress_main(h2, args, dev, world, rank):
         out["cpu_baseline"] = c["cpu_baseline"]
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def construction_line(h2, A, values=("U", "E", "S", "D")) -> dict:
+    """Build the workload's matrix on the GPU (h2_build: KD tree, boxes, Chebyshev nodes, dual traversal,
+    FP64 values) from the generator's points and compare its structure with the host generator's."""
+    import oracle
+    from oracle import construct
+
+    pts = h2gen.uniform(A.seed, (A.n, A.dim))
+    t0 = time.perf_counter()
+    B = h2.Built(pts, m=A.m, p=A.p, eta=A.eta, kernel=A.kernel, ell=A.ell, values=values)
+    wall = time.perf_counter() - t0
+    t = B.times()
+    same = (np.array_equal(B.read("perm"), A.perm) and np.array_equal(B.read("S_colidx"), A.S_colidx)
+            and np.array_equal(B.read("S_rowptr"), A.S_rowptr) and np.array_equal(B.read("D_colidx"), A.D_colidx)
+            and np.array_equal(B.read("D_rowptr"), A.D_rowptr))
+    out = {"n": A.n, "dim": A.dim, "nS": B.nS, "nD": B.nD, "values": list(values),
+           "gpu_ms": {k: round(v, 3) for k, v in t.items()}, "gpu_total_ms": round(sum(t.values()), 3),
+           "call_s": round(wall, 3), "device_bytes": B.device_bytes, "structure_equals_generator": bool(same)}
+    B.close()
+    # the construction oracle (plain numpy, one thread of loops) on a bounded sample of the family
+    nb = 1 << 12
+    pts_s = h2gen.uniform(A.seed, (nb, A.dim))
+    t1 = time.perf_counter()
+    perm, lo, q = construct.cluster_tree(pts_s, A.m)
+    bmin, bmax = construct.node_boxes(pts_s[perm], lo, q)
+    construct.dual_traversal(bmin, bmax, q, A.eta)
+    sec = time.perf_counter() - t1
+    out["cpu_baseline"] = {"value": round(nb / sec, 1), "unit": "points/s (structure)", "cores": 1, "kind": "oracle",
+                           "sample": f"oracle/construct.py structure at n={nb} ({sec:.2f} s)"}
+    out["gpu_points_per_s_structure"] = round(A.n / ((t["tree_ms"] + t["blocks_ms"]) * 1e-3), 1)
+    return out
 
 
 def dense_kernel_name(A, nv: int, storage: str, bases_fp32: bool) -> str:
@@ -609,6 +641,9 @@ def main():
 
         # algebraic compression (Sec. 5) of the 2D 8x8-Chebyshev problem at n = 2^16
         out["compression"] = compress_line(h2, dev, "compress_2d_small", 3, 1, cpu=(rank == 0 and world == 1))
+
+        # construction of this workload's matrix on the GPU (Sec. 4.6), FP64 values included
+        out["construction"] = construction_line(h2, A)
 
         if rank == 0 and world == 1:
             sec, reps, cores = run_oracle_baseline(A, x_np)
@@ -857,8 +892,17 @@ def large_main(h2, args, cfg, dev, dist, world, rank, spec):
     gen = spec["dense"] == "generated"
     A = h2gen.generate(**cfg, coupling_values=False, dense_values=not gen)
     t_host = time.perf_counter() - t0
-    M = h2.H2Matrix.from_generator(A, storage=spec["storage"], bases_fp32=spec["bases_fp32"], coupling="kernel",
-                                   dense=spec["dense"])
+    t0 = time.perf_counter()
+    built = None
+    if gen:
+        # the whole matrix from the points on the GPU (h2_build), then a handle that evaluates the coupling
+        # blocks and generates the dense blocks on the device (h2_create_built)
+        built = h2.Built(h2gen.uniform(A.seed, (A.n, A.dim)), m=A.m, p=A.p, eta=A.eta, kernel=A.kernel, ell=A.ell,
+                         values=("U", "E"))
+        M = built.matrix(storage=spec["storage"], bases_fp32=spec["bases_fp32"], coupling="kernel", dense="generated")
+    else:
+        M = h2.H2Matrix.from_generator(A, storage=spec["storage"], bases_fp32=spec["bases_fp32"], coupling="kernel",
+                                       dense=spec["dense"])
     build_s = time.perf_counter() - t0
     A.D_val = None  # the device holds the codes; free the host copy
     info = M.info()
@@ -922,6 +966,11 @@ def large_main(h2, args, cfg, dev, dist, world, rank, spec):
            "vectors_per_s": max(l["vectors_per_s"] for l in lines), "gpu_launches": head["launches_per_step"] * args.steps,
            "rel_err_vs_fp64_oracle": max(l["rel_err_vs_fp64_oracle_sampled_rows"] for l in lines),
            "lines": lines, "build_s": round(build_s, 1), "host_structure_s": round(t_host, 1), "clocks": clk.summary()}
+    if built is not None:
+        out["construction"] = {"gpu_ms": {k: round(v, 2) for k, v in built.times().items()},
+                               "source": "h2_build (structure, U, E on the GPU) + h2_create_built",
+                               "handle_s": round(build_s, 1), "host_generator_s": round(t_host, 1)}
+        built.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     M.close()

@@ -594,13 +594,31 @@ __global__ void __launch_bounds__(128) k_coupling_m(const MatDesc* __restrict__ 
     for (int v = 0; v < NVW; v++) acc[r][v] = 0.f;
   uint4 a0[CB][OPS], a1[CB][OPS];
   float x0[CB][OPS][NVW], x1[CB][OPS][NVW], s0[CB], s1[CB];
-  // loads only: nothing here consumes a loaded value, so a batch's loads stay in flight
-  // while the previous batch is computed
-  auto load = [&](int32_t b0, int nslot, int bt, uint4(&a)[CB][OPS], float(&xv)[CB][OPS][NVW], float(&sc)[CB]) {
+  int32_t cA[CB], cB[CB];   // column nodes of a batch, fetched one batch before its codes and vectors
+  float sA[CB], sB[CB];
+  // the column nodes and scales of a batch: loaded one batch ahead, so that the vector loads
+  // that depend on them never wait inside `load`
+  auto fetch = [&](int32_t b0, int nslot, int bt, int32_t(&col)[CB], float(&scl)[CB]) {
 #pragma unroll
     for (int u = 0; u < CB; u++) {
       const int slot = bt * CB + u;
-      sc[u] = 0.f;
+      col[u] = 0;
+      scl[u] = 0.f;
+      if (slot < nslot) {  // warp-uniform
+        const int32_t gb = b0 + slot / SPB;
+        col[u] = __ldg(Scol + gb);
+        scl[u] = __ldg(sscale + gb);
+      }
+    }
+  };
+  // loads only: nothing here consumes a loaded value, so a batch's loads stay in flight
+  // while the previous batch is computed
+  auto load = [&](int32_t b0, int nslot, int bt, const int32_t(&col)[CB], const float(&scl)[CB],
+                  uint4(&a)[CB][OPS], float(&xv)[CB][OPS][NVW], float(&sc)[CB]) {
+#pragma unroll
+    for (int u = 0; u < CB; u++) {
+      const int slot = bt * CB + u;
+      sc[u] = scl[u];
 #pragma unroll
       for (int o = 0; o < OPS; o++) {
         a[u][o] = make_uint4(0u, 0u, 0u, 0u);
@@ -610,8 +628,7 @@ __global__ void __launch_bounds__(128) k_coupling_m(const MatDesc* __restrict__ 
       if (slot < nslot) {  // warp-uniform
         const int32_t gb = b0 + slot / SPB;
         const int tq = slot % SPB;
-        sc[u] = __ldg(sscale + gb);
-        const float* X = xhat + ((int64_t)__ldg(Scol + gb) * nv + vbase) * kp;
+        const float* X = xhat + ((int64_t)col[u] * nv + vbase) * kp;
         const uint16_t* blk = S + (int64_t)gb * kk8 + 8 * m;
 #pragma unroll
         for (int o = 0; o < OPS; o++) {
@@ -691,22 +708,41 @@ __global__ void __launch_bounds__(128) k_coupling_m(const MatDesc* __restrict__ 
     c.nslot = (__shfl_sync(0xFFFFFFFFu, cr.sr, c.r + 1) - c.b0) * SPB;
     return true;
   };
-  Cursor lc, cc;
+  Cursor ic, lc, cc;   // index fetches run one batch ahead of the loads, the loads one ahead of the compute
+  begin(ic);
   begin(lc);
   begin(cc);
-  load(lc.b0, lc.nslot, lc.bt, a0, x0, s0);
+  fetch(ic.b0, ic.nslot, ic.bt, cA, sA);
+  bool more_i = advance(ic);
+  if (more_i) {
+    fetch(ic.b0, ic.nslot, ic.bt, cB, sB);
+    more_i = advance(ic);
+  }
+  load(lc.b0, lc.nslot, lc.bt, cA, sA, a0, x0, s0);
   bool more = advance(lc);
+  if (more_i) {
+    fetch(ic.b0, ic.nslot, ic.bt, cA, sA);
+    more_i = advance(ic);
+  }
   while (true) {
     if (more) {
-      load(lc.b0, lc.nslot, lc.bt, a1, x1, s1);
+      load(lc.b0, lc.nslot, lc.bt, cB, sB, a1, x1, s1);
       more = advance(lc);
+      if (more_i) {
+        fetch(ic.b0, ic.nslot, ic.bt, cB, sB);
+        more_i = advance(ic);
+      }
     }
     compute(a0, x0, s0);
     if ((cc.bt + 1) * CB >= cc.nslot) flush(cc.r);
     if (!advance(cc)) break;
     if (more) {
-      load(lc.b0, lc.nslot, lc.bt, a0, x0, s0);
+      load(lc.b0, lc.nslot, lc.bt, cA, sA, a0, x0, s0);
       more = advance(lc);
+      if (more_i) {
+        fetch(ic.b0, ic.nslot, ic.bt, cA, sA);
+        more_i = advance(ic);
+      }
     }
     compute(a1, x1, s1);
     if ((cc.bt + 1) * CB >= cc.nslot) flush(cc.r);
