@@ -663,6 +663,7 @@ def main():
 # phase on the tensor cores for passes of 8 or more vectors (64-point leaves)
 MIXED_FORMS = [("int16", True), ("fp16", True), ("fp16", False), ("bf16", False)]
 MIXED_NV = [1, 8, 32, 64]
+MIXED_F32_FORMS = [("int16", True), ("fp16", False)]   # also timed with FP32 vectors
 
 
 def mixed_lines(h2, A, info64, dev, stream, y_ref, x_np, steps, world, rank):
@@ -695,10 +696,28 @@ def mixed_lines(h2, A, info64, dev, stream, y_ref, x_np, steps, world, rank):
             ms = e0.elapsed_time(e1) / k
             yy = Y[:, :min(nv, 2)].cpu().numpy()
             err = oracle.rel_l2(yy, ref2[:, :yy.shape[1]])
-            lines.append({"storage": form, "bases_fp32": bases, "nv": nv, "tuned": tuned, "ms_per_step": round(ms, 4),
-                          "GBs": round(mb * world / (ms * 1e-3) / 1e9, 1),
+            lines.append({"storage": form, "bases_fp32": bases, "nv": nv, "xy": "f64", "tuned": tuned,
+                          "ms_per_step": round(ms, 4), "GBs": round(mb * world / (ms * 1e-3) / 1e9, 1),
                           "vectors_per_s": round(nv * world / (ms * 1e-3), 1),
                           "stored_bytes": mb, "rel_err_vs_fp64_oracle": err})
+            if (form, bases) in MIXED_F32_FORMS and nv in (1, max(MIXED_NV)):
+                # the same product with FP32 vectors (h2_matvec_f32): half the vector bytes
+                X32 = X.float().t().contiguous().t()
+                Y32 = torch.empty((nv, A.n), dtype=torch.float32, device=dev).t()
+                for _ in range(3):
+                    M.matvec_f32(X32, Y32, stream=stream)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(k):
+                    M.matvec_f32(X32, Y32, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms32 = e0.elapsed_time(e1) / k
+                yy = Y32[:, :min(nv, 2)].cpu().numpy().astype(np.float64)
+                lines.append({"storage": form, "bases_fp32": bases, "nv": nv, "xy": "f32", "tuned": tuned,
+                              "ms_per_step": round(ms32, 4), "GBs": round(mb * world / (ms32 * 1e-3) / 1e9, 1),
+                              "vectors_per_s": round(nv * world / (ms32 * 1e-3), 1), "stored_bytes": mb,
+                              "rel_err_vs_fp64_oracle": oracle.rel_l2(yy, ref2[:, :yy.shape[1]])})
         M.close()
     return lines
 

@@ -210,6 +210,13 @@ h2_status h2_create_generated(const h2_desc* d, const h2_coupling_kernel* kc, co
 h2_status h2_matvec(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream);
 
 /*
+ * As h2_matvec with FP32 vectors (x read and y written as float), for the
+ * scaled storage forms, whose arithmetic is FP32 anyway: half the vector
+ * traffic of the FP64 call. H2_ERR_UNSUPPORTED for the FP64 form.
+ */
+h2_status h2_matvec_f32(h2_handle h, int32_t nv, const float* x, int64_t ldx, float* y, int64_t ldy, void* stream);
+
+/*
  * Same product with HOST buffers: x is copied host->device, the product runs,
  * y is copied device->host, and the call returns after `stream` has drained.
  * Pinned host memory gives full-speed copies; pageable memory works too.

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "H2_OK", 1: "H2_ERR_INVALID", 2: "H2_ERR_OOM", 3: "H2_ERR_CUD
                 5: "H2_ERR_TIMEOUT"}
 
 # every symbol include/h2.h declares
-EXPORTS = ["h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
+EXPORTS = ["h2_create", "h2_create_kernel_coupling", "h2_matvec", "h2_matvec_f32", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
            "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_create_generated", "h2_tune", "h2_destroy", "h2_batch_create", "h2_batch_matvec", "h2_batch_check",
            "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_tune", "h2_batch_destroy",
            "h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read", "h2_compress_profile",
@@ -73,6 +73,7 @@ def _load():
     lib.h2_create_generated.argtypes = [ctypes.POINTER(h2_desc), ctypes.POINTER(h2_coupling_kernel), vp, ctypes.POINTER(vp)]
     lib.h2_matvec.argtypes = [vp, i32, vp, i64, vp, i64, vp]
     lib.h2_matvec_host.argtypes = [vp, i32, vp, i64, vp, i64, vp]
+    lib.h2_matvec_f32.argtypes = [vp, i32, vp, i64, vp, i64, vp]
     lib.h2_info.argtypes = [vp, vp]
     lib.h2_destroy.argtypes = [vp]
     lib.h2_profile.argtypes = [vp, i32]
@@ -105,7 +106,7 @@ def _load():
     lib.h2_built_destroy.argtypes = [vp]
     lib.h2_create_built.argtypes = [vp, i32, i32, i32, ctypes.POINTER(vp)]
     lib.h2_last_error.restype = ctypes.c_char_p
-    for name in ("h2_create_built", "h2_build", "h2_built_info", "h2_built_times", "h2_built_read", "h2_built_destroy", "h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read",
+    for name in ("h2_matvec_f32", "h2_create_built", "h2_build", "h2_built_info", "h2_built_times", "h2_built_read", "h2_built_destroy", "h2_compress_create", "h2_compress_run", "h2_compress_result", "h2_compress_read",
                  "h2_compress_profile", "h2_compress_profile_read", "h2_compress_info", "h2_compress_destroy", "h2_create", "h2_create_kernel_coupling", "h2_create_generated", "h2_matvec", "h2_matvec_host", "h2_check", "h2_debug_withhold_copy", "h2_info", "h2_profile",
                  "h2_profile_read", "h2_matvec_static", "h2_matvec_static_check", "h2_destroy", "h2_batch_create", "h2_batch_matvec",
                  "h2_batch_check", "h2_batch_info", "h2_batch_profile", "h2_batch_profile_read", "h2_batch_destroy",
@@ -217,6 +218,26 @@ class H2Matrix:
         ldx = X.stride(1) if nv > 1 else self.n
         ldy = Y.stride(1) if nv > 1 else self.n
         _check(_lib.h2_matvec(self._h, nv, _ptr(X), ldx, _ptr(Y), ldy, _stream_ptr(stream)))
+        return Y[:, 0] if (vec and y is None) else (y if y is not None else Y)
+
+    def matvec_f32(self, x, y=None, stream=None):
+        """y = A^H x with FP32 vectors (h2_matvec_f32; scaled storage forms). x, y: torch float32 CUDA
+        tensors, shape (n,) or (n, nv) column-major."""
+        import torch
+        assert x.is_cuda and x.dtype == torch.float32
+        vec = x.dim() == 1
+        X = x.unsqueeze(1) if vec else x
+        if X.stride(0) != 1:
+            X = X.t().contiguous().t()
+        nv = X.shape[1]
+        if y is None:
+            Y = torch.empty((nv, self.n), dtype=torch.float32, device=x.device).t()
+        else:
+            Y = y.unsqueeze(1) if y.dim() == 1 else y
+            assert Y.stride(0) == 1 and Y.dtype == torch.float32
+        ldx = X.stride(1) if nv > 1 else self.n
+        ldy = Y.stride(1) if nv > 1 else self.n
+        _check(_lib.h2_matvec_f32(self._h, nv, _ptr(X), ldx, _ptr(Y), ldy, _stream_ptr(stream)))
         return Y[:, 0] if (vec and y is None) else (y if y is not None else Y)
 
     def matvec_host(self, x: np.ndarray, y: np.ndarray | None = None, stream=None) -> np.ndarray:

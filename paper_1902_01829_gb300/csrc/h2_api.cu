@@ -827,6 +827,20 @@ h2_status h2_matvec(h2_handle h, int32_t nv, const double* x, int64_t ldx, doubl
   return matvec_device(h, nv, x, ldx, y, ldy, (cudaStream_t)stream);
 }
 
+h2_status h2_matvec_f32(h2_handle h, int32_t nv, const float* x, int64_t ldx, float* y, int64_t ldy, void* stream) {
+  if (!h || !x || !y) return fail(H2_ERR_INVALID, "NULL handle or vector");
+  if (nv < 1) return fail(H2_ERR_INVALID, "nv = %d < 1", nv);
+  if (ldx < h->n || ldy < h->n) return fail(H2_ERR_INVALID, "leading dimension below n");
+  if (h->storage == H2_FP64) return fail(H2_ERR_UNSUPPORTED, "FP32 vectors need a scaled storage form");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int v0 = 0; v0 < nv; v0 += kPassVectors) {
+    const int nvp = std::min(kPassVectors, nv - v0);
+    h2_status s = mixed_pass(h, nvp, x + (int64_t)v0 * ldx, ldx, y + (int64_t)v0 * ldy, ldy, st, 1);
+    if (s != H2_OK) return s;
+  }
+  return H2_OK;
+}
+
 h2_status h2_matvec_host(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream) {
   if (!h || !x || !y) return fail(H2_ERR_INVALID, "NULL handle or vector");
   if (nv < 1) return fail(H2_ERR_INVALID, "nv = %d < 1", nv);

@@ -86,8 +86,9 @@ struct TcCall {
   int64_t leaves = 0, leaf0 = 0;
   int k = 0, kp = 0, grid = 0;
   float dmax = 0.f, umax = 0.f;  // largest block scale of the dense blocks and of the leaf bases
-  double* y = nullptr;
+  double* y = nullptr;   // FP32 when y32
   int64_t ldy = 0;
+  int y32 = 0;
   int nv = 0;
   int* err = nullptr;
   long long budget = kWaitBudget;
@@ -255,7 +256,9 @@ h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cuda
 h2_status mixed_configure(h2_matrix_s* h, int chunk_opt, int cw, int tree_opt);
 // passes of at least this many vectors use the tensor-core dense phase (panel-layout handles)
 constexpr int kTcMinVectors = 8;
-h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st);
+// one pass of up to 16 vectors; xy32: x and y are FP32 (else FP64)
+h2_status mixed_pass(h2_matrix_s* h, int nv, const void* x, int64_t ldx, void* y, int64_t ldy, cudaStream_t st,
+                     int xy32 = 0);
 
 }  // namespace h2i
 

@@ -102,6 +102,7 @@ struct CallChunk {
   long long ldx[kCallChunk];
   long long ldy[kCallChunk];
   int nv[kCallChunk];
+  int xy32;
 };
 static_assert(sizeof(CallChunk) < 32000, "kernel parameter space");
 
@@ -114,6 +115,7 @@ __global__ void k_set_calls(h2::MatDesc* mats, CallChunk c) {
     D.y = c.y[i];
     D.ldy = c.ldy[i];
     D.nv = c.nv[i];
+    D.xy32 = c.xy32;
   }
 }
 
@@ -158,10 +160,11 @@ h2::MatDesc fill_desc(const h2_matrix_s* h, int tree_L) {
 
 // write the fields of one product pass into a matrix table (entries [0, count))
 h2_status set_calls(h2::MatDesc* mats, int64_t count, const int* nv, const double* const* x, const int64_t* ldx,
-                    double* const* y, const int64_t* ldy, cudaStream_t st) {
+                    double* const* y, const int64_t* ldy, cudaStream_t st, int xy32 = 0) {
   for (int64_t c0 = 0; c0 < count; c0 += kCallChunk) {
     CallChunk c{};
     c.first = (int)c0;
+    c.xy32 = xy32;
     c.count = (int)std::min<int64_t>(kCallChunk, count - c0);
     for (int i = 0; i < c.count; i++) {
       c.x[i] = x[c0 + i];
@@ -844,13 +847,17 @@ h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cuda
   }
 }
 
-h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
+h2_status mixed_pass(h2_matrix_s* h, int nv, const void* xv, int64_t ldx, void* yv, int64_t ldy, cudaStream_t st,
+                     int xy32) {
+  // the kernels take the vectors' element type from the descriptor (xy32)
+  const double* x = static_cast<const double*>(xv);
+  double* y = static_cast<double*>(yv);
   MixedLaunch L = h->mx.launch;
   L.budget = h->budget;
   L.prof = &h->prof;
   cudaError_t me = mark(&h->prof, st);
   if (me != cudaSuccess) return h2_fail(H2_ERR_CUDA, "profiling event: %s", cudaGetErrorString(me));
-  h2_status s = set_calls(static_cast<h2::MatDesc*>(L.mats), 1, &nv, &x, &ldx, &y, &ldy, st);
+  h2_status s = set_calls(static_cast<h2::MatDesc*>(L.mats), 1, &nv, &x, &ldx, &y, &ldy, st, xy32);
   if (s != H2_OK) return s;
   const MixedData& M = h->mx;
   if (M.panel && nv >= kTcMinVectors && h->storage != H2_INT16_SCALED) {  // dense phase on the tensor cores
@@ -874,6 +881,7 @@ h2_status mixed_pass(h2_matrix_s* h, int nv, const double* x, int64_t ldx, doubl
     T.umax = M.umax;
     T.y = y;
     T.ldy = ldy;
+    T.y32 = xy32;
     T.nv = nv;
     T.err = h->err;
     T.budget = h->budget;

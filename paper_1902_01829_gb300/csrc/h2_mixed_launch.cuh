@@ -148,6 +148,7 @@ h2_status tc_launch(const TcCall& T, cudaStream_t st) {
     P.y = T.y;
     P.ldy = T.ldy;
     P.nv = T.nv;
+    P.y32 = T.y32;
     P.kp = T.kp;
     P.err = T.err;
     P.budget = T.budget;

@@ -126,8 +126,24 @@ struct MatDesc {
   long long ldx;
   double* y;
   long long ldy;
-  int nv, pad1;
+  int nv, xy32;   // xy32: x and y are FP32 (else FP64)
 };
+
+// x and y are FP64 or, for products that ask for it, FP32 (MatDesc::xy32)
+__device__ __forceinline__ float x_load(const double* x, bool x32, long long idx) {
+  return x32 ? __ldg(reinterpret_cast<const float*>(x) + idx) : __double2float_rn(__ldg(x + idx));
+}
+__device__ __forceinline__ void y_store(void* y, bool y32, long long idx, float v, bool assign) {
+  if (y32) {
+    float* p = reinterpret_cast<float*>(y) + idx;
+    if (assign) *p = v;
+    else atomicAdd(p, v);
+  } else {
+    double* p = reinterpret_cast<double*>(y) + idx;
+    if (assign) *p = (double)v;
+    else atomicAdd(p, (double)v);
+  }
+}
 
 // ---------------------------------------------------------------- generic warp routine
 // rows += scale * (A * x_cols) for a column-major R x C block of codes; lane
@@ -212,7 +228,7 @@ struct TreeParamsM {
   float* yhat;
   int* ticket;
   int64_t kk8;
-  int k, kp, LR, q, L, nv;
+  int k, kp, LR, q, L, nv, xy32;
 };
 
 constexpr int kTreeWarpsM = 8;
@@ -241,6 +257,7 @@ __device__ __forceinline__ TreeParamsM tree_params(const MatDesc& D) {
   P.q = D.q;
   P.L = D.L;
   P.nv = D.nv;
+  P.xy32 = D.xy32;
   return P;
 }
 
@@ -267,7 +284,6 @@ __device__ __forceinline__ void project_leaf_m(const TreeParamsM& P, int64_t j, 
   const int spad = (sj + 3) & ~3;
   float* xj = P.x4 + P.xp4_off[j] * P.nv;
   if (convert) {
-    const double* __restrict__ xs = P.x + off;
     // every load of the chunk is issued before any store (the stores could alias x for the compiler)
     float xr[NVB][2];
 #pragma unroll
@@ -275,7 +291,7 @@ __device__ __forceinline__ void project_leaf_m(const TreeParamsM& P, int64_t j, 
 #pragma unroll
       for (int h = 0; h < 2; h++) {
         const int a = lane + 32 * h;
-        xr[v][h] = (v < P.nv && a < sj) ? __double2float_rn(__ldg(xs + v * P.ldx + a)) : 0.f;  // padding is zero
+        xr[v][h] = (v < P.nv && a < sj) ? x_load(P.x, P.xy32, off + v * P.ldx + a) : 0.f;  // padding is zero
       }
 #pragma unroll
     for (int v = 0; v < NVB; v++)
@@ -430,10 +446,7 @@ __device__ __forceinline__ void expand_leaf_m(const MatDesc& D, int64_t j, int l
 #pragma unroll
     for (int v = 0; v < NVB; v++)
       if (v < nv) {
-        double* yp = D.y + v * D.ldy + off + row;
-        const double val = (double)(mb.scale * acc[r][v]);
-        if (assign) *yp = val;
-        else atomicAdd(yp, val);
+        y_store(D.y, D.xy32, v * D.ldy + off + row, mb.scale * acc[r][v], assign);
       }
   }
   __syncwarp();  // wbuf is reused by the warp's next leaf
@@ -951,7 +964,7 @@ struct MixedStreamParams {
 // blocks' codes and vector chunks then follow each other at fixed strides); block t at 8 + 4 t:
 // cols | FP32-entries flag << 16, vs, matrix offset in bytes, scale (bits);
 // [40 + t] block t's vector offset in bytes; [48] nv; [50..51] y; [52..53] ldy.
-constexpr int kHdVoff = 40, kHdNv = 48, kHdY = 50, kHdLdy = 52;
+constexpr int kHdVoff = 40, kHdNv = 48, kHdXy32 = 49, kHdY = 50, kHdLdy = 52;
 template <int NST, int SB, int VAREA>
 __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const StreamShared& S, int ib, int ie,
                                               MixedBlock* blkbuf) {
@@ -986,7 +999,7 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
     const float* l_yhat = nullptr;
     double* l_y = nullptr;
     long long l_ldy = 0;
-    int l_nv = 0;
+    int l_nv = 0, l_xy32 = 0;
     if (base + lane < ie) {
       const MatDesc& D = P.mats[d1.w >> 8];
       l_dmat = D.dmat;
@@ -995,6 +1008,7 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
       l_y = D.y;
       l_ldy = D.ldy;
       l_nv = D.nv;
+      l_xy32 = D.xy32;
     }
     __syncwarp();
     for (int t = 0; t < cnt; t++) {
@@ -1024,6 +1038,7 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
       const unsigned long long ydst = __shfl_sync(0xFFFFFFFFu, (unsigned long long)l_y, t);
       const long long ldy = (long long)__shfl_sync(0xFFFFFFFFu, (unsigned long long)l_ldy, t);
       const int nv = __shfl_sync(0xFFFFFFFFu, l_nv, t);
+      const int xy32 = __shfl_sync(0xFFFFFFFFu, l_xy32, t);
       unsigned char* stage = S.stage0 + s * SB;
       int* hd = reinterpret_cast<int*>(stage);
       // per-block side information, one lane per block
@@ -1067,6 +1082,7 @@ __device__ __forceinline__ void mixed_produce(const MixedStreamParams& P, const 
         hd[3] = flags;
         hd[4] = uniform;
         hd[kHdNv] = nv;
+        hd[kHdXy32] = xy32;
         *reinterpret_cast<unsigned long long*>(hd + kHdY) = ydst;
         *reinterpret_cast<long long*>(hd + kHdLdy) = ldy;
       }
@@ -1435,7 +1451,8 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
     const int* hd = reinterpret_cast<const int*>(stage);
     const int R = min(hd[0], 64), nb = min(hd[1], kMixedMaxBlocks), row = hd[2], flags = hd[3];
     const int nv = min(hd[kHdNv], NVB);
-    double* const ydst = reinterpret_cast<double*>(*reinterpret_cast<const unsigned long long*>(hd + kHdY));
+    void* const ydst = reinterpret_cast<void*>(*reinterpret_cast<const unsigned long long*>(hd + kHdY));
+    const bool y32 = hd[kHdXy32] != 0;
     const long long ldy = *reinterpret_cast<const long long*>(hd + kHdLdy);
     // the variant for the item's vector count (a matrix of a batch may take fewer than NVB)
     const bool eight = kEight && R > 32;
@@ -1515,7 +1532,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
           float sum = 0.f;
 #pragma unroll
           for (int w = 0; w < CW; w++) sum += red[(w * NVB + v) * 64 + r];
-          atomicAdd(ydst + v * ldy + row + r, (double)sum);  // y was zeroed; the leaf expansion adds too
+          y_store(ydst, y32, v * ldy + row + r, sum, false);  // y was zeroed or assigned; the other part adds too
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(S.rowfree);
@@ -1535,7 +1552,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1) k_dense_stream_m(MixedStream
           float sum = 0.f;
 #pragma unroll
           for (int w = 0; w < CW; w++) sum += redp[(w * NVB + v) * 64 + r];
-          atomicAdd(ydst + v * ldy + row + r, (double)sum);  // y was zeroed; the leaf expansion adds too
+          y_store(ydst, y32, v * ldy + row + r, sum, false);  // y was zeroed or assigned; the other part adds too
         }
         __syncwarp();
         if (lane == 0) {
@@ -1572,18 +1589,17 @@ __global__ void __launch_bounds__(256) k_split_x4(const MatDesc* __restrict__ ma
     const int64_t off = D.leaf_off[J.leaf];
     const int sj = (int)(D.leaf_off[J.leaf + 1] - off), spad = (sj + 3) & ~3;
     float* xj = D.x4 + D.xp4_off[J.leaf] * nv;
-    const double* __restrict__ xs = D.x + off;
-    double* __restrict__ yz = D.y + off;
+    const bool xy32 = D.xy32 != 0;
 #pragma unroll 4
     for (int v = 0; v < nv; v++) {
       // leaf sizes <= 64: two entries per lane
-      const double x0 = lane < sj ? __ldg(xs + v * D.ldx + lane) : 0.0;
-      const double x1 = lane + 32 < sj ? __ldg(xs + v * D.ldx + lane + 32) : 0.0;
-      if (lane < spad) xj[v * spad + lane] = __double2float_rn(x0);
-      if (lane + 32 < spad) xj[v * spad + lane + 32] = __double2float_rn(x1);
+      const float x0 = lane < sj ? x_load(D.x, xy32, off + v * D.ldx + lane) : 0.f;
+      const float x1 = lane + 32 < sj ? x_load(D.x, xy32, off + v * D.ldx + lane + 32) : 0.f;
+      if (lane < spad) xj[v * spad + lane] = x0;
+      if (lane + 32 < spad) xj[v * spad + lane + 32] = x1;
       if (zero_y) {
-        if (lane < sj) yz[v * D.ldy + lane] = 0.0;
-        if (lane + 32 < sj) yz[v * D.ldy + lane + 32] = 0.0;
+        if (lane < sj) y_store(D.y, xy32, off + v * D.ldy + lane, 0.f, true);
+        if (lane + 32 < sj) y_store(D.y, xy32, off + v * D.ldy + lane + 32, 0.f, true);
       }
     }
   }

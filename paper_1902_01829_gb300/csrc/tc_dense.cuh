@@ -98,9 +98,9 @@ struct TcParams {
   const float* yhat;    // [node][v][kp]
   const float* vscale;  // [16] per-vector power-of-two scale s_v
   const int4* brec;     // builder records, kTcRecInts / 4 per item
-  double* y;
+  double* y;            // FP32 when y32
   long long ldy;
-  int nv, kp;
+  int nv, kp, y32, pad0;
   int* err;
   long long budget;
 };
@@ -502,10 +502,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
           for (int v = 0; v < kTcVec; v++) sum[v] += xr[v];
           __syncwarp();
           if (lane == 0) mbar_arrive(accempty + b);
-          double* yr = P.y + row_off + 32 * q + lane;
+          const long long yo = row_off + 32 * q + lane;
 #pragma unroll
           for (int v = 0; v < kTcVec; v++)
-            if (v < P.nv) yr[v * P.ldy] = (double)(sum[v] * inv[v]);
+            if (v < P.nv) {
+              if (P.y32) reinterpret_cast<float*>(P.y)[yo + v * P.ldy] = sum[v] * inv[v];
+              else P.y[yo + v * P.ldy] = (double)(sum[v] * inv[v]);
+            }
         }
         r++;
       }

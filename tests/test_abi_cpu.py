@@ -25,7 +25,7 @@ def h2():
 def _declared_symbols():
     src = open(os.path.join(ROOT, "include", "h2.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(h2_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(h2_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol(h2):

@@ -179,3 +179,37 @@ def test_tune_chooses_a_candidate_and_keeps_the_product(h2, c1):
     F = h2.H2Matrix.from_generator(c1, storage="fp64")
     assert F.tune(X, Y) == {"consumer_warps": 0, "chunk_blocks": 0, "tree_leaves": 0}  # no options in the plain form
     F.close()
+
+
+@pytest.mark.parametrize("form,bases_fp32,dims", [("int16", True, (2, 4096, 32, 4)), ("fp16", True, (2, 4096, 32, 4)),
+                                                 ("fp16", False, (2, 8192, 64, 4)), ("bf16", False, (3, 16384, 64, 4))])
+@pytest.mark.parametrize("nv", [1, 3, 16, 20])
+def test_fp32_vectors(h2, form, bases_fp32, dims, nv):
+    """h2_matvec_f32: x read and y written as FP32. Against the quantized oracle on the same (FP32-exact)
+    x, the bound of the FP32 accumulation plus the rounding of y to FP32 (2^-24 relative); fp16/bf16 with
+    16-bit bases and 64-point leaves take the tensor-core dense phase at 8 or more vectors (split term)."""
+    dim, n, m, p = dims
+    A = h2gen.generate(dim=dim, n=n, m=m, p=p, eta=0.9, kernel="exp", ell=0.1 if dim == 2 else 0.2, seed=17)
+    x = h2gen.vectors(640 + nv, A.n, nv).astype(np.float32).astype(np.float64)
+    M = h2.H2Matrix.from_generator(A, storage=form, bases_fp32=bases_fp32)
+    x32 = torch.from_numpy(np.ascontiguousarray(x.T.astype(np.float32))).cuda().t()
+    y32 = M.matvec_f32(x32)
+    y64 = M.matvec(to_dev(x))
+    M.check()
+    assert y32.dtype == torch.float32
+    y32 = y32.cpu().numpy().astype(np.float64)
+    y64 = y64.cpu().numpy()
+    M.close()
+    tc = (not bases_fp32) and m == 64 and nv >= 8
+    tol = acc_tol(A) + 2.0 ** -24 + (tc_split_tol(form) if tc else 0.0)
+    ref = oracle.matvec(A, x, **quant.dequantized_arrays(A, form, bases_fp32))
+    check(oracle.rel_l2(y32, ref), tol, ("fp32 x/y", form, bases_fp32, dims, nv))
+    assert oracle.rel_l2(y32, y64) <= tol
+
+
+def test_fp32_vectors_rejected_for_fp64_form(h2, c1):
+    M = h2.H2Matrix.from_generator(c1)
+    with pytest.raises(h2.H2Error) as ei:
+        M.matvec_f32(torch.zeros(c1.n, dtype=torch.float32, device="cuda"))
+    assert ei.value.status == h2.H2_ERR_UNSUPPORTED
+    M.close()
