@@ -451,6 +451,8 @@ def main():
     ap.add_argument("--coupling", default="stored", choices=["stored", "kernel"],
                     help="scaled forms: coupling blocks stored, or evaluated from the kernel in every product")
     ap.add_argument("--no-batch", action="store_true", help="extras without the batched-workload line")
+    ap.add_argument("--batch-count", type=int, default=256, help="--workload batch256: members of the batch (the "
+                    "first ones of the 256-member workload; fewer for profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -874,7 +876,7 @@ def batch_main(h2, args, dev, dist, world, rank, hbm, peak_kind):
     import torch
 
     with ClockSampler(dev.index) as clk:
-        b = batch_line(h2, dev, args.steps, world, rank, hbm, timed_barrier=dist)
+        b = batch_line(h2, dev, args.steps, world, rank, hbm, count=args.batch_count, timed_barrier=dist)
     out = {"metric": METRIC, "value": b["GBs"], "unit": "GB/s", "n_gpus": world, "steps": max(5, args.steps),
            "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "fp16 + per-block f32 scale (stored) / f32 (computed)", "data": "synthetic",

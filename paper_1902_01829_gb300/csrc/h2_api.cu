@@ -879,7 +879,7 @@ h2_status h2_tune(h2_handle h, int32_t nv, const double* x, int64_t ldx, double*
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
   // 16 dense consumer warps exist for passes of at most 8 vectors
-  const int ncw = std::min(nv, kPassVectors) <= 8 ? 2 : 1;
+  const int ncw = 2;  // 8 or 16 dense consumer warps
   float best = 3.4e38f;
   int best_opt = kDefaultChunkOpt, best_cw = h->mx.launch.cw, best_tree = 0;
   h2_status s = H2_OK;

@@ -1179,7 +1179,7 @@ h2_status h2_batch_tune(h2_batch b, const int32_t* nv, const double* const* x, c
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
-  const int ncw = std::min(nvmax, kPassVectors) <= 8 ? 2 : 1;  // 16 dense consumer warps: passes of <= 8 vectors
+  const int ncw = 2;  // 8 or 16 dense consumer warps
   float best = 3.4e38f;
   int best_c = b->chunk_opt, best_t = b->tree_opt, best_cw = b->launch.cw;
   h2_status s = H2_OK;

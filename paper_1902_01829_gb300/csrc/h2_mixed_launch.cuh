@@ -105,12 +105,11 @@ h2_status dense_launch_cw(const MixedLaunch& L, cudaStream_t st) {
 
 // consumer warps of the dense stream: rows of at most 32 points give each warp little
 // arithmetic per item, and twice the warps hide more latency (measured: 163 -> 134 us on a
-// 2^17-point matrix with 32-point leaves); 64-point rows run faster with 8
+// 2^17-point matrix with 32-point leaves); 64-point rows run faster with 8. With 16 vectors
+// per pass the 16-warp variant fits 96 registers a thread (a few spilled).
 template <int F, int NVB>
 h2_status dense_launch(const MixedLaunch& L, cudaStream_t st) {
-  if constexpr (NVB <= 8) {
-    if (L.cw == 2 * h2::kMixedCW) return dense_launch_cw<F, NVB, 2 * h2::kMixedCW>(L, st);
-  }
+  if (L.cw == 2 * h2::kMixedCW) return dense_launch_cw<F, NVB, 2 * h2::kMixedCW>(L, st);
   return dense_launch_cw<F, NVB, h2::kMixedCW>(L, st);
 }
 
