@@ -63,6 +63,7 @@ struct MixedLaunch {
   bool bases_fp32 = false;
   int cw = 8;                        // consumer warps of the dense stream (8, or 16 for passes of <= 8 vectors)
   bool kf = false;                   // coupling blocks evaluated from the kernel (no stored S)
+  int kf_kind = 0;                   // its kernel: H2_KERNEL_EXP or H2_KERNEL_MATERN32
   Profiler* prof = nullptr;          // profiler whose events mark the phases (or none)
   const void* rjobs = nullptr;       // h2::RowJob per leaf row of every matrix (split x, leaf expansion)
   int64_t nrjobs = 0;

@@ -826,6 +826,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   L.k = k;
   L.bases_fp32 = M.bases_fp32;
   L.kf = h->kf;
+  L.kf_kind = h->kf_kind;
   L.rjobs = M.rjobs;
   L.nrjobs = leaves;
   CUDA_TRY(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));

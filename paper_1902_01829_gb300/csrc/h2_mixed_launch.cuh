@@ -37,7 +37,8 @@ void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st, bo
     constexpr int NVW = NVB < 4 ? NVB : 4, VG = NVB / NVW;
     prefer_max_shared(k_upsweep_tree_m<FB, RPL, NVB>);
     prefer_max_shared(k_downsweep_tree_m<FB, RPL, NVB>);
-    prefer_max_shared(k_coupling_kf<RPL, NVB>);
+    prefer_max_shared(k_coupling_kf<RPL, NVB, 0>);
+    prefer_max_shared(k_coupling_kf<RPL, NVB, 1>);
     prefer_max_shared(k_coupling_m<F, 16, NVW, (NVW <= 2 ? 4 : 2), VG>);
     prefer_max_shared(k_coupling_m<F, 32, NVW, (NVW <= 1 ? 2 : 1), VG>);
     prefer_max_shared(k_coupling_m<F, 64, NVW, (NVW <= 1 ? 2 : 1), VG>);
@@ -53,7 +54,8 @@ void bucket_phase(const MixedLaunch& L, int phase, int nvlo, cudaStream_t st, bo
     const unsigned cgrid = (unsigned)((L.nchunks + 3) / 4);
     const int k = L.k;
     if (L.kf) {  // coupling blocks evaluated from the kernel
-      k_coupling_kf<RPL, NVB><<<cgrid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
+      if (L.kf_kind == 1) k_coupling_kf<RPL, NVB, 1><<<cgrid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
+      else k_coupling_kf<RPL, NVB, 0><<<cgrid, 128, 0, st>>>(mats, L.chunks, L.nchunks, nvlo, NVB);
     } else if (k == 16 || k == 32 || k == 64) {
       // up to four vectors per warp; 8 and 16 vectors take two and four warps per chunk
       constexpr int NVW = NVB < 4 ? NVB : 4, VG = NVB / NVW;

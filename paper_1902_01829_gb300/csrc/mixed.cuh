@@ -818,7 +818,15 @@ __global__ void __launch_bounds__(128) k_coupling_m_generic(const MatDesc* __res
 // stages its block's column points and vectors in the warp's shared memory; r = r2 * rsqrt(r2)
 // and exp(-t) = __expf(-t) (CUDA's fast intrinsics: relative errors of a few 1e-6 here, below the
 // form's FP32 accumulation bound).
-template <int RPL, int NVB>
+// 2^x by the special-function unit (PTX ex2.approx: relative error a few 2^-23)
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// KIND: H2_KERNEL_EXP (0) or H2_KERNEL_MATERN32 (1); the descriptor's kf_kind selects the instance
+template <int RPL, int NVB, int KIND>
 __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const MatDesc* __restrict__ mats,
                                                                      const int4* __restrict__ chunks, int64_t nchunks,
                                                                      int nvlo, int nvhi) {
@@ -840,8 +848,8 @@ __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const Mat
   const float4* __restrict__ clo = D.kf_clo;
   const float4* __restrict__ off = D.kf_off;
   const float inv_ell = D.kf_inv_ell;
-  const bool matern = D.kf_kind == 1;
-  const float tscale = matern ? 1.7320508f * inv_ell : inv_ell;
+  // exp: K = 2^(-r c), c = log2(e) / ell; Matern-3/2: t = r sqrt(3) / ell, K = (1 + t) 2^(-t log2(e))
+  const float tscale = KIND == 1 ? 1.7320508f * inv_ell : 1.4426950f * inv_ell;
   const int32_t* __restrict__ Scol = D.Scol;
   const float* __restrict__ xhat = D.xhat;
   float* __restrict__ yhat = D.yhat;
@@ -877,6 +885,17 @@ __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const Mat
         const float4 hi_j = __ldg(chi + j), lo_j = __ldg(clo + j);
         const float cx = (hi_i.x - hi_j.x) + (lo_i.x - lo_j.x), cy = (hi_i.y - hi_j.y) + (lo_i.y - lo_j.y),
                     cz = (hi_i.z - hi_j.z) + (lo_i.z - lo_j.z);
+        // row point minus the column centre, once per block: a coordinate difference is then one
+        // subtraction. The clusters of a coupling block are separated (their boxes' distance is
+        // positive and at least their diameter / eta), so the difference does not cancel and
+        // keeps FP32 relative precision, and r^2 > 0.
+        float ax[RPL], ay[RPL], az[RPL];
+#pragma unroll
+        for (int rr = 0; rr < RPL; rr++) {
+          ax[rr] = cx + oi[rr].x;
+          ay[rr] = cy + oi[rr].y;
+          az[rr] = cz + oi[rr].z;
+        }
         // one run of four columns; FULL: all four below k (no clamping or masking)
         auto run = [&](int mu0, auto full_tag) {
           constexpr bool FULL = decltype(full_tag)::value;
@@ -886,11 +905,16 @@ __global__ void __launch_bounds__(128, RPL == 1 ? 6 : 4) k_coupling_kf(const Mat
             const float4 oj = obuf[FULL ? mu0 + e : min(mu0 + e, k - 1)];
 #pragma unroll
             for (int rr = 0; rr < RPL; rr++) {
-              const float dx = cx + (oi[rr].x - oj.x), dy = cy + (oi[rr].y - oj.y), dz = cz + (oi[rr].z - oj.z);
+              const float dx = ax[rr] - oj.x, dy = ay[rr] - oj.y, dz = az[rr] - oj.z;
               const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              const float t = (r2 > 0.f ? r2 * rsqrtf(r2) : 0.f) * tscale;
-              const float ex = __expf(-t);
-              const float val = matern ? (1.f + t) * ex : ex;
+              const float t = (r2 * rsqrtf(r2)) * tscale;
+              float val;
+              if constexpr (KIND == 1) {
+                const float ex = ex2_approx(-1.4426950f * t);
+                val = fmaf(t, ex, ex);
+              } else {
+                val = ex2_approx(-t);
+              }
               sv[rr][e] = (FULL || mu0 + e < k) ? val : 0.f;
             }
           }
