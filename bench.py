@@ -45,6 +45,10 @@ WORKLOADS = {
     "compress_2d": "algebraic compression (Sec. 5: orthogonalization, basis generation, truncation, projection) of the "
                    "2D exp(-r/0.1) covariance H^2 matrix, n=2^20 uniform points, m=64, k=64 (8x8 Chebyshev), eta=0.9, "
                    "FP64, relative threshold 1e-7",
+    "build_2d": "construction on the GPU (Sec. 4.6: KD tree, boxes, Chebyshev nodes, dual traversal, FP64 U, E, S, D) "
+                "of the 2D exp(-r/0.1) covariance H^2 matrix, n=2^20 uniform points, m=64, k=16, eta=0.9",
+    "build_3d": "construction on the GPU (Sec. 4.6; structure, U and E) of the 3D Matern-3/2 (length 0.1) covariance "
+                "H^2 matrix, n=2^22 uniform points in the unit cube, m=64, k=64, eta=0.7",
     "compress_2d_small": "algebraic compression (Sec. 5) of the 2D exp(-r/0.1) covariance H^2 matrix, n=2^16 uniform "
                          "points, m=64, k=64 (8x8 Chebyshev), eta=0.9, FP64, relative threshold 1e-7",
     "compress_3d": "algebraic compression (Sec. 5) of the 3D exp(-r/0.2) covariance H^2 matrix, n=2^18 uniform points "
@@ -331,6 +335,71 @@ def compress_line(h2, dev, name: str, steps: int, warmup: int, cpu: bool = True)
 
 
 COMPRESS_METRIC = "H^2 algebraic compression throughput (points/s) and time, Sec. 5"
+BUILD = {"build_2d": ("2d_n1M", ("U", "E", "S", "D")), "build_3d": ("3d_n4M", ("U", "E"))}
+
+
+def reference_build(args):
+    """The construction oracle (oracle/construct.py, plain numpy) on a bounded sample of the workload's family:
+    the structure (cluster tree, boxes, dual traversal) of 2^14 points."""
+    import oracle
+    from oracle import construct
+
+    name, _ = BUILD[args.workload]
+    cfg = dict(h2gen.CONFIGS[name])
+    nb = 1 << 14
+    pts = h2gen.uniform(cfg["seed"], (nb, cfg["dim"]))
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t = time.perf_counter()
+        perm, lo, q = construct.cluster_tree(pts, cfg["m"])
+        bmin, bmax = construct.node_boxes(pts[perm], lo, q)
+        construct.dual_traversal(bmin, bmax, q, cfg["eta"])
+        times.append(time.perf_counter() - t)
+    sec = statistics.median(times)
+    val = round(nb / sec, 1)
+    print(json.dumps({"impl": "reference", "metric": "H^2 construction on the GPU (points/s), Sec. 4.6", "value": val,
+                      "unit": "points/s", "n_gpus": 1, "steps": len(times), "warmup": 0,
+                      "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": WORKLOADS[args.workload], "sample_n": nb},
+                      "cpu_baseline": {"value": val, "unit": "points/s", "cores": 1, "kind": "oracle",
+                                       "sample": f"structure of {nb} points of the family ({len(times)} runs)"},
+                      "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+def build_main(h2, args, dev, world, rank):
+    """--workload build_2d / build_3d: the construction on the GPU (h2_build) as the main line, timed over
+    a few builds (CUDA events inside the library), with the host generator's time as context."""
+    import torch
+
+    name, values = BUILD[args.workload]
+    cfg = dict(h2gen.CONFIGS[name])
+    t0 = time.perf_counter()
+    A = h2gen.generate(**cfg, values=False)
+    host_s = time.perf_counter() - t0
+    pts = h2gen.uniform(A.seed, (A.n, A.dim))
+    steps, warm = max(1, min(args.steps, 5)), max(1, min(args.warmup, 3))
+    for _ in range(warm):
+        h2.Built(pts, m=A.m, p=A.p, eta=A.eta, kernel=A.kernel, ell=A.ell, values=values).close()
+    times = []
+    with ClockSampler(dev.index) as clk:
+        for _ in range(steps):
+            B = h2.Built(pts, m=A.m, p=A.p, eta=A.eta, kernel=A.kernel, ell=A.ell, values=values)
+            times.append(B.times())
+            same = np.array_equal(B.read("S_colidx"), A.S_colidx) and np.array_equal(B.read("perm"), A.perm)
+            B.close()
+    ms = {k: statistics.median(t[k] for t in times) for k in times[0]}
+    total = sum(ms.values())
+    out = {"metric": "H^2 construction on the GPU (points/s), Sec. 4.6", "value": round(A.n / (total * 1e-3), 1),
+           "unit": "points/s", "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": round(total, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.workload], "n": A.n, "nS": A.nS, "nD": A.nD, "values": list(values),
+                      "parallelism": "1 GPU"},
+           "phase_ms": {k: round(v, 3) for k, v in ms.items()}, "structure_equals_generator": bool(same),
+           "host_generator_structure_s": round(host_s, 2), "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def reference_compress(args):
@@ -482,6 +551,8 @@ def main():
         return batch_main(h2, args, dev, dist, world, rank, hbm, peak_kind)
     if args.workload in COMPRESS:
         return compress_main(h2, args, dev, world, rank)
+    if args.workload in BUILD:
+        return build_main(h2, args, dev, world, rank)
     if args.workload in LARGE:
         return large_main(h2, args, cfg, dev, dist, world, rank, LARGE[args.workload])
     A = h2gen.generate(**cfg)
@@ -1007,6 +1078,8 @@ def reference_arm(args, cfg, world):
         return reference_batch(args, world)
     if args.workload in COMPRESS:
         return reference_compress(args)
+    if args.workload in BUILD:
+        return reference_build(args)
     if args.workload in LARGE:
         print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle needs the stored coupling values "
                           "(126 GB at n=2^20, 960 GB at n=2^22) that this workload never makes (it evaluates them "
