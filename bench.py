@@ -37,6 +37,8 @@ WORKLOADS = {
     "2d_n256k": "2D exp(-r/0.1) covariance H^2 matvec, n=2^18 uniform points, m=64, k=16, eta=0.9, FP64",
     "3d_n512k": "3D exp(-r/0.2) covariance H^2 matvec, n=2^19 uniform points in the unit cube, m=64, k=64 (4x4x4 Chebyshev), "
                 "eta=0.9, FP64",
+    "3d_n64k": "3D exp(-r/0.2) covariance H^2 matvec, n=2^16 uniform points in the unit cube, m=64, k=64 (4x4x4 Chebyshev), "
+               "eta=0.9, FP64",
     "3d_n1M_kc": "3D exp(-r/0.2) covariance H^2 matvec, n=2^20 uniform points in the unit cube, m=64, k=64 (4x4x4 "
                  "Chebyshev), eta=0.9, int16 + per-block f32 scale (S none: evaluated from the kernel), f32 bases",
     "3d_n4M_gen": "3D Matern-3/2 (length 0.1) covariance H^2 matvec, n=2^22 uniform points in the unit cube, m=64, "

@@ -226,6 +226,8 @@ CONFIGS = {
     "3d_n1M": dict(dim=3, n=1 << 20, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=3),
     # the same 3D workload at n=2^19 (its FP64 arrays, about 91 GB, fit the host memory of one GPU node)
     "3d_n512k": dict(dim=3, n=1 << 19, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=3),
+    # the same 3D workload at n=2^16 (1.6 GB of 16-bit coupling codes, far larger than L2): the 3D profiling case
+    "3d_n64k": dict(dim=3, n=1 << 16, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=6),
     # 3D, n=2^22, Matern-3/2 length 0.1, m=64, k=64, eta=0.7
     "3d_n4M": dict(dim=3, n=1 << 22, m=64, p=4, eta=0.7, kernel="matern32", ell=0.1, seed=5),
 }

@@ -204,7 +204,9 @@ h2_status h2_create_generated(const h2_desc* d, const h2_coupling_kernel* kc, co
  * fp16 or bf16 codes, 16-bit bases, k a multiple of 16 (at most 64) and every
  * leaf of 64 points, a pass of 8 or more vectors runs the dense blocks on the
  * tensor cores (vector operands split into two 16-bit parts, so the result
- * keeps the FP32 accumulation accuracy of the other path).
+ * keeps the FP32 accumulation accuracy of the other path). With fp16 or bf16
+ * codes and k = 64, such a pass also runs the coupling blocks (Eq. 3) on the
+ * tensor cores, whatever the leaves and bases.
  * Errors: H2_ERR_INVALID (NULL, nv < 1, ld < n), H2_ERR_CUDA (launch failed).
  */
 h2_status h2_matvec(h2_handle h, int32_t nv, const double* x, int64_t ldx, double* y, int64_t ldy, void* stream);
@@ -388,8 +390,11 @@ h2_status h2_batch_matvec(h2_batch b, const int32_t* nv, const double* const* x,
  *   coupling row chunks:    about 64, 128 or 256 coupling blocks per warp
  *   tree jobs:              subtrees of 16, 32 or 64 leaves per CTA
  * (one warm-up and two timed batched products each, arguments as for
- * h2_batch_matvec). chosen[0] consumer warps, chosen[1] chunk size, chosen[2]
- * leaves per tree CTA. Synchronizes `stream`.
+ * h2_batch_matvec), then the split of the dense work items over the CTAs:
+ * each leaf row weighed by its bytes times (1 + beta nv/16), nv its member's
+ * vectors per pass, beta in {0, 1, 2, 4} (the fastest kept). chosen[0]
+ * consumer warps, chosen[1] chunk size, chosen[2] leaves per tree CTA.
+ * Synchronizes `stream`.
  */
 h2_status h2_batch_tune(h2_batch b, const int32_t* nv, const double* const* x, const int64_t* ldx,
                         double* const* y, const int64_t* ldy, void* stream, int32_t chosen[3]);

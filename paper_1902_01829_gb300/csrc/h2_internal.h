@@ -72,7 +72,8 @@ struct MixedLaunch {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
-// the tensor-core dense phase of one pass (one matrix, panel layout, fp16 / bf16 codes)
+// a tensor-core phase of one pass (one matrix, panel layout, fp16 / bf16 codes): the dense phase with
+// the leaf expansion, or (coupling) the coupling blocks of every level, yhat_i = sum_j S_ij xhat_j
 struct TcCall {
   const h2::StreamItem* items = nullptr;
   const int* cta_begin = nullptr;
@@ -93,6 +94,18 @@ struct TcCall {
   int nv = 0;
   int* err = nullptr;
   long long budget = kWaitBudget;
+  // coupling: y is the FP32 yhat ([node][v][kp], zeroed first), the vectors come from xhat, the
+  // per-vector scales cover smax |xhat| over `nodes` nodes, and the blocks have unpadded panels
+  int coupling = 0;
+  const float* xhat = nullptr;
+  int64_t nodes = 0;
+  float smax = 0.f;
+};
+
+// the tensor-core phases of one pass (either may be absent)
+struct TcPass {
+  const TcCall* dense = nullptr;
+  const TcCall* coupling = nullptr;
 };
 
 // device copy of the precision form (per-block scaled 16-bit storage, FP32 arithmetic)
@@ -126,6 +139,10 @@ struct MixedData {
   float4* kf_clo = nullptr;      // and their low parts
   float4* kf_off = nullptr;      // [node][k] offsets of the interpolation points from the centre
   int4* tc_brec = nullptr;       // and the builders' records of those items
+  bool spanel = false;           // coupling codes in the panel layout, unpadded (fp16 / bf16, k = 64)
+  float smax = 0.f;              // largest coupling block scale
+  ItemList tc_sitems;            // the coupling phase's tensor-core items (spanel) and their records
+  int4* tc_sbrec = nullptr;
   void* rjobs = nullptr;         // h2::RowJob per leaf row (matrix index 0)
   std::vector<unsigned char> rjobs_host;  // the same, kept for batches
   // the table-driven kernels' tables for this matrix alone (a batch of one)
@@ -251,7 +268,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d);
 h2_status validate_desc(const h2_desc* d, bool s_values, bool d_values, int64_t* nS, int64_t* nD, int64_t* nDval,
                         int* m_max);
 // one product pass; buckets: bit b set when some matrix has a vector count in bucket b
-h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc = nullptr);
+h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcPass* tc = nullptr);
 // precision form: use coupling chunk target option `chunk_opt`, `cw` dense consumer warps and
 // tree subtrees at level (default level - tree_opt)
 h2_status mixed_configure(h2_matrix_s* h, int chunk_opt, int cw, int tree_opt);
@@ -278,4 +295,9 @@ struct h2_batch_s {
   std::vector<void*> allocs;
   cudaStream_t side = nullptr;  // the tree phases beside the dense phase
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the dense items' split over the CTAs (h2_batch_tune weighs each row by its member's vector count)
+  std::vector<h2::StreamItem> items_host;
+  std::vector<int64_t> row_bytes, row_item0;
+  std::vector<int32_t> row_mat;
+  int* cta_begin_dev = nullptr;
 };

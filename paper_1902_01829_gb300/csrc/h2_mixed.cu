@@ -20,7 +20,7 @@
 namespace h2i {
 
 template <int F>
-h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc);
+h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcPass* tc);
 
 }  // namespace h2i
 
@@ -153,6 +153,7 @@ h2::MatDesc fill_desc(const h2_matrix_s* h, int tree_L) {
   D.kf_off = M.kf_off;
   D.kf_inv_ell = h->kf_inv_ell;
   D.kf_kind = h->kf_kind;
+  D.spanel = M.spanel ? 1 : 0;
   D.rjobs = static_cast<const h2::RowJob*>(M.rjobs);
   D.blk = static_cast<const h2::MixedBlock*>(M.dblk);
   return D;
@@ -372,6 +373,74 @@ h2_status mixed_configure(h2_matrix_s* h, int chunk_opt, int cw, int tree_opt) {
   return H2_OK;
 }
 
+// The coupling phase's tensor-core items (k = 64, codes in the unpadded panel layout): the blocks of
+// each coupling row, up to four per item (two M = 128 pairs), in row order; the builders' records
+// name each block's column node (xhat offset j kp, second vector source), K = 64 and its scale.
+// Rows are weighed by bytes and MMAs, as the dense phase's.
+h2_status build_coupling_items(h2_matrix_s* h, const h2_desc* d, const std::vector<float>& sc) {
+  MixedData& M = h->mx;
+  const int64_t nodes = h->n_nodes, bbytes = 64 * 64 * 2;
+  const int32_t* Srow = d->S_rowptr;
+  const int32_t* Scol = d->S_colidx;
+  std::vector<h2::StreamItem> items;
+  std::vector<int32_t> brec;
+  std::vector<int64_t> row_bytes((size_t)nodes, 0), row_item0((size_t)nodes + 1, 0);
+  constexpr int kBlocks = 4;
+  int kp[h2::kTcMaxBlocks], bo[h2::kTcMaxBlocks], pm = 0, sm = 0;
+  for (int u = 0; u < h2::kTcMaxBlocks; u++) kp[u] = 64;
+  for (int64_t i = 0; i < nodes; i++) {
+    row_item0[(size_t)i] = (int64_t)items.size();
+    const int64_t g0 = Srow[i], g1 = Srow[i + 1];
+    for (int64_t g = g0; g < g1; g += kBlocks) {
+      const int nb = (int)std::min<int64_t>(kBlocks, g1 - g);
+      if (h2::tc_layout(nb, kp, bo, &pm, &sm) > h2::kTcStageB || nb * bbytes > h2::kTcStageMat)
+        return h2_fail(H2_ERR_INVALID, "internal: coupling item exceeds a tensor-core stage");
+      h2::StreamItem it{};
+      it.m_off = g * bbytes;
+      it.m_bytes = (int)(nb * bbytes);
+      it.shape = 64u | ((unsigned)nb << 8);
+      it.v_off = g;
+      it.row = (int)i;
+      it.flags = (g + nb == g1 ? h2::kItemFlagLast : 0) | (pm << h2::kTcPairShift);
+      items.push_back(it);
+      int32_t r[h2::kTcRecInts] = {0};
+      r[0] = nb | (pm << 8);
+      for (int u = 0; u < nb; u++) {
+        const int64_t j = Scol[g + u];
+        if (j < 0 || j >= nodes || j * 64 > INT32_MAX)
+          return h2_fail(H2_ERR_UNSUPPORTED, "coupling column %lld exceeds the tensor-core records", (long long)j);
+        r[1 + 3 * u] = (int32_t)(j * 64);
+        r[2 + 3 * u] = 64 | (1 << 16);
+        std::memcpy(&r[3 + 3 * u], &sc[(size_t)(g + u)], sizeof(float));
+      }
+      brec.insert(brec.end(), r, r + h2::kTcRecInts);
+      int64_t mmas = 0;
+      for (int u = 0; u < nb; u++)
+        if (((pm | sm) >> u) & 1) mmas += 4;
+      row_bytes[(size_t)i] += nb * bbytes + 4096 * mmas + 512;
+    }
+  }
+  row_item0[(size_t)nodes] = (int64_t)items.size();
+  if (items.empty()) return h2_fail(H2_ERR_INVALID, "internal: coupling blocks without coupling items");
+  if (items.size() > (size_t)INT32_MAX) return h2_fail(H2_ERR_UNSUPPORTED, "too many coupling items");
+  const std::vector<int> begin = balance(row_bytes, row_item0, h->grid);
+  for (size_t c = 0; c + 1 < begin.size(); c++)
+    if (begin[c] > begin[c + 1]) return h2_fail(H2_ERR_INVALID, "internal: item ranges not monotone");
+  for (const h2::StreamItem& it : items) {  // audit, as the kernel reads the items
+    const int nb = (int)((it.shape >> 8) & 0xFF);
+    const bool ok = nb >= 1 && nb <= kBlocks && it.m_off % 16 == 0 && it.m_bytes == nb * bbytes &&
+                    it.m_off + it.m_bytes <= h->nS * bbytes && it.row >= 0 && it.row < nodes;
+    if (!ok) return h2_fail(H2_ERR_INVALID, "internal: coupling tensor-core item fails the layout audit");
+  }
+  h2_status st;
+  if ((st = upload(h, &M.tc_sbrec, reinterpret_cast<const int4*>(brec.data()), (int64_t)items.size() * (h2::kTcRecInts / 4))) != H2_OK)
+    return st;
+  if ((st = upload(h, &M.tc_sitems.items, items.data(), (int64_t)items.size())) != H2_OK) return st;
+  if ((st = upload(h, &M.tc_sitems.cta_begin, begin.data(), (int64_t)begin.size())) != H2_OK) return st;
+  M.tc_sitems.count = (int64_t)items.size();
+  return H2_OK;
+}
+
 h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   MixedData& M = h->mx;
   const int form = form_of(h->storage);
@@ -492,6 +561,26 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
     std::vector<float> sc((size_t)std::max<int64_t>(1, h->nS), 0.f);
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t b = 0; b < h->nS; b++) sc[b] = quantize(d->S_val + b * kk, kk, form, codes.data() + b * kk8);
+    // fp16 / bf16 at k = 64: the codes in the panel layout without the pad (the tensor cores' MN-major
+    // operand layout: rows 8m .. 8m + 7 of column c at codes 512 m + 8 c), so that passes of 8 or
+    // more vectors run the coupling phase on the tensor cores
+    M.spanel = form != h2::kFormInt16 && k == 64 && h->nS > 0;
+    if (M.spanel) {
+#pragma omp parallel
+      {
+        uint16_t tmp[4096];
+#pragma omp for schedule(static)
+        for (int64_t b = 0; b < h->nS; b++) {
+          uint16_t* blk = codes.data() + b * kk8;
+          for (int c = 0; c < 64; c++)
+            for (int m = 0; m < 8; m++)
+              for (int i = 0; i < 8; i++) tmp[512 * m + 8 * c + i] = blk[64 * c + 8 * m + i];
+          std::memcpy(blk, tmp, sizeof(tmp));
+        }
+      }
+      for (int64_t b = 0; b < h->nS; b++) M.smax = std::max(M.smax, sc[b]);
+      if ((st = build_coupling_items(h, d, sc)) != H2_OK) return st;
+    }
     if ((st = upload(h, &M.smat, codes.data(), h->nS * kk8)) != H2_OK) return st;
     if ((st = upload(h, &M.sscale, sc.data(), h->nS)) != H2_OK) return st;
   }
@@ -810,7 +899,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   CUDA_TRY(cudaMemset(M.xhat, 0, (size_t)(nodes * kPassVectors * M.kp4) * sizeof(float)));
   CUDA_TRY(cudaMemset(M.yhat, 0, (size_t)(nodes * kPassVectors * M.kp4) * sizeof(float)));
 
-  if (M.panel) {
+  if (M.panel || M.spanel) {  // the per-vector scales of the tensor-core phases
     if ((st = dalloc(h, &M.tc_vmax, 16)) != H2_OK) return st;
     if ((st = dalloc(h, &M.tc_vscale, 16)) != H2_OK) return st;
   }
@@ -840,7 +929,7 @@ h2_status mixed_build(h2_matrix_s* h, const h2_desc* d) {
   return mixed_configure(h, kDefaultChunkOpt, h->m_max <= 32 ? 2 * h2::kMixedCW : h2::kMixedCW, 0);
 }
 
-h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {
+h2_status mixed_launch(int storage, const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcPass* tc) {
   switch (form_of(storage)) {
     case h2::kFormFp16: return mixed_pass_form<h2::kFormFp16>(L, buckets, st, tc);
     case h2::kFormBf16: return mixed_pass_form<h2::kFormBf16>(L, buckets, st, tc);
@@ -861,8 +950,14 @@ h2_status mixed_pass(h2_matrix_s* h, int nv, const void* xv, int64_t ldx, void* 
   h2_status s = set_calls(static_cast<h2::MatDesc*>(L.mats), 1, &nv, &x, &ldx, &y, &ldy, st, xy32);
   if (s != H2_OK) return s;
   const MixedData& M = h->mx;
-  if (M.panel && nv >= kTcMinVectors && h->storage != H2_INT16_SCALED) {  // dense phase on the tensor cores
-    TcCall T;
+  const bool fp16 = h->storage == H2_FP16_SCALED;
+  const bool tc_ok = nv >= kTcMinVectors && h->storage != H2_INT16_SCALED;
+  TcCall T, TS;
+  TcPass P;
+  // set_calls, upsweep, coupling, downsweep (+ expansion), dense; the split of x when the dense phase
+  // runs beside the tree phases (passes of up to four vectors, not profiled)
+  int launches = 5;
+  if (M.panel && tc_ok) {  // dense phase on the tensor cores
     T.items = M.tc_items.items;
     T.cta_begin = M.tc_items.cta_begin;
     T.brec = M.tc_brec;
@@ -886,12 +981,37 @@ h2_status mixed_pass(h2_matrix_s* h, int nv, const void* xv, int64_t ldx, void* 
     T.nv = nv;
     T.err = h->err;
     T.budget = h->budget;
-    h->prof.launches += h->storage == H2_FP16_SCALED ? 7 : 6;  // set_calls, 3 tree, (vmax,) vscale, tc
-    return mixed_launch(h->storage, L, 1u << bucket_of(nv), st, &T);
+    P.dense = &T;
+    launches += fp16 ? 2 : 1;  // (vmax,) vscale before the tensor-core kernel
   }
-  // set_calls, upsweep, coupling, downsweep (+ expansion), dense; the split of x when the dense phase
-  // runs beside the tree phases (passes of up to four vectors, not profiled)
-  h->prof.launches += 5 + (bucket_of(nv) <= 2 && !h->prof.on ? 1 : 0);
+  if (M.spanel && tc_ok) {  // coupling phase on the tensor cores
+    TS.items = M.tc_sitems.items;
+    TS.cta_begin = M.tc_sitems.cta_begin;
+    TS.brec = M.tc_sbrec;
+    TS.dmat = M.smat;
+    TS.vmax = M.tc_vmax;
+    TS.vscale = M.tc_vscale;
+    TS.k = h->k;
+    TS.kp = M.kp4;
+    TS.grid = h->grid;
+    TS.y = reinterpret_cast<double*>(M.yhat);
+    TS.ldy = M.kp4;
+    TS.y32 = 1;
+    TS.nv = nv;
+    TS.err = h->err;
+    TS.budget = h->budget;
+    TS.coupling = 1;
+    TS.xhat = M.xhat;
+    TS.nodes = h->n_nodes;
+    TS.smax = M.smax;
+    P.coupling = &TS;
+    launches += fp16 ? 2 : 1;
+  }
+  if (P.dense || P.coupling) {
+    h->prof.launches += launches;
+    return mixed_launch(h->storage, L, 1u << bucket_of(nv), st, &P);
+  }
+  h->prof.launches += launches + (bucket_of(nv) <= 2 && !h->prof.on ? 1 : 0);
   return mixed_launch(h->storage, L, 1u << bucket_of(nv), st);
 }
 
@@ -1015,6 +1135,7 @@ h2_status batch_build(h2_batch_s* b) {
     for (size_t r = 0; r + 1 < M.row_item0.size(); r++) {
       row_item0.push_back(item0 + M.row_item0[r]);
       row_bytes.push_back(M.row_bytes[r]);
+      b->row_mat.push_back((int32_t)i);
     }
     blk0 += M.nblk;
   }
@@ -1033,6 +1154,10 @@ h2_status batch_build(h2_batch_s* b) {
   if ((st = balloc(b, &di, (int64_t)items.size(), items.data())) != H2_OK) return st;
   int* db = nullptr;
   if ((st = balloc(b, &db, (int64_t)begin.size(), begin.data())) != H2_OK) return st;
+  b->cta_begin_dev = db;
+  b->row_bytes = row_bytes;
+  b->row_item0 = row_item0;
+  b->items_host = items;
   h2::MixedBlock* blk = nullptr;
   if ((st = balloc(b, &blk, blk0)) != H2_OK) return st;
   for (int64_t i = 0, o = 0; i < count; o += b->hs[(size_t)i]->mx.nblk, i++)
@@ -1126,6 +1251,29 @@ h2_status h2_batch_create(const h2_handle* hs, int32_t count, h2_batch* out) {
   return H2_OK;
 }
 
+namespace {
+
+// The dense items' split over the CTAs for the vector counts nv (nullptr: bytes alone): row r of
+// member i weighs bytes_r (1 + beta nv_i / 16), since a row's arithmetic grows with its vectors
+// while its bytes do not; the split is uploaded after `stream` has drained (no product reads it).
+h2_status batch_rebalance(h2_batch b, const int32_t* nv, float beta, cudaStream_t stream) {
+  std::vector<int64_t> w(b->row_bytes.size());
+  for (size_t r = 0; r < w.size(); r++) {
+    const int v = nv ? std::max(0, std::min(nv[b->row_mat[r]], kPassVectors)) : 0;
+    w[r] = (int64_t)((double)b->row_bytes[r] * (1.0 + beta * v / kPassVectors));
+  }
+  const std::vector<int> begin = balance(w, b->row_item0, b->launch.grid);
+  h2_status st = audit_producer_batches(b->items_host, begin);
+  if (st != H2_OK) return st;
+  for (size_t c = 0; c + 1 < begin.size(); c++)
+    if (begin[c] > begin[c + 1]) return h2_fail(H2_ERR_INVALID, "internal: item ranges not monotone");
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  CUDA_TRY(cudaMemcpy(b->cta_begin_dev, begin.data(), begin.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return H2_OK;
+}
+
+}  // namespace
+
 h2_status h2_batch_matvec(h2_batch b, const int32_t* nv, const double* const* x, const int64_t* ldx, double* const* y,
                           const int64_t* ldy, void* stream) {
   if (!b) return h2_fail(H2_ERR_INVALID, "NULL batch");
@@ -1211,6 +1359,33 @@ h2_status h2_batch_tune(h2_batch b, const int32_t* nv, const double* const* x, c
   cudaEventDestroy(e1);
   if (s != H2_OK) return s;
   if ((s = batch_configure(b, best_c, best_t, best_cw)) != H2_OK) return s;
+  // then the dense items' split over the CTAs: rows weighed by bytes, or also by their vector counts
+  if (nv) {
+    const float betas[4] = {0.f, 1.f, 2.f, 4.f};
+    float best_b = 0.f;
+    best = 3.4e38f;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    for (int i = 0; i < 4 && s == H2_OK; i++) {
+      if ((s = batch_rebalance(b, nv, betas[i], st)) != H2_OK) break;
+      if ((s = h2_batch_matvec(b, nv, x, ldx, y, ldy, stream)) != H2_OK) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 2 && s == H2_OK; r++) s = h2_batch_matvec(b, nv, x, ldx, y, ldy, stream);
+      cudaEventRecord(e1, st);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess) s = h2_fail(H2_ERR_CUDA, "timing a work split: %s", cudaGetErrorString(ce));
+      else if (ms < best) {
+        best = ms;
+        best_b = betas[i];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != H2_OK) return s;
+    if ((s = batch_rebalance(b, nv, best_b, st)) != H2_OK) return s;
+  }
   chosen[0] = best_cw;
   chosen[1] = kChunkOpts[best_c];
   chosen[2] = 1 << kTreeOpts[best_t];

@@ -2,5 +2,5 @@
 #include "h2_mixed_launch.cuh"
 
 namespace h2i {
-template h2_status mixed_pass_form<h2::kFormFp16>(const MixedLaunch&, unsigned, cudaStream_t, const TcCall*);
+template h2_status mixed_pass_form<h2::kFormFp16>(const MixedLaunch&, unsigned, cudaStream_t, const TcPass*);
 }  // namespace h2i

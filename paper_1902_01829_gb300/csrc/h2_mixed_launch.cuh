@@ -115,7 +115,8 @@ h2_status dense_launch(const MixedLaunch& L, cudaStream_t st) {
   return dense_launch_cw<F, NVB, h2::kMixedCW>(L, st);
 }
 
-// dense phase on the tensor cores: per-vector scales, then the persistent tcgen05 kernel
+// a phase on the tensor cores (the dense phase, or the coupling phase): per-vector scales, then the
+// persistent tcgen05 kernel
 template <int F>
 h2_status tc_launch(const TcCall& T, cudaStream_t st) {
   using namespace h2;
@@ -126,31 +127,45 @@ h2_status tc_launch(const TcCall& T, cudaStream_t st) {
     if (attr == cudaErrorNotReady)
       attr = cudaFuncSetAttribute(k_dense_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (attr != cudaSuccess) return h2_fail(H2_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(attr));
+    if (!T.items || !T.cta_begin || !T.brec || !T.dmat || !T.vmax || !T.vscale || !T.y || T.nv < 1 || T.nv > kTcVec ||
+        (T.coupling ? !T.xhat : (!T.x4 || !T.yhat || !T.xp4_off)))
+      return h2_fail(H2_ERR_INVALID, "internal: tensor-core phase without its buffers");
     const bool fp16 = F == kFormFp16;
     if (fp16) {
       cudaError_t e = cudaMemsetAsync(T.vmax, 0, kTcVec * sizeof(unsigned), st);
       if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-      // 32 warps per SM (152 SMs), each over a stride of leaves for one vector
-      const long long warps = (long long)T.nv * std::max<long long>(1, std::min<long long>(T.leaves, 152 * 32 / T.nv));
-      k_tc_vmax<F><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
-          T.x4, T.yhat, reinterpret_cast<const long long*>(T.xp4_off), T.leaves, T.leaf0, T.nv, T.kp, T.k, T.dmax,
-          T.umax, warps, T.vmax);
+      // 32 warps per SM (152 SMs), each over a stride of leaves (nodes) for one vector
+      const long long units = T.coupling ? T.nodes : T.leaves;
+      const long long warps = (long long)T.nv * std::max<long long>(1, std::min<long long>(units, 152 * 32 / T.nv));
+      if (T.coupling)
+        k_tc_vmax_nodes<F><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(T.xhat, T.nodes, T.nv, T.kp, T.k,
+                                                                             T.smax, warps, T.vmax);
+      else
+        k_tc_vmax<F><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+            T.x4, T.yhat, reinterpret_cast<const long long*>(T.xp4_off), T.leaves, T.leaf0, T.nv, T.kp, T.k, T.dmax,
+            T.umax, warps, T.vmax);
     }
     k_tc_vscale<F><<<1, 32, 0, st>>>(T.vmax, T.vscale, fp16 ? 1 : 0);
+    if (T.coupling) {  // rows without coupling blocks hold zeros; the others are assigned
+      cudaError_t e = cudaMemsetAsync(T.y, 0, (size_t)(T.nodes * T.nv * T.kp) * sizeof(float), st);
+      if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
     TcParams P{};
     P.items = T.items;
     P.cta_begin = T.cta_begin;
     P.blk = static_cast<const MixedBlock*>(T.blk);
     P.dmat = static_cast<const char*>(T.dmat);
     P.x4 = T.x4;
-    P.yhat = T.yhat;
+    P.yhat = T.coupling ? T.xhat : T.yhat;  // the builders' second vector source
     P.vscale = T.vscale;
     P.brec = T.brec;
     P.y = T.y;
     P.ldy = T.ldy;
+    P.rowmul = T.coupling ? (long long)T.nv * T.kp : 1;
     P.nv = T.nv;
     P.y32 = T.y32;
     P.kp = T.kp;
+    P.ppad = T.coupling ? 0 : kPanelPad;
     P.err = T.err;
     P.budget = T.budget;
     k_dense_tc<F><<<T.grid, kTcThreads, kTcSmem, st>>>(P);
@@ -167,7 +182,9 @@ h2_status tc_launch(const TcCall& T, cudaStream_t st) {
 // copies x itself, the expansion assigns y and the dense phase adds after it. The tensor-core
 // pass fuses the expansion into its dense phase.
 template <int F, int FB, int RPL>
-h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {
+h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcPass* tp) {
+  const TcCall* tc = tp ? tp->dense : nullptr;      // dense phase and expansion on the tensor cores
+  const TcCall* tcs = tp ? tp->coupling : nullptr;  // coupling phase on the tensor cores
   cudaError_t me = cudaSuccess;
   auto mk = [&]() {
     if (L.prof && me == cudaSuccess) me = mark(L.prof, st);
@@ -183,7 +200,7 @@ h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st, 
   };
   // passes of more than four vectors keep the phases in order: their tree kernels' shared memory does
   // not fit beside the dense stream's, and the dense phase is bound by arithmetic there (measured)
-  const bool overlap = !tc && top <= 2 && !(L.prof && L.prof->on) && L.side && L.ev_fork && L.ev_join;
+  const bool overlap = !tc && !tcs && top <= 2 && !(L.prof && L.prof->on) && L.side && L.ev_fork && L.ev_join;
   h2_status s = H2_OK;
   if (overlap) {
     const long long swarps = std::min<long long>(L.nrjobs, (long long)L.grid * 64);
@@ -201,8 +218,12 @@ h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st, 
     if (e != cudaSuccess) return h2_fail(H2_ERR_CUDA, "join from the side stream: %s", cudaGetErrorString(e));
   } else {
     for (int phase = 0; phase < 3; phase++) {
-      for (int b = 0; b < kBuckets; b++)
-        if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, st, true, tc ? 0 : 2);
+      if (phase == 1 && tcs) {
+        if ((s = tc_launch<F>(*tcs, st)) != H2_OK) return s;
+      } else {
+        for (int b = 0; b < kBuckets; b++)
+          if ((buckets >> b) & 1u) bucket_dispatch<F, FB, RPL>(L, phase, b, st, true, tc ? 0 : 2);
+      }
       mk();
     }
     if ((s = dense(st)) != H2_OK) return s;
@@ -216,7 +237,7 @@ h2_status mixed_pass_t(const MixedLaunch& L, unsigned buckets, cudaStream_t st, 
 
 // FB: format of the bases and transfers (the storage format, or FP32 entries)
 template <int F>
-h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcCall* tc) {
+h2_status mixed_pass_form(const MixedLaunch& L, unsigned buckets, cudaStream_t st, const TcPass* tc) {
   if (L.bases_fp32)
     return L.k > 32 ? mixed_pass_t<F, h2::kFormF32, 2>(L, buckets, st, tc)
                     : mixed_pass_t<F, h2::kFormF32, 1>(L, buckets, st, tc);

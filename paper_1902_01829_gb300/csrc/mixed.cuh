@@ -110,7 +110,8 @@ struct MatDesc {
   float* yhat;
   int* ticket;
   long long kk8, n_nodes;
-  int k, kp, LR, q, L, pad0;
+  int k, kp, LR, q, L;
+  int spanel;            // k = 64: coupling codes in the panel layout (8 panels of 8 rows, 1024 bytes apart)
   // coupling blocks from the kernel (k_coupling_kf): node centres as FP32 high and low parts,
   // the interpolation points' offsets from the centre, 1 / ell and the kernel kind
   const float4* kf_chi;
@@ -564,7 +565,8 @@ __device__ __forceinline__ ChunkRows chunk_rows(const int32_t* __restrict__ Srow
 }
 
 // k = 16, 32 or 64. Lane l reads 16 bytes, 8 consecutive codes (rows 8m ..
-// 8m + 7, m = l % RG, RG = k / 8) of a column c = l / RG + (32 / RG) t, so a
+// 8m + 7, m = l % RG, RG = k / 8) of a column c = l / RG + (32 / RG) t (16
+// contiguous bytes both column-major and in the panel layout), so a
 // 16 x 16 block is one 512-byte load of the warp; a slot is OPS such octets
 // per lane (a quarter of a 64 x 64 block, a whole block for k <= 32). The
 // block scale multiplies the vector entry (S_ij x_j = Q (sigma x_j)). The warp
@@ -600,6 +602,9 @@ __global__ void __launch_bounds__(128) k_coupling_m(const MatDesc* __restrict__ 
   const ChunkRows cr = chunk_rows(D.Srow, yhat, row0, rows, nv, kp, lane, vbase, min(NVW, nv - vbase));
   if (!cr.nonempty) return;
   const int m = lane % RG, cl = lane / RG;
+  // octet (m, c) of a block: 8 m + K c codes (column-major), or 512 m + 8 c (panel layout, K = 64)
+  const bool spanel = K == 64 && D.spanel != 0;
+  const int om = spanel ? 512 * m : 8 * m, oc = spanel ? 8 : K;
   float acc[8][NVW];
 #pragma unroll
   for (int r = 0; r < 8; r++)
@@ -642,11 +647,11 @@ __global__ void __launch_bounds__(128) k_coupling_m(const MatDesc* __restrict__ 
         const int32_t gb = b0 + slot / SPB;
         const int tq = slot % SPB;
         const float* X = xhat + ((int64_t)col[u] * nv + vbase) * kp;
-        const uint16_t* blk = S + (int64_t)gb * kk8 + 8 * m;
+        const uint16_t* blk = S + (int64_t)gb * kk8 + om;
 #pragma unroll
         for (int o = 0; o < OPS; o++) {
           const int c = cl + CS * (tq * OPS + o);
-          a[u][o] = __ldg(reinterpret_cast<const uint4*>(blk + K * c));
+          a[u][o] = __ldg(reinterpret_cast<const uint4*>(blk + oc * c));
 #pragma unroll
           for (int v = 0; v < NVW; v++) xv[u][o][v] = (vbase + v < nv) ? __ldg(X + v * kp + c) : 0.f;
         }

@@ -25,6 +25,12 @@
 // alternate between rows); four epilogue warps read them back (tcgen05.ld), add the
 // two halves and the two parts of each vector, divide by s_v and write y in FP64.
 //
+// The coupling phase (Eq. 3) at k = 64 runs the same kernel: a work item is up to four
+// coupling blocks S_ij of one row i (any level; their codes in the panel layout without
+// the pad, P.ppad = 0), the builders read xhat_j ([node][v][kp]) through the second vector
+// source, and the epilogue assigns the row's yhat_i at row i * P.rowmul (P.rowmul = nv kp,
+// FP32); the leaf expansion has no part in it.
+//
 // Warp roles (320 threads, one CTA per SM, persistent over byte-balanced work items
 // of their own, up to four 64 x 64 blocks and U): 0 producer (TMA of the codes and a
 // header for the MMA thread), 1 MMA issuer (one thread), 2-5 B-tile builders (reading
@@ -100,7 +106,9 @@ struct TcParams {
   const int4* brec;     // builder records, kTcRecInts / 4 per item
   double* y;            // FP32 when y32
   long long ldy;
-  int nv, kp, y32, pad0;
+  long long rowmul;     // output row r of an item starts at row * rowmul (1: y; nv kp: the coupling's yhat)
+  int nv, kp, y32;
+  int ppad;             // bytes between a block's panels beyond 16 K (kPanelPad; 0 for coupling blocks)
   int* err;
   long long budget;
 };
@@ -241,8 +249,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
             if (b < nb) {
               hd[4 + 3 * b] = aoff;
               hd[5 + 3 * b] = kp[b];
-              hd[6 + 3 * b] = 16 * kp[b] + kPanelPad;  // panel stride
-              aoff += 8 * (16 * kp[b] + kPanelPad);
+              hd[6 + 3 * b] = 16 * kp[b] + P.ppad;  // panel stride
+              aoff += 8 * (16 * kp[b] + P.ppad);
             }
           }
           hd[0] = nb;
@@ -502,7 +510,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(TcParams P) {
           for (int v = 0; v < kTcVec; v++) sum[v] += xr[v];
           __syncwarp();
           if (lane == 0) mbar_arrive(accempty + b);
-          const long long yo = row_off + 32 * q + lane;
+          const long long yo = (long long)row_off * P.rowmul + 32 * q + lane;
 #pragma unroll
           for (int v = 0; v < kTcVec; v++)
             if (v < P.nv) {
@@ -545,6 +553,25 @@ __global__ void k_tc_vmax(const float* __restrict__ x4, const float* __restrict_
   }
   for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
   if (lane == 0) atomicMax(vmax + v, __float_as_uint(m));  // non-negative floats order as their bits
+}
+
+// The same maxima for the coupling phase: smax |xhat_v| over the first k entries of every node's
+// xhat ([node][v][kp]); warp w takes vector w % nv and nodes w / nv, w / nv + warps / nv, ...
+template <int F>
+__global__ void k_tc_vmax_nodes(const float* __restrict__ xhat, long long nodes, int nv, int kp, int k, float smax,
+                                long long warps, unsigned* __restrict__ vmax) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= warps || nv < 1) return;
+  const int v = (int)(w % nv);
+  const long long step = warps / nv;
+  float m = 0.f;
+  for (long long j = w / nv; j < nodes; j += step) {
+    const float* xs = xhat + (j * nv + v) * (long long)kp;
+    for (int r = lane; r < k; r += 32) m = fmaxf(m, fabsf(xs[r]) * smax);
+  }
+  for (int off = 16; off; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, off));
+  if (lane == 0) atomicMax(vmax + v, __float_as_uint(m));
 }
 
 template <int F>

@@ -86,6 +86,25 @@ def test_batch_matches_quantized_oracle(h2, members, form, bases_fp32):
         M.close()
 
 
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+def test_batch_of_k64_members_with_panel_coupling(h2, form):
+    """k = 64 members keep their coupling codes in the panel layout (the tensor-core operand layout);
+    the batch reads them on the CUDA cores, for every member's vector count."""
+    mats = [(h2gen.generate(dim=3, n=4096, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=4201), 16),
+            (h2gen.generate(dim=3, n=2500, m=64, p=4, eta=0.8, kernel="matern32", ell=0.2, seed=4202), 3)]
+    Ms = [h2.H2Matrix.from_generator(A, storage=form) for A, _ in mats]
+    B = h2.H2Batch(Ms)
+    xs_np = [h2gen.vectors(720 + i, A.n, nv) for i, (A, nv) in enumerate(mats)]
+    xs = [to_dev(x) for x in xs_np]
+    ys = [nan_like(A.n, nv) for A, nv in mats]
+    B.matvec(xs, ys)
+    B.check()
+    _check_members(mats, xs_np, ys, form, False)
+    B.close()
+    for M in Ms:
+        M.close()
+
+
 def test_batch_repeated_calls_and_new_buffers(h2, members):
     Ms = [h2.H2Matrix.from_generator(A, storage="fp16") for A, _ in members]
     B = h2.H2Batch(Ms)

@@ -142,15 +142,55 @@ def test_panel_layout_and_tensor_cores_2d(h2, panel2d, form, nv):
     check(oracle.rel_l2(out, ref), tol, ("panel 2d", form, nv))
 
 
+def launches_per_pass(nv, form, dense_tc, coupling_tc):
+    """Kernel launches of a profiled product: five per pass (set_calls, upsweep, coupling, downsweep,
+    dense) plus, for a pass of >= 8 vectors, the per-vector scale kernels of each phase on the tensor
+    cores (vmax for fp16, vscale)."""
+    extra = 2 if form == "fp16" else 1
+    passes = [min(16, nv - v0) for v0 in range(0, nv, 16)]
+    return sum(5 + (extra * (int(dense_tc) + int(coupling_tc)) if p >= 8 else 0) for p in passes)
+
+
 @pytest.mark.parametrize("form", ["fp16", "bf16"])
-@pytest.mark.parametrize("nv", [2, 16])
+@pytest.mark.parametrize("nv", [2, 16, 20])
 def test_panel_layout_and_tensor_cores_3d_k64(h2, form, nv):
+    """k = 64: the coupling blocks are stored in the panel layout; passes of >= 8 vectors run both the
+    coupling and the dense phase on the tensor cores, smaller passes read the same codes on the CUDA
+    cores (nv = 20: one pass of each)."""
     A = h2gen.generate(dim=3, n=8192, m=64, p=4, eta=0.9, kernel="exp", ell=0.2, seed=22)
     assert A.k == 64 and all(A.leaf_size(i) == 64 for i in range(A.leaves))
     x = h2gen.vectors(650 + nv, A.n, nv)
-    y = run(h2, A, form, x)
+    M = h2.H2Matrix.from_generator(A, storage=form)
+    M.profile(True)
+    y = M.matvec(to_dev(x))
+    M.check()
+    _, launches = M.profile_read()
+    assert launches == launches_per_pass(nv, form, True, True), launches
+    out = y.cpu().numpy()
+    M.close()
     tol = acc_tol(A) + (tc_split_tol(form) if nv >= 8 else 0.0)
-    check(oracle.rel_l2(y, oracle.matvec(A, x, **quant.dequantized_arrays(A, form))), tol, ("panel 3d", form, nv))
+    check(oracle.rel_l2(out, oracle.matvec(A, x, **quant.dequantized_arrays(A, form))), tol, ("panel 3d", form, nv))
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+@pytest.mark.parametrize("nv", [3, 16])
+def test_coupling_on_tensor_cores_without_dense_panels(h2, form, nv):
+    """k = 64 with ragged leaves and FP32 bases: the dense phase stays on the CUDA cores, the coupling
+    phase of a 16-vector pass runs on the tensor cores."""
+    A = h2gen.generate(dim=3, n=7001, m=64, p=4, eta=0.8, kernel="matern32", ell=0.2, seed=23)
+    assert A.k == 64 and any(A.leaf_size(i) != 64 for i in range(A.leaves))
+    x = h2gen.vectors(655 + nv, A.n, nv)
+    M = h2.H2Matrix.from_generator(A, storage=form, bases_fp32=True)
+    M.profile(True)
+    y = M.matvec(to_dev(x))
+    M.check()
+    _, launches = M.profile_read()
+    assert launches == launches_per_pass(nv, form, False, True), launches
+    out = y.cpu().numpy()
+    M.close()
+    tol = acc_tol(A) + (tc_split_tol(form) if nv >= 8 else 0.0)
+    check(oracle.rel_l2(out, oracle.matvec(A, x, **quant.dequantized_arrays(A, form, bases_fp32=True))), tol,
+          ("coupling tc 3d ragged", form, nv))
 
 
 def test_tensor_core_pass_scales_large_vectors(h2, panel2d):
