@@ -362,17 +362,25 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_upsweep_tree_m(const MatDe
   for (int64_t t = warp; t < ((int64_t)1 << T); t += kTreeWarpsM)
     project_leaf_m<F, RPL, NVB>(P, (sub << T) + t, lane, wbuf, convert != 0);
   __syncthreads();
+  constexpr int NVW = slice_vectors<NVB>();
   for (int lvl = P.q - 1; lvl >= P.L; lvl--) {
     const int64_t node0 = ((int64_t)1 << lvl) - 1 + (sub << (lvl - P.L));
-    for (int64_t t = warp; t < ((int64_t)1 << (lvl - P.L)); t += kTreeWarpsM)
-      up_node_m<F, RPL, NVB, false>(P, node0 + t, lane, wbuf, 0, P.nv);
+    const int nn = 1 << (lvl - P.L);
+    if (nn >= kTreeWarpsM || P.nv <= NVW) {  // a warp per node, all vectors
+      for (int t = warp; t < nn; t += kTreeWarpsM) up_node_m<F, RPL, NVB, false>(P, node0 + t, lane, wbuf, 0, P.nv);
+    } else {  // fewer nodes than warps: a warp per (node, slice of NVW vectors)
+      const int ns = (P.nv + NVW - 1) / NVW;
+      for (int u = warp; u < nn * ns; u += kTreeWarpsM) {
+        const int t = u % nn, v0 = (u / nn) * NVW;
+        up_node_m<F, RPL, NVW, false>(P, node0 + t, lane, wbuf, v0, min(NVW, P.nv - v0));
+      }
+    }
     __syncthreads();
   }
   __threadfence();
   __syncthreads();
   // climb while this CTA arrives second at the parent; every warp takes a slice of the vectors
   __shared__ int second;
-  constexpr int NVW = slice_vectors<NVB>();
   const int v0 = warp * NVW, nw = min(NVW, P.nv - v0);
   int64_t node = ((int64_t)1 << P.L) - 1 + sub;
   while (node > 0) {
@@ -507,19 +515,39 @@ __global__ void __launch_bounds__(kTreeWarpsM * 32) k_downsweep_tree_m(const Mat
   __syncthreads();
   for (int lvl = P.L + 1; lvl <= P.q; lvl++) {
     const int64_t node0 = ((int64_t)1 << lvl) - 1 + (sub << (lvl - P.L));
-    for (int64_t t = warp; t < ((int64_t)1 << (lvl - P.L)); t += kTreeWarpsM) {
-      const int64_t ch = node0 + t;
-      float acc[RPL][NVB];
+    const int nn = 1 << (lvl - P.L);
+    if (nn >= kTreeWarpsM || P.nv <= NVW) {  // a warp per node, all vectors
+      for (int t = warp; t < nn; t += kTreeWarpsM) {
+        const int64_t ch = node0 + t;
+        float acc[RPL][NVB];
 #pragma unroll
-      for (int r = 0; r < RPL; r++)
+        for (int r = 0; r < RPL; r++)
 #pragma unroll
-        for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
-      stage_vectors<false>(wbuf, P.yhat + ((ch - 1) / 2) * P.nv * P.kp, P.nv * P.kp, lane);
-      warp_mv_m<F, RPL, NVB>(static_cast<const typename CodeT<F>::T*>(P.E) + (ch - 1) * P.kk8, P.escale[ch - 1], P.k,
-                             P.k, P.LR, wbuf, P.kp, P.nv, acc, lane);
-      __syncwarp();
-      group_reduce_m(acc, P.LR);
-      store_node_m<RPL, NVB, true>(P.yhat + ch * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, acc, lane);
+          for (int v = 0; v < NVB; v++) acc[r][v] = 0.f;
+        stage_vectors<false>(wbuf, P.yhat + ((ch - 1) / 2) * P.nv * P.kp, P.nv * P.kp, lane);
+        warp_mv_m<F, RPL, NVB>(static_cast<const typename CodeT<F>::T*>(P.E) + (ch - 1) * P.kk8, P.escale[ch - 1], P.k,
+                               P.k, P.LR, wbuf, P.kp, P.nv, acc, lane);
+        __syncwarp();
+        group_reduce_m(acc, P.LR);
+        store_node_m<RPL, NVB, true>(P.yhat + ch * P.nv * P.kp, P.k, P.kp, P.LR, P.nv, acc, lane);
+      }
+    } else {  // fewer nodes than warps: a warp per (node, slice of NVW vectors)
+      const int ns = (P.nv + NVW - 1) / NVW;
+      for (int u = warp; u < nn * ns; u += kTreeWarpsM) {
+        const int64_t ch = node0 + u % nn;
+        const int s0 = (u / nn) * NVW, sw = min(NVW, P.nv - s0);
+        float acc[RPL][NVW];
+#pragma unroll
+        for (int r = 0; r < RPL; r++)
+#pragma unroll
+          for (int v = 0; v < NVW; v++) acc[r][v] = 0.f;
+        stage_vectors<false>(wbuf, P.yhat + (((ch - 1) / 2) * P.nv + s0) * P.kp, sw * P.kp, lane);
+        warp_mv_m<F, RPL, NVW>(static_cast<const typename CodeT<F>::T*>(P.E) + (ch - 1) * P.kk8, P.escale[ch - 1], P.k,
+                               P.k, P.LR, wbuf, P.kp, sw, acc, lane);
+        __syncwarp();
+        group_reduce_m(acc, P.LR);
+        store_node_m<RPL, NVW, true>(P.yhat + (ch * P.nv + s0) * P.kp, P.k, P.kp, P.LR, sw, acc, lane);
+      }
     }
     __syncthreads();
   }
